@@ -1,0 +1,427 @@
+/*
+ * fbf_oracle.c -- plain, slow, FP64 CPU oracle for the shiftable Fourier-kernel
+ * bilateral filter of Ghosh & Chaudhury, "On Fast Bilateral Filtering using
+ * Fourier Kernels" (arXiv 1603.08081).
+ *
+ * TEST INFRASTRUCTURE.  Only the test suite, the package smoke check and the
+ * benchmark's CPU-baseline leg load this library.  It shares no code, header,
+ * table or helper with the CUDA library, and neither side includes the other.
+ *
+ * What is here, each function citing the passage it follows:
+ *   orc_phi            range kernels: Gaussian eq. (3); exponential (Sec. I)
+ *   orc_fit_samples    least-squares fit of the cosine series eq. (6) to samples,
+ *                      eqs. (7)-(8), smallest order with residual <= eps (Sec. III)
+ *   orc_fit            the same on the grid Lambda_T of Sec. III / Algorithm 2
+ *   orc_weights_1d     spatial kernel eq. (2) on Omega = [-W, W]^2, sum w = 1
+ *                      (Sec. IV); box kernel (Sec. I)
+ *   orc_direct         direct O(W^2)-per-pixel filter: eq. (1) with the exact
+ *                      range kernel, or eq. (9) with phi_N
+ *   orc_alg1           Algorithm 1 in the paper's complex notation, eqs. (4)-(5)
+ *   orc_grad_direct    d/df(m) of sum_i g(i) fhat(i), fhat from eq. (9)
+ *
+ * The fit uses Householder QR, deliberately not the modified Gram-Schmidt
+ * recursion of Algorithm 2, so the two are independent: the least-squares
+ * solution is unique, and both must reach it.
+ *
+ * Readings of the paper taken here (the paper is silent or garbled there):
+ *   * basis columns are cos(k*omega*t), k = 0..K-1, omega = pi/T; K counts
+ *     coefficients d_0..d_{K-1} (the order "N" of Tables 3-4);
+ *   * the fit stops at the first K with ||b - A d||_2 <= eps;
+ *   * borders: REFLECT is half-sample symmetric (index -1 -> 0, period 2n);
+ *     TRUNCATE sums only over neighbours inside the image;
+ *   * Gaussian W defaults to ceil(3 sigma_s) (Sec. I gives W = 3 sigma_s); the
+ *     box kernel is uniform over [-W, W]^2.
+ */
+#define _USE_MATH_DEFINES
+#include <complex.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+#define ORC_RANGE_GAUSSIAN 0
+#define ORC_RANGE_EXPONENTIAL 1
+#define ORC_SPATIAL_GAUSSIAN 0
+#define ORC_SPATIAL_BOX 1
+#define ORC_BORDER_REFLECT 0
+#define ORC_BORDER_TRUNCATE 1
+
+int orc_num_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+/* Range kernel.  Gaussian: eq. (3).  Exponential: exp(-|t|/sigma_r), the kernel
+ * of the works cited in Sec. I (the paper names it without printing it). */
+double orc_phi(int kernel, double sigma_r, double t) {
+  if (kernel == ORC_RANGE_EXPONENTIAL) return exp(-fabs(t) / sigma_r);
+  return exp(-(t * t) / (2.0 * sigma_r * sigma_r));
+}
+
+/* phi_N(t) = d_0 + sum_{k>=1} d_k cos(k omega t), omega = pi / T  (eq. (6)). */
+double orc_phi_n(const double *d, int K, double T, double t) {
+  double omega = M_PI / T, s = 0.0;
+  for (int k = 0; k < K; ++k) s += d[k] * cos((double)k * omega * t);
+  return s;
+}
+
+/* Least squares over the columns a_k = [cos(k omega t_l)]_l, k = 0..K-1
+ * (eqs. (7)-(8)).  For K = 1, 2, ... solve min_d ||b - A_K d||_2 and stop at the
+ * first K with E_K = ||b - A_K d||_2 <= eps (Sec. III, the loop of Algorithm 2).
+ * K_fixed > 0 solves at exactly that K instead.
+ *
+ * Householder QR: after reflection j the leading (j+1)x(j+1) block of R and the
+ * first j+1 entries of Q^T b are those of the (j+1)-column problem, so each K
+ * costs one back-substitution plus a residual evaluated directly as b - A d.
+ *
+ * Returns 0 (converged / fixed K reached), 1 (eps not reached by Kmax columns),
+ * -1 (bad argument).  d_out gets K_out coefficients. */
+int orc_fit_samples(const double *t, const double *b, int L, double T, double eps,
+                    int K_fixed, int Kmax, double *d_out, int *K_out, double *E_out,
+                    double *linf_out) {
+  if (L < 1 || !(T > 0.0) || Kmax < 1) return -1;
+  int Kcap = K_fixed > 0 ? K_fixed : Kmax;
+  if (Kcap > L) {
+    if (K_fixed > 0) return -1;
+    Kcap = L;
+  }
+  double omega = M_PI / T;
+  double *A = malloc(sizeof(double) * (size_t)L * Kcap); /* column-major, untouched */
+  double *M = malloc(sizeof(double) * (size_t)L * Kcap); /* reduced in place to R */
+  double *y = malloc(sizeof(double) * (size_t)L);
+  double *v = malloc(sizeof(double) * (size_t)L);
+  double *d = malloc(sizeof(double) * (size_t)Kcap);
+  for (int k = 0; k < Kcap; ++k)
+    for (int l = 0; l < L; ++l) A[(size_t)k * L + l] = cos((double)k * omega * t[l]);
+  memcpy(M, A, sizeof(double) * (size_t)L * Kcap);
+  memcpy(y, b, sizeof(double) * (size_t)L);
+
+  int status = 1, K = Kcap;
+  double E = INFINITY, linf = INFINITY;
+  for (int j = 0; j < Kcap; ++j) {
+    double *cj = M + (size_t)j * L;
+    double nrm = 0.0;
+    for (int l = j; l < L; ++l) nrm += cj[l] * cj[l];
+    nrm = sqrt(nrm);
+    double alpha = cj[j] > 0.0 ? -nrm : nrm;
+    double vv = 0.0;
+    for (int l = j; l < L; ++l) v[l] = cj[l];
+    v[j] -= alpha;
+    for (int l = j; l < L; ++l) vv += v[l] * v[l];
+    if (vv > 0.0) {
+      for (int c = j + 1; c < Kcap; ++c) {
+        double *cc = M + (size_t)c * L, s = 0.0;
+        for (int l = j; l < L; ++l) s += v[l] * cc[l];
+        s = 2.0 * s / vv;
+        for (int l = j; l < L; ++l) cc[l] -= s * v[l];
+      }
+      double s = 0.0;
+      for (int l = j; l < L; ++l) s += v[l] * y[l];
+      s = 2.0 * s / vv;
+      for (int l = j; l < L; ++l) y[l] -= s * v[l];
+    }
+    cj[j] = alpha;
+    for (int l = j + 1; l < L; ++l) cj[l] = 0.0;
+
+    /* Solve R d = (Q^T b) for the first j+1 unknowns (back-substitution). */
+    int n = j + 1;
+    for (int i = n - 1; i >= 0; --i) {
+      double s = y[i];
+      for (int c = i + 1; c < n; ++c) s -= M[(size_t)c * L + i] * d[c];
+      d[i] = s / M[(size_t)i * L + i];
+    }
+    /* Residual evaluated directly: E = ||b - A d||, plus its max norm. */
+    double e2 = 0.0, emax = 0.0;
+    for (int l = 0; l < L; ++l) {
+      double r = b[l];
+      for (int c = 0; c < n; ++c) r -= A[(size_t)c * L + l] * d[c];
+      e2 += r * r;
+      if (fabs(r) > emax) emax = fabs(r);
+    }
+    E = sqrt(e2);
+    linf = emax;
+    if (K_fixed == 0 && E <= eps) {
+      status = 0;
+      K = n;
+      break;
+    }
+    if (K_fixed > 0 && n == K_fixed) {
+      status = 0;
+      K = n;
+      break;
+    }
+  }
+  for (int k = 0; k < K; ++k) d_out[k] = d[k];
+  *K_out = K;
+  *E_out = E;
+  *linf_out = linf;
+  free(A);
+  free(M);
+  free(y);
+  free(v);
+  free(d);
+  return status;
+}
+
+/* The fit on the sampling grid of Sec. III: Lambda_T = {0, 1, ..., T} when
+ * levels == 0 (T a positive integer), else `levels` equispaced points on [0, T]
+ * (a reading for non-integer T, e.g. T = 1 with 256 quantisation levels).
+ * b = [phi(t)]_t (the first sampling step of Algorithm 2).  Kmax caps K. */
+int orc_fit(int kernel, double sigma_r, double T, double eps, int K_fixed, int levels,
+            int Kmax, double *d_out, int *K_out, double *E_out, double *linf_out) {
+  if (!(T > 0.0) || !(sigma_r > 0.0)) return -1;
+  int L;
+  if (levels == 0) {
+    if (T != floor(T) || T > 1e6) return -1;
+    L = (int)T + 1;
+  } else {
+    if (levels < 2) return -1;
+    L = levels;
+  }
+  double *t = malloc(sizeof(double) * (size_t)L), *b = malloc(sizeof(double) * (size_t)L);
+  for (int l = 0; l < L; ++l) {
+    t[l] = levels == 0 ? (double)l : (double)l * T / (double)(levels - 1);
+    b[l] = orc_phi(kernel, sigma_r, t[l]);
+  }
+  int kmax = Kmax < L ? Kmax : L;
+  int st = orc_fit_samples(t, b, L, T, eps, K_fixed, kmax, d_out, K_out, E_out, linf_out);
+  free(t);
+  free(b);
+  return st;
+}
+
+/* 1-D spatial weights on [-W, W] (w1[j + W] = weight of offset j), normalised
+ * to sum 1 so that the 2-D weights w(j) = w1(j_y) w1(j_x) sum to 1 (Sec. IV).
+ * Gaussian: eq. (2), separable as exp(-j_y^2/2s^2) exp(-j_x^2/2s^2).  Box:
+ * uniform.  Returns the tap count 2W + 1, or -1. */
+int orc_weights_1d(int spatial, double sigma_s, int W, double *w1) {
+  if (W < 0) return -1;
+  double s = 0.0;
+  for (int j = -W; j <= W; ++j) {
+    double v = spatial == ORC_SPATIAL_BOX ? 1.0
+                                          : exp(-(double)(j * j) / (2.0 * sigma_s * sigma_s));
+    w1[j + W] = v;
+    s += v;
+  }
+  for (int j = 0; j < 2 * W + 1; ++j) w1[j] /= s;
+  return 2 * W + 1;
+}
+
+/* Half-sample symmetric reflection into [0, n): ... 1 0 | 0 1 ... n-1 | n-1 ... */
+static long orc_reflect(long i, long n) {
+  long p = 2 * n;
+  long m = i % p;
+  if (m < 0) m += p;
+  return m < n ? m : p - 1 - m;
+}
+
+/* Direct evaluation of eq. (1) (use_phi_n == 0, exact range kernel) or of eq.
+ * (9) (use_phi_n != 0, phi replaced by phi_N of eq. (6)) at every pixel, or at
+ * the npts pixels (ys[p], xs[p]) when ys != NULL.  The sum runs over j in
+ * Omega = [-W, W]^2 with neighbour f(i - j); out = P / Q with P, Q the
+ * numerator and denominator (the P_1, Q_1 / P_2, Q_2 of the Appendix). */
+void orc_direct(const double *f, int H, int Wd, const double *w1, int W, int border,
+                int use_phi_n, int kernel, double sigma_r, const double *d, int K, double T,
+                const int *ys, const int *xs, long npts, double *out, double *P, double *Q) {
+  long n = ys ? npts : (long)H * Wd;
+#pragma omp parallel for schedule(dynamic, 16)
+  for (long p = 0; p < n; ++p) {
+    long iy = ys ? ys[p] : p / Wd, ix = ys ? xs[p] : p % Wd;
+    double fc = f[iy * Wd + ix], num = 0.0, den = 0.0;
+    for (int jy = -W; jy <= W; ++jy) {
+      long sy = iy - jy;
+      if (border == ORC_BORDER_REFLECT) sy = orc_reflect(sy, H);
+      else if (sy < 0 || sy >= H) continue;
+      for (int jx = -W; jx <= W; ++jx) {
+        long sx = ix - jx;
+        if (border == ORC_BORDER_REFLECT) sx = orc_reflect(sx, Wd);
+        else if (sx < 0 || sx >= Wd) continue;
+        double fn = f[sy * Wd + sx];
+        double t = fn - fc;
+        double ph = use_phi_n ? orc_phi_n(d, K, T, t) : orc_phi(kernel, sigma_r, t);
+        double wj = w1[jy + W] * w1[jx + W];
+        num += wj * ph * fn;
+        den += wj * ph;
+      }
+    }
+    out[p] = num / den;
+    if (P) P[p] = num;
+    if (Q) Q[p] = den;
+  }
+}
+
+/* Separable 2-D convolution Y = X * w on output rows [r0, r1): Y(i) =
+ * sum_j w1(j_y) w1(j_x) X(i - j), X extended by the border rule.  X holds the
+ * image rows [xr0, xr1) (enough for the outputs requested). */
+static void orc_conv2(const double complex *X, int xr0, int xr1, int H, int Wd,
+                      const double *w1, int W, int border, int r0, int r1, double complex *Y,
+                      double complex *tmp) {
+  int he = r1 - r0 + 2 * W;
+  (void)xr1;
+#pragma omp parallel for schedule(static)
+  for (int k = 0; k < he; ++k) {
+    long e = (long)r0 - W + k; /* extended row index */
+    double complex *trow = tmp + (size_t)k * Wd;
+    if (border == ORC_BORDER_TRUNCATE && (e < 0 || e >= H)) {
+      for (int x = 0; x < Wd; ++x) trow[x] = 0.0;
+      continue;
+    }
+    long s = border == ORC_BORDER_REFLECT ? orc_reflect(e, H) : e;
+    const double complex *xrow = X + (size_t)(s - xr0) * Wd;
+    for (int x = 0; x < Wd; ++x) {
+      double complex acc = 0.0;
+      for (int j = -W; j <= W; ++j) {
+        long sx = (long)x - j;
+        if (border == ORC_BORDER_REFLECT) sx = orc_reflect(sx, Wd);
+        else if (sx < 0 || sx >= Wd) continue;
+        acc += w1[j + W] * xrow[sx];
+      }
+      trow[x] = acc;
+    }
+  }
+#pragma omp parallel for schedule(static)
+  for (int y = r0; y < r1; ++y) {
+    for (int x = 0; x < Wd; ++x) {
+      double complex acc = 0.0;
+      for (int j = -W; j <= W; ++j) acc += w1[j + W] * tmp[(size_t)(y - j - r0 + W) * Wd + x];
+      Y[(size_t)(y - r0) * Wd + x] = acc;
+    }
+  }
+}
+
+/* Algorithm 1 (Shiftable Bilateral Filtering) in the paper's complex notation,
+ * for output rows [r0, r1).  With N = K - 1 and c_0 = d_0, c_{+-n} = d_n / 2
+ * (Sec. III, below eq. (6)):
+ *   for n = -N..N:  G = exp(i n omega f),  F = G f,  H = c_n conj(G),
+ *                   Fbar = F * w,  Gbar = G * w   (eq. (5) and its analogue),
+ *                   P += H Fbar,  Q += H Gbar;
+ *   out = P / Q.
+ * (The paper's line computing the convolutions prints "Gbar" twice; the first is
+ * Fbar = F * w, which the next line uses.)  P and Q are real up to rounding;
+ * their imaginary parts are returned for checking.  Arrays are (r1-r0) x Wd. */
+int orc_alg1(const double *f, int H, int Wd, const double *w1, int W, int border,
+             const double *d, int K, double T, int r0, int r1, double *out, double *P,
+             double *Q, double *Pim, double *Qim) {
+  if (r0 < 0 || r1 > H || r0 >= r1 || K < 1 || !(T > 0.0)) return -1;
+  int xr0 = r0 - W < 0 ? 0 : r0 - W, xr1 = r1 + W > H ? H : r1 + W;
+  if (border == ORC_BORDER_REFLECT && (W >= r0 || r1 + W > H)) { /* reflected rows */
+    xr0 = 0;
+    xr1 = H;
+  }
+  size_t nx = (size_t)(xr1 - xr0) * Wd, ny = (size_t)(r1 - r0) * Wd;
+  size_t nt = (size_t)(r1 - r0 + 2 * W) * Wd;
+  double complex *G = malloc(sizeof(double complex) * nx);
+  double complex *F = malloc(sizeof(double complex) * nx);
+  double complex *Fb = malloc(sizeof(double complex) * ny);
+  double complex *Gb = malloc(sizeof(double complex) * ny);
+  double complex *Pc = calloc(ny, sizeof(double complex));
+  double complex *Qc = calloc(ny, sizeof(double complex));
+  double complex *tmp = malloc(sizeof(double complex) * nt);
+  double omega = M_PI / T;
+  int N = K - 1;
+  for (int n = -N; n <= N; ++n) {
+    int an = n < 0 ? -n : n;
+    double cn = n == 0 ? d[0] : 0.5 * d[an];
+#pragma omp parallel for schedule(static)
+    for (long p = 0; p < (long)nx; ++p) {
+      double fv = f[(size_t)xr0 * Wd + p];
+      G[p] = cexp(I * ((double)n * omega * fv));
+      F[p] = G[p] * fv;
+    }
+    orc_conv2(F, xr0, xr1, H, Wd, w1, W, border, r0, r1, Fb, tmp);
+    orc_conv2(G, xr0, xr1, H, Wd, w1, W, border, r0, r1, Gb, tmp);
+#pragma omp parallel for schedule(static)
+    for (long p = 0; p < (long)ny; ++p) {
+      double fv = f[(size_t)r0 * Wd + p];
+      double complex Hc = cn * conj(cexp(I * ((double)n * omega * fv)));
+      Pc[p] += Hc * Fb[p];
+      Qc[p] += Hc * Gb[p];
+    }
+  }
+  for (size_t p = 0; p < ny; ++p) {
+    out[p] = creal(Pc[p]) / creal(Qc[p]);
+    if (P) P[p] = creal(Pc[p]);
+    if (Q) Q[p] = creal(Qc[p]);
+    if (Pim) Pim[p] = cimag(Pc[p]);
+    if (Qim) Qim[p] = cimag(Qc[p]);
+  }
+  free(G);
+  free(F);
+  free(Fb);
+  free(Gb);
+  free(Pc);
+  free(Qc);
+  free(tmp);
+  return 0;
+}
+
+/* Derivative of phi_N: phi_N'(t) = -sum_k k omega d_k sin(k omega t). */
+static double orc_dphi_n(const double *d, int K, double T, double t) {
+  double omega = M_PI / T, s = 0.0;
+  for (int k = 1; k < K; ++k) s -= (double)k * omega * d[k] * sin((double)k * omega * t);
+  return s;
+}
+
+/* Gradient of L = sum_i g(i) fhat(i), fhat = P_2 / Q_2 of eq. (9), with respect
+ * to every input pixel f(m), by direct differentiation of the window sums:
+ *   dL/df(m) = sum_i g(i)/Q(i) [dP(i)/df(m) - fhat(i) dQ(i)/df(m)].
+ * f(m) enters P(i), Q(i) as a neighbour (every (i, j) whose mapped source
+ * index i - j is m) and as the centre (i = m).  For one pair (i, j) with
+ * neighbour value u = f(i-j), centre c = f(i), t = u - c:
+ *   P term  w phi_N(t) u :  d/du = w (phi_N(t) + u phi_N'(t)),  d/dc = -w u phi_N'(t)
+ *   Q term  w phi_N(t)   :  d/du = w phi_N'(t),                  d/dc = -w phi_N'(t)
+ * Under REFLECT a mirrored neighbour index that maps onto m contributes to m;
+ * under TRUNCATE neighbours outside the image are absent.  T, omega and d are
+ * constants.  Evaluated by looping over every output pixel and scattering,
+ * serial over rows of i to keep the scatter race-free. */
+void orc_grad_direct(const double *f, const double *g, int H, int Wd, const double *w1, int W,
+                     int border, const double *d, int K, double T, double *grad) {
+  size_t np = (size_t)H * Wd;
+  double *a = malloc(sizeof(double) * np), *bb = malloc(sizeof(double) * np);
+  double *P = malloc(sizeof(double) * np), *Q = malloc(sizeof(double) * np);
+  double *out = malloc(sizeof(double) * np);
+  orc_direct(f, H, Wd, w1, W, border, 1, 0, 1.0, d, K, T, NULL, NULL, 0, out, P, Q);
+  for (size_t p = 0; p < np; ++p) {
+    a[p] = g[p] / Q[p];        /* weight of dP */
+    bb[p] = g[p] * out[p] / Q[p]; /* weight of dQ */
+    grad[p] = 0.0;
+  }
+  for (long iy = 0; iy < H; ++iy) {
+    for (long ix = 0; ix < Wd; ++ix) {
+      size_t i = (size_t)iy * Wd + ix;
+      double c = f[i];
+      double centre = 0.0;
+      for (int jy = -W; jy <= W; ++jy) {
+        long sy = iy - jy;
+        if (border == ORC_BORDER_REFLECT) sy = orc_reflect(sy, H);
+        else if (sy < 0 || sy >= H) continue;
+        for (int jx = -W; jx <= W; ++jx) {
+          long sx = ix - jx;
+          if (border == ORC_BORDER_REFLECT) sx = orc_reflect(sx, Wd);
+          else if (sx < 0 || sx >= Wd) continue;
+          size_t m = (size_t)sy * Wd + sx;
+          double u = f[m], t = u - c;
+          double wj = w1[jy + W] * w1[jx + W];
+          double ph = orc_phi_n(d, K, T, t), dph = orc_dphi_n(d, K, T, t);
+          grad[m] += wj * (a[i] * (ph + u * dph) - bb[i] * dph);
+          centre += wj * (-a[i] * u * dph + bb[i] * dph);
+        }
+      }
+      grad[i] += centre;
+    }
+  }
+  free(a);
+  free(bb);
+  free(P);
+  free(Q);
+  free(out);
+}
