@@ -312,10 +312,14 @@ int orc_alg1(const double *f, int H, int Wd, const double *w1, int W, int border
              const double *d, int K, double T, int r0, int r1, double *out, double *P,
              double *Q, double *Pim, double *Qim) {
   if (r0 < 0 || r1 > H || r0 >= r1 || K < 1 || !(T > 0.0)) return -1;
-  int xr0 = r0 - W < 0 ? 0 : r0 - W, xr1 = r1 + W > H ? H : r1 + W;
-  if (border == ORC_BORDER_REFLECT && (W >= r0 || r1 + W > H)) { /* reflected rows */
-    xr0 = 0;
-    xr1 = H;
+  /* Source rows [xr0, xr1) that the window of rows [r0, r1) reaches. */
+  int xr0 = H, xr1 = 0;
+  for (long e = (long)r0 - W; e < (long)r1 + W; ++e) {
+    long s = e;
+    if (border == ORC_BORDER_REFLECT) s = orc_reflect(e, H);
+    else if (e < 0 || e >= H) continue;
+    if (s < xr0) xr0 = (int)s;
+    if (s + 1 > xr1) xr1 = (int)s + 1;
   }
   size_t nx = (size_t)(xr1 - xr0) * Wd, ny = (size_t)(r1 - r0) * Wd;
   size_t nt = (size_t)(r1 - r0 + 2 * W) * Wd;
