@@ -1,0 +1,388 @@
+"""Benchmark: Mpixel/s of the shiftable Fourier-kernel bilateral filter on GB300.
+
+Workload (one "step"): one 2048x2048 uint8 synthetic image (seed 1100; see
+paper_1603_08081_gb300/synth.py) filtered under all six settings
+sigma_s in {3, 5, 10} x sigma_r in {20, 40}, Gaussian spatial and range kernels,
+coefficients fitted to eps = 1e-3 (K = 17 for sigma_r = 20, K = 9 for 40),
+REFLECT border.  The coefficient fit is host work done once and reported apart.
+
+Printed: ONE JSON line (rank 0).  `value` is whole-job Mpixel/s with inputs
+resident in HBM; `e2e` is the same metric through the public Python API with
+pinned host buffers (H2D of the image and D2H of every output inside the timed
+region).  The L2 is flushed (256 MiB write) between timed steps, outside the
+per-step events.  `roofline` is for the dominant kernel launch (largest share
+of the step), FP32-pipe bound, against an FFMA peak measured in the same
+process.  `cpu_baseline` times the FP64 oracle (Algorithm 1 form) on a
+bounded row slab of the same workload and reports its agreement with the GPU
+output on that slab (the max-error condition of the metric).
+
+--impl reference times that oracle alone, as the reference arm.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Mpixel/s at max err <=0.5 gray level: FP32 plain vs BF16 tensor-core form"
+H = W_IMG = 2048
+SEED = 1100
+SETTINGS = [(ss, sr) for ss in (3.0, 5.0, 10.0) for sr in (20.0, 40.0)]
+EPS = 1e-3
+T = 255.0
+WORKLOAD = "2048x2048 u8 synthetic (seed 1100), sigma_s in {3,5,10} x sigma_r in {20,40}, eps=1e-3, reflect"
+
+
+def algorithmic_flops_per_pixel(K: int, W: int) -> float:
+    """2 flops per multiply-add of the separable FIR over C = 4(K-1) + 2 real
+    channels (cos, sin, f cos, f sin per harmonic n >= 1; f and 1 for n = 0),
+    two passes of 2W+1 taps."""
+    C = 4 * (K - 1) + 2
+    return 2.0 * 2.0 * (2 * W + 1) * C
+
+
+# ----------------------------------------------------------------- helpers ---
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self._t.join(timeout=2)
+
+    def summary(self):
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        backend = "nccl" if os.environ.get("FBF_BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+        dist.init_process_group(backend=backend, rank=rank, world_size=world)
+    return world, rank, local
+
+
+def dist_max(x: float, world: int, device=None) -> float:
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dist_barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+# ------------------------------------------------------------- CPU oracle ---
+
+def oracle_slab(img, ss, sr, rows):
+    import oracle as O
+
+    fit = O.fit(O.RANGE_GAUSSIAN, sr, T, EPS)
+    Wn = O.default_W(ss)
+    w1 = O.weights_1d(O.SPATIAL_GAUSSIAN, ss, Wn)
+    t0 = time.perf_counter()
+    out = O.alg1(img, w1, O.BORDER_REFLECT, fit.d, T, rows=rows)[0]
+    return out, time.perf_counter() - t0
+
+
+def cpu_baseline(img, slab_rows: int, gpu_outs=None):
+    """Oracle (FP64 Algorithm 1) on rows [0, slab_rows) of every setting; the
+    slab includes the top border.  Returns the baseline dict and the max error
+    of the GPU outputs on the same slabs (when given)."""
+    import oracle as O
+
+    total_t, total_px, max_err = 0.0, 0, 0.0
+    per = []
+    for i, (ss, sr) in enumerate(SETTINGS):
+        out, dt = oracle_slab(img, ss, sr, (0, slab_rows))
+        total_t += dt
+        total_px += out.size
+        if gpu_outs is not None:
+            e = float(np.max(np.abs(gpu_outs[i][:slab_rows].astype(np.float64) - out)))
+            max_err = max(max_err, e)
+            per.append(e)
+    res = {"value": total_px / total_t / 1e6, "unit": "Mpixel/s", "cores": O.num_threads(),
+           "kind": "oracle",
+           "sample": "FP64 Algorithm-1 oracle on rows 0..%d of the 2048x2048 image, all 6 settings"
+                     " (%d pixels, %.1f s)" % (slab_rows - 1, total_px, total_t)}
+    return res, (max_err if gpu_outs is not None else None), per
+
+
+# ------------------------------------------------------------- FFMA peak ---
+
+def ffma_peak_tflops(torch):
+    """FP32 FMA-pipe throughput measured with the library's FFMA probe kernel."""
+    from paper_1603_08081_gb300 import fbf
+
+    return fbf.fbf_measure_fp32_peak()
+
+
+# ------------------------------------------------------------------ main ---
+
+def run_ours(args):
+    import torch
+
+    world, rank, local = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1603_08081_gb300 import fbf
+    from paper_1603_08081_gb300.synth import make_image
+
+    img = make_image(H, W_IMG, SEED)
+    t0 = time.perf_counter()
+    coeffs = [fbf.fbf_fit_coeffs("gaussian", sr, T, EPS) for (_, sr) in SETTINGS]
+    fit_ms = (time.perf_counter() - t0) * 1e3 / len(SETTINGS)
+    params = [fbf.make_params(c, ss, 0, "gaussian", "reflect", args.form)
+              for c, (ss, _) in zip(coeffs, SETTINGS)]
+    Ws = [fbf.fbf_resolve_window(p) for p in params]
+
+    stream = torch.cuda.Stream(device=dev)
+    x = torch.from_numpy(img).to(dev)
+    outs = [torch.empty((H, W_IMG), dtype=torch.float32, device=dev) for _ in SETTINGS]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    n_set = len(SETTINGS)
+
+    def step(evs=None):
+        for i, p in enumerate(params):
+            if evs is not None:
+                evs[i][0].record(stream)
+            fbf.fbf_filter(p, x, out=outs[i], stream=stream)
+            if evs is not None:
+                evs[i][1].record(stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(max(args.warmup, 3)):
+            step()
+    torch.cuda.synchronize(dev)
+
+    ev = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(n_set)]
+          for _ in range(args.steps)]
+    per_launch = np.zeros((args.steps, n_set))
+    dist_barrier(world)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        for s in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            step(ev[s])
+        torch.cuda.synchronize(dev)
+    dist_barrier(world)
+    for s in range(args.steps):
+        for i in range(n_set):
+            per_launch[s, i] = ev[s][i][0].elapsed_time(ev[s][i][1])
+    step_ms = per_launch.sum(axis=1)
+    total_ms = float(step_ms.sum())
+    total_ms = dist_max(total_ms, world, dev)
+    px_step = n_set * H * W_IMG
+    value = world * px_step * args.steps / (total_ms * 1e-3) / 1e6
+
+    # Dominant launch: the setting with the largest mean time.
+    mean_launch = per_launch.mean(axis=0)
+    dom = int(np.argmax(mean_launch))
+    K_dom, W_dom = coeffs[dom].K, Ws[dom]
+    flops = algorithmic_flops_per_pixel(K_dom, W_dom) * H * W_IMG
+    achieved = flops / (mean_launch[dom] * 1e-3) / 1e12
+    peak = fbf.fbf_measure_fp32_peak(local)
+    per_setting = []
+    for i, (ss, sr) in enumerate(SETTINGS):
+        per_setting.append({
+            "sigma_s": ss, "sigma_r": sr, "K": coeffs[i].K, "W": Ws[i],
+            "ms": round(float(mean_launch[i]), 4),
+            "mpix_s": round(H * W_IMG / (mean_launch[i] * 1e-3) / 1e6, 1),
+            "fp32_tflops_algorithmic": round(algorithmic_flops_per_pixel(coeffs[i].K, Ws[i]) * H * W_IMG
+                                             / (mean_launch[i] * 1e-3) / 1e12, 2)})
+
+    # End to end through the public API: pinned host image in, every output back.
+    host_in = torch.from_numpy(img).pin_memory()
+    host_outs = [torch.empty((H, W_IMG), dtype=torch.float32).pin_memory() for _ in SETTINGS]
+    e2e_steps = max(2, min(args.steps, 5))
+
+    def e2e_step():
+        with torch.cuda.stream(stream):
+            xd = host_in.to(dev, non_blocking=True)
+            for i, p in enumerate(params):
+                y = fbf.fbf_filter(p, xd, out=outs[i], stream=stream)
+                host_outs[i].copy_(y, non_blocking=True)
+        stream.synchronize()
+
+    e2e_step()
+    dist_barrier(world)
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        e2e_step()
+    torch.cuda.synchronize(dev)
+    e2e_s = dist_max(time.perf_counter() - t0, world, dev)
+    e2e_val = world * px_step * e2e_steps / e2e_s / 1e6
+
+    result = {
+        "metric": METRIC, "value": round(value, 1), "unit": "Mpixel/s", "n_gpus": world,
+        "steps": args.steps, "warmup": max(args.warmup, 3),
+        "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "form": args.form,
+        "config": {"workload": WORKLOAD, "image": "2048x2048 u8", "settings": len(SETTINGS),
+                   "eps": EPS, "T": T, "border": "reflect", "spatial": "gaussian",
+                   "l2": "flushed between steps (256 MiB write, outside the timed events)",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "fit_ms_per_setting": round(fit_ms, 3),
+        "per_setting": per_setting,
+        "roofline": {"bound": "alu", "kernel": "fbf_fp32_u8_kernel",
+                     "launch": "sigma_s=%g sigma_r=%g K=%d W=%d" % (SETTINGS[dom][0], SETTINGS[dom][1], K_dom, W_dom),
+                     "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
+                     "frac": round(achieved / peak, 4), "traffic": None,
+                     "peak_source": "FP32 FFMA probe measured in this process (of measured)"},
+        "e2e": {"value": round(e2e_val, 1), "unit": "Mpixel/s",
+                "h2d_bytes_per_step": H * W_IMG, "d2h_bytes_per_step": n_set * H * W_IMG * 4},
+        "gpu_launches": n_set * args.steps,
+        "clocks": clk.summary(),
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        torch.cuda.synchronize(dev)
+        gpu_outs = [o.cpu().numpy() for o in outs]
+        cb, max_err, per_err = cpu_baseline(img.astype(np.float64), args.slab_rows, gpu_outs)
+        result["cpu_baseline"] = cb
+        result["max_err_vs_oracle"] = round(max_err, 6)
+        result["accuracy_ok"] = bool(max_err <= 0.5)
+        for i, e in enumerate(per_err):
+            result["per_setting"][i]["max_err_vs_oracle"] = round(e, 6)
+    if rank == 0:
+        print(json.dumps(result), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+
+
+def run_reference(args):
+    """Reference arm: the FP64 oracle itself on a bounded sample, per step."""
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1603_08081_gb300.synth import make_image
+
+    import oracle as O
+
+    img = make_image(H, W_IMG, SEED).astype(np.float64)
+    rows = args.ref_rows
+    for _ in range(args.warmup if args.warmup < 1 else 1):
+        oracle_slab(img, *SETTINGS[0], (0, rows))
+    t_all, px = 0.0, 0
+    for s in range(args.steps):
+        for (ss, sr) in SETTINGS:
+            r0 = (s * 97) % (H - rows)
+            out, dt = oracle_slab(img, ss, sr, (r0, r0 + rows))
+            t_all += dt
+            px += out.size
+    value = px / t_all / 1e6
+    sample = ("FP64 Algorithm-1 oracle, %d-row slab of the 2048x2048 image per setting per step,"
+              " 6 settings" % rows)
+    res = {"impl": "reference", "metric": METRIC, "value": round(value, 4), "unit": "Mpixel/s",
+           "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": round(t_all / args.steps * 1e3, 2), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "sample_rows_per_setting": rows},
+           "cpu_baseline": {"value": round(value, 4), "unit": "Mpixel/s", "cores": O.num_threads(),
+                            "kind": "oracle", "sample": sample},
+           "e2e": {"value": round(value, 4), "unit": "Mpixel/s", "h2d_bytes_per_step": 0,
+                   "d2h_bytes_per_step": 0}}
+    print(json.dumps(res), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--form", default="fp32", choices=["fp32", "auto", "tc_fp16", "tc_bf16"])
+    ap.add_argument("--slab-rows", type=int, default=24, help="rows of the CPU-baseline sample")
+    ap.add_argument("--ref-rows", type=int, default=8, help="rows per setting per reference step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", type=int, default=None,
+                    help="run a single setting (index into the six) -- for profiling")
+    args = ap.parse_args()
+    global SETTINGS
+    if args.only is not None:
+        SETTINGS = [SETTINGS[args.only]]
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,174 @@
+/*
+ * fbf.h -- C ABI of the GB300 (sm_103a) shiftable Fourier-kernel bilateral filter.
+ *
+ * Method: Ghosh & Chaudhury, "On Fast Bilateral Filtering using Fourier
+ * Kernels" (arXiv 1603.08081).  The bilateral filter of eq. (1),
+ *
+ *     f_BF(i) = sum_j w(j) phi(f(i-j) - f(i)) f(i-j) / sum_j w(j) phi(f(i-j) - f(i)),
+ *
+ * is approximated by replacing the range kernel phi with the cosine series of
+ * eq. (6), phi_N(t) = d_0 + sum_{n=1}^{K-1} d_n cos(n omega t), omega = pi / T,
+ * whose coefficients minimise the squared error on the grid {0, ..., T}
+ * (eqs. (7)-(8), Algorithm 2).  The approximation (eq. (9)) is then computed as
+ * K rounds of modulate / convolve with w / demodulate / accumulate, followed
+ * by one division (Algorithm 1, eqs. (4)-(5)).
+ *
+ * Conventions.
+ *   - K counts the coefficients d_0 .. d_{K-1}.  (The paper's Tables 3-4 call
+ *     this number N; Algorithm 2's column counter is the same K.)
+ *   - Images are single channel, row-major, with a row pitch in BYTES.
+ *   - Device pointers are plain CUDA device pointers; every device call is
+ *     asynchronous on the given stream, never synchronises, and (unless stated)
+ *     allocates nothing.  The caller owns every buffer.
+ *   - Errors are returned as fbf_status; nothing is thrown across the ABI.
+ *     A fault inside a kernel surfaces at the caller's next synchronisation.
+ */
+#ifndef FBF_H
+#define FBF_H
+
+#include <stddef.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FBF_OK = 0,
+  FBF_ERR_INVALID_ARGUMENT = 1, /* null pointer, bad size/pitch, sigma <= 0, ... */
+  FBF_ERR_NOT_CONVERGED = 2,    /* fit: eps not reached within the column limit */
+  FBF_ERR_RANGE = 3,            /* window or order beyond the compiled limits     */
+  FBF_ERR_UNSUPPORTED = 4,      /* valid request this build does not implement   */
+  FBF_ERR_CUDA = 5,             /* a CUDA runtime call or launch failed            */
+  FBF_ERR_TIMEOUT = 6           /* a bounded device-side wait gave up              */
+} fbf_status;
+
+/* Range kernel phi.  Gaussian: eq. (3), phi(t) = exp(-t^2 / (2 sigma_r^2)).
+ * Exponential: phi(t) = exp(-|t| / sigma_r) (the kernel of the works cited in
+ * Sec. I; the paper names it without printing the formula). */
+typedef enum { FBF_RANGE_GAUSSIAN = 0, FBF_RANGE_EXPONENTIAL = 1 } fbf_range_kernel;
+
+/* Spatial kernel w on Omega = [-W, W]^2 (Sec. I).  Gaussian: eq. (2),
+ * separable; box: uniform.  Weights are normalised to sum 1 (Sec. IV). */
+typedef enum { FBF_SPATIAL_GAUSSIAN = 0, FBF_SPATIAL_BOX = 1 } fbf_spatial_kernel;
+
+/* Border rule (the paper leaves it open).  REFLECT: half-sample symmetric
+ * extension (index -1 -> 0, -2 -> 1, ...; repeated for windows wider than the
+ * image).  TRUNCATE: the window sums of eq. (1) run only over pixels inside the
+ * image (equivalently, both modulated channels are zero outside). */
+typedef enum { FBF_BORDER_REFLECT = 0, FBF_BORDER_TRUNCATE = 1 } fbf_border;
+
+/* Element type of the input image. */
+typedef enum { FBF_U8 = 0, FBF_F32 = 1 } fbf_dtype;
+
+/* Arithmetic form of the device filter.  FP32: every step in FP32 on the FMA
+ * pipe.  AUTO: the fastest form this build provides for the request. */
+typedef enum {
+  FBF_FORM_AUTO = 0,
+  FBF_FORM_FP32 = 1,
+  FBF_FORM_TC_FP16 = 2,
+  FBF_FORM_TC_BF16 = 3
+} fbf_form;
+
+#define FBF_KMAX 256 /* maximum number of coefficients K                 */
+#define FBF_WMAX 32  /* maximum half window W (taps 2W+1 <= 65)           */
+
+/* Fitted range-kernel approximation, eq. (6): phi_N(t) = sum_k d[k] cos(k omega t). */
+typedef struct {
+  int K;             /* number of coefficients d[0..K-1]                      */
+  int levels;        /* grid size used by the fit (T+1 for the integer grid)  */
+  double T;          /* half period; omega = pi / T                           */
+  double omega;      /* pi / T                                                */
+  double resid_l2;   /* ||b - A d||_2 on the grid (the E of Algorithm 2)      */
+  double resid_linf; /* max_t |phi(t) - phi_N(t)| on the grid (eq. (10))     */
+  double d[FBF_KMAX];
+} fbf_coeffs;
+
+/* Filter parameters. */
+typedef struct {
+  fbf_spatial_kernel spatial;
+  double sigma_s;           /* Gaussian spatial scale (ignored for the box)      */
+  int W;                    /* half window; <= 0 selects ceil(3 sigma_s)         */
+  fbf_border border;
+  fbf_form form;
+  const fbf_coeffs *coeffs; /* host pointer, read during the call only           */
+} fbf_params;
+
+/*
+ * fbf_fit_coeffs -- Algorithm 2 (Progressive Fourier Approximation), host, FP64.
+ *
+ * Samples b = [phi(t)] on the grid, then grows the basis {1, cos(wt),
+ * cos(2wt), ...} one column at a time, updating a QR factorisation by one
+ * modified Gram-Schmidt step per column, solving R d = Q^T b by
+ * back-substitution, and stopping at the first K with ||b - A d||_2 <= eps
+ * (Sec. III; the residual is evaluated as b - A d).
+ *
+ *   kernel, sigma_r  range kernel phi and its scale (> 0)
+ *   T                half period (> 0); omega = pi / T
+ *   eps              tolerance (> 0) when K_fixed == 0
+ *   K_fixed          > 0: fit exactly this many coefficients, ignore eps
+ *   levels           0: grid {0, 1, ..., T} (T must be an integer);
+ *                    >= 2: that many equispaced points on [0, T]
+ *   out              filled on FBF_OK and on FBF_ERR_NOT_CONVERGED (then with
+ *                    the largest order tried: min(grid size, FBF_KMAX))
+ * Returns FBF_ERR_INVALID_ARGUMENT for bad inputs, FBF_ERR_RANGE if K_fixed
+ * exceeds FBF_KMAX or the grid size.
+ */
+fbf_status fbf_fit_coeffs(fbf_range_kernel kernel, double sigma_r, double T, double eps,
+                          int K_fixed, int levels, fbf_coeffs *out);
+
+/*
+ * fbf_filter -- Algorithm 1 (Shiftable Bilateral Filtering) on the GPU.
+ *
+ * Computes, for every pixel, fhat(i) = P(i) / Q(i) with
+ *   P = sum_n d_n Re[e^{-i n w f} (w * (f e^{i n w f}))],
+ *   Q = sum_n d_n Re[e^{-i n w f} (w * e^{i n w f})],
+ * i.e. eq. (9) with phi_N, by one fused kernel that stages each image tile and
+ * its W halo in shared memory, generates the modulated channels on the fly,
+ * runs the separable row and column passes and accumulates all K terms in
+ * registers: the image is read once and only the output is written.
+ *
+ *   p          parameters; p->coeffs from fbf_fit_coeffs (K <= FBF_KMAX)
+ *   d_in       device image, H rows of Wd elements of type dtype, row pitch
+ *              in_pitch bytes (>= Wd * element size)
+ *   dtype      FBF_U8: values 0..255, coeffs->T must be an integer >= 1
+ *              (the phase n*omega*f is reduced exactly in integers);
+ *              FBF_F32: any finite values (a separate path; see status)
+ *   d_out      device FP32 output, H x Wd, row pitch out_pitch bytes; must not
+ *              overlap d_in
+ *   stream     CUDA stream (0 = legacy default stream)
+ * The approximation guarantee of eq. (12) needs 0 <= f <= T and
+ * T >= every window difference.  H == 0 or Wd == 0 is a no-op.
+ * Returns FBF_ERR_RANGE when W > FBF_WMAX, FBF_ERR_UNSUPPORTED for a form or
+ * dtype this build does not implement, FBF_ERR_CUDA when the launch fails.
+ */
+fbf_status fbf_filter(const fbf_params *p, const void *d_in, fbf_dtype dtype, int H, int Wd,
+                      size_t in_pitch, float *d_out, size_t out_pitch, cudaStream_t stream);
+
+/* Half window actually used for the parameters (W, or ceil(3 sigma_s) when
+ * W <= 0), or -1 when invalid.  Host only. */
+int fbf_resolve_window(const fbf_params *p);
+
+/* Reads and clears the library's device-side error word on the current device
+ * (non-zero when a bounded wait inside a kernel gave up).  Synchronises the
+ * device.  *code receives the word. */
+fbf_status fbf_device_error(unsigned int *code);
+
+/* FP32-pipe throughput probe (the roofline denominator of the FP32 form).
+ * Runs independent FMA chains on every SM of `device` -- scalar FFMA when
+ * packed == 0, the two-lane fma.rn.f32x2 otherwise -- and writes the measured
+ * throughput in TFLOP/s (2 flops per FMA) to *tflops.  Not part of the filter:
+ * it allocates and frees a small result buffer and synchronises the device. */
+fbf_status fbf_measure_fp32_peak(int device, int packed, double *tflops);
+
+/* Static description of a status code. */
+const char *fbf_status_string(fbf_status s);
+
+/* Library version, major * 10000 + minor * 100 + patch. */
+int fbf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FBF_H */

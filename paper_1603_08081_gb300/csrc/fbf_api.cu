@@ -1,0 +1,88 @@
+// C-ABI entry points for the device filter: argument validation, packing of
+// the per-launch constants, and dispatch to the kernel forms.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+
+#include "fbf_internal.h"
+
+// Device-side error word of the library.  Kernels that wait on a barrier or a
+// flag give up after a bounded number of polls and OR a code in here.
+__device__ unsigned int g_fbf_device_error = 0;
+
+namespace fbf {
+
+fbf_status pack_filter_args(const fbf_params *p, const void *d_in, fbf_dtype dtype, int H, int Wd,
+                            size_t in_pitch, float *d_out, size_t out_pitch, FilterArgs *a) {
+  if (!p || !p->coeffs || !a) return FBF_ERR_INVALID_ARGUMENT;
+  if (H < 0 || Wd < 0) return FBF_ERR_INVALID_ARGUMENT;
+  if (dtype != FBF_U8 && dtype != FBF_F32) return FBF_ERR_INVALID_ARGUMENT;
+  if (p->spatial != FBF_SPATIAL_GAUSSIAN && p->spatial != FBF_SPATIAL_BOX) return FBF_ERR_INVALID_ARGUMENT;
+  if (p->border != FBF_BORDER_REFLECT && p->border != FBF_BORDER_TRUNCATE) return FBF_ERR_INVALID_ARGUMENT;
+  if (p->spatial == FBF_SPATIAL_GAUSSIAN && !(p->sigma_s > 0.0 && std::isfinite(p->sigma_s)))
+    return FBF_ERR_INVALID_ARGUMENT;
+  if (p->spatial == FBF_SPATIAL_BOX && p->W <= 0) return FBF_ERR_INVALID_ARGUMENT;
+  const int W = resolve_window(p->spatial, p->sigma_s, p->W);
+  if (W < 0) return FBF_ERR_INVALID_ARGUMENT;
+  if (W > FBF_WMAX) return FBF_ERR_RANGE;
+  const fbf_coeffs *c = p->coeffs;
+  if (c->K < 1) return FBF_ERR_INVALID_ARGUMENT;
+  if (c->K > FBF_KMAX) return FBF_ERR_RANGE;
+  if (!(c->T > 0.0) || !std::isfinite(c->T)) return FBF_ERR_INVALID_ARGUMENT;
+  const size_t esz = dtype == FBF_U8 ? 1 : 4;
+  if (H > 0 && Wd > 0) {
+    if (!d_in || !d_out) return FBF_ERR_INVALID_ARGUMENT;
+    if (in_pitch < (size_t)Wd * esz || out_pitch < (size_t)Wd * sizeof(float)) return FBF_ERR_INVALID_ARGUMENT;
+    if (out_pitch % sizeof(float) != 0) return FBF_ERR_INVALID_ARGUMENT;
+    if (dtype == FBF_F32 && in_pitch % sizeof(float) != 0) return FBF_ERR_INVALID_ARGUMENT;
+    if ((size_t)H * out_pitch > ((size_t)1 << 62)) return FBF_ERR_INVALID_ARGUMENT;
+  }
+  if (dtype == FBF_U8) {
+    // u8 phases are reduced exactly in integers: T must be an integer.
+    if (c->T != std::floor(c->T) || c->T > 32767.0) return FBF_ERR_UNSUPPORTED;
+  }
+  std::memset(a, 0, sizeof(*a));
+  a->in = d_in;
+  a->in_pitch = in_pitch;
+  a->out = d_out;
+  a->out_pitch = out_pitch;
+  a->H = H;
+  a->Wd = Wd;
+  a->W = W;
+  a->K = c->K;
+  a->T = (float)c->T;
+  a->twoT = dtype == FBF_U8 ? 2 * (int)c->T : 0;
+  a->border = (int)p->border;
+  spatial_weights(p->spatial, p->sigma_s, W, a->w);
+  for (int k = 0; k < c->K; ++k) a->d[k] = (float)c->d[k];
+  return FBF_OK;
+}
+
+}  // namespace fbf
+
+using namespace fbf;
+
+extern "C" fbf_status fbf_filter(const fbf_params *p, const void *d_in, fbf_dtype dtype, int H, int Wd,
+                                 size_t in_pitch, float *d_out, size_t out_pitch, cudaStream_t stream) {
+  FilterArgs a;
+  fbf_status st = pack_filter_args(p, d_in, dtype, H, Wd, in_pitch, d_out, out_pitch, &a);
+  if (st != FBF_OK) return st;
+  if (H == 0 || Wd == 0) return FBF_OK;
+  const fbf_form form = p->form;
+  if (form != FBF_FORM_AUTO && form != FBF_FORM_FP32 && form != FBF_FORM_TC_FP16 && form != FBF_FORM_TC_BF16)
+    return FBF_ERR_INVALID_ARGUMENT;
+  if (dtype != FBF_U8) return FBF_ERR_UNSUPPORTED;
+  if (form == FBF_FORM_TC_FP16 || form == FBF_FORM_TC_BF16) return FBF_ERR_UNSUPPORTED;
+  return launch_fp32_u8(a, stream);
+}
+
+extern "C" fbf_status fbf_device_error(unsigned int *code) {
+  if (!code) return FBF_ERR_INVALID_ARGUMENT;
+  if (cudaDeviceSynchronize() != cudaSuccess) return FBF_ERR_CUDA;
+  unsigned int v = 0, zero = 0;
+  if (cudaMemcpyFromSymbol(&v, g_fbf_device_error, sizeof(v)) != cudaSuccess) return FBF_ERR_CUDA;
+  if (cudaMemcpyToSymbol(g_fbf_device_error, &zero, sizeof(zero)) != cudaSuccess) return FBF_ERR_CUDA;
+  *code = v;
+  return FBF_OK;
+}

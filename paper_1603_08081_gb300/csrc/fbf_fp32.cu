@@ -1,0 +1,282 @@
+// Fused FP32 shiftable bilateral filter for uint8 images (Algorithm 1, all K
+// terms in one kernel).
+//
+// One CTA owns an output tile of BX x BY pixels.  It stages the tile plus a W
+// halo on every side as 16-bit LUT indices in shared memory, stored transposed
+// (column-major) so that both 1-D passes read conflict-free, and then runs,
+// for each harmonic n = 0..K-1:
+//
+//   modulate   channels (cos, sin, f cos, f sin)(n omega f) are gathered from a
+//              per-harmonic table indexed by the pixel value (u8 input, integer
+//              T: the phase n*f mod 2T is exact in integers).  The table holds 8
+//              interleaved copies so a quarter-warp's 16-byte gathers never hit
+//              the same bank group, whatever the pixel values;
+//   row pass   1-D FIR with the 2W+1 taps along x over the BY + 2W halo rows
+//              (lane = row, each thread slides along x producing 8 outputs with
+//              an 8-register rotating window), results to a shared row buffer;
+//   col pass   1-D FIR along y (lane = column, 8 outputs per thread);
+//   demod      P += d_n (cos th_i Fr + sin th_i Fi),  Q += d_n (cos th_i Gr +
+//              sin th_i Gi) in registers (the real part of c_n e^{-in w f} Fbar_n
+//              + c_{-n} e^{in w f} Fbar_{-n}, c_{+-n} = d_n / 2, Sec. III).
+//
+// After the last harmonic the tile writes fhat = P / Q once.  Out-of-image
+// halo pixels hold the reflected value (REFLECT) or a sentinel whose channels
+// are all zero (TRUNCATE).
+#include <cuda_runtime.h>
+
+#include "fbf_internal.h"
+
+namespace fbf {
+namespace {
+
+constexpr int kCopies = 8;           // interleaved LUT copies (one per lane of a quarter-warp)
+constexpr int kLutEntries = 257;     // pixel values 0..255 plus the zero sentinel
+constexpr int kSentinel = 256;
+constexpr int kRun = 8;              // outputs per thread in each 1-D pass
+
+struct Layout {
+  int HY, NG, HYP, HX, HXA, PT, PR;
+  size_t row_off, tile_off, bytes;
+};
+
+// Shared-memory layout for a BX x BY tile with half window W:
+//   [LUT buffer 0][LUT buffer 1]   float4[257 * 8] each
+//   [row buffer]                   float4[(HYP + 1) * PR], PR = BX + 1 (odd)
+//   [tile]                         u16[HXA * PT], column-major, PT/2 odd
+__host__ __device__ inline Layout make_layout(int BX, int BY, int W) {
+  Layout L;
+  L.HY = BY + 2 * W;
+  L.NG = (L.HY + 31) / 32;
+  L.HYP = L.NG * 32;
+  L.HX = BX + 2 * W;
+  L.HXA = L.HX + kRun;
+  L.PT = L.HYP + 2;
+  L.PR = BX + 1;
+  const size_t lut = 2ull * kLutEntries * kCopies * sizeof(float4);
+  L.row_off = lut;
+  L.tile_off = L.row_off + (size_t)(L.HYP + 1) * L.PR * sizeof(float4);
+  const size_t tile = (size_t)L.HXA * L.PT * sizeof(unsigned short);
+  L.bytes = L.tile_off + ((tile + 127) & ~(size_t)127);
+  return L;
+}
+
+__device__ __forceinline__ int reflect_index(int i, int n) {
+  const int p = 2 * n;
+  int m = i % p;
+  if (m < 0) m += p;
+  return m < n ? m : p - 1 - m;
+}
+
+__device__ __forceinline__ void fma4(float4 &acc, float w, const float4 &v) {
+  acc.x = fmaf(w, v.x, acc.x);
+  acc.y = fmaf(w, v.y, acc.y);
+  acc.z = fmaf(w, v.z, acc.z);
+  acc.w = fmaf(w, v.w, acc.w);
+}
+
+// Table of (cos, sin, v cos, v sin)(n omega v) for v = 0..255, 8 copies each;
+// lane l of a quarter-warp reads copy l.  Copies are written rotated so the 8
+// stores of one value land in 8 different bank groups.
+__device__ __forceinline__ void build_lut(float4 *L, int n, int twoT, float T, int tid, int nt) {
+  for (int v = tid; v < 256; v += nt) {
+    const int m = (n * v) % twoT;  // exact phase index: n*omega*v = pi * m / T (mod 2 pi)
+    float sn, cs;
+    sincospif((float)m / T, &sn, &cs);
+    const float fv = (float)v;
+    const float4 e = make_float4(cs, sn, fv * cs, fv * sn);
+#pragma unroll
+    for (int j = 0; j < kCopies; ++j) L[v * kCopies + ((j + v) & (kCopies - 1))] = e;
+  }
+}
+
+// One 1-D pass of kRun outputs: acc[o] = sum_k w[k] * src(o + k), where src(p)
+// is produced by `load(p)`.  The kRun-register window v holds src positions
+// p == j (mod kRun); after tap k the position k is dead and is replaced by
+// k + kRun.  Taps run in chunks of kRun (static register names) plus a tail
+// with warp-uniform guards.  The last load reads position taps - 1 + kRun,
+// which callers keep inside their buffers.
+template <class Load>
+__device__ __forceinline__ void fir_run(const float *w, int taps, Load load, float4 (&acc)[kRun]) {
+  float4 v[kRun];
+#pragma unroll
+  for (int j = 0; j < kRun; ++j) {
+    v[j] = load(j);
+    acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+  int k = 0;
+  for (; k + kRun <= taps; k += kRun) {
+#pragma unroll
+    for (int j = 0; j < kRun; ++j) {
+      const float wk = w[k + j];
+#pragma unroll
+      for (int o = 0; o < kRun; ++o) fma4(acc[o], wk, v[(o + j) & (kRun - 1)]);
+      v[j] = load(k + j + kRun);
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < kRun; ++j) {
+    if (k + j < taps) {
+      const float wk = w[k + j];
+#pragma unroll
+      for (int o = 0; o < kRun; ++o) fma4(acc[o], wk, v[(o + j) & (kRun - 1)]);
+      v[j] = load(k + j + kRun);
+    }
+  }
+}
+
+template <int BX, int BY, int NT>
+__global__ void __launch_bounds__(NT, 1) fbf_fp32_u8_kernel(const __grid_constant__ FilterArgs a) {
+  static_assert(BX % 32 == 0 && BY % kRun == 0 && NT % 32 == 0, "tile shape");
+  constexpr int NW = NT / 32;
+  constexpr int NXR = BX / kRun;       // row-pass x runs
+  constexpr int NCG = BX / 32;         // column-pass column groups
+  constexpr int NYR = BY / kRun;       // column-pass y runs
+  constexpr int UPW = NCG * NYR / NW;  // column-pass units per warp
+  static_assert(NCG * NYR % NW == 0, "column units must divide evenly among warps");
+
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int W = a.W, taps = 2 * W + 1;
+  const Layout Ly = make_layout(BX, BY, W);
+  float4 *lut = reinterpret_cast<float4 *>(smem);
+  float4 *rowbuf = reinterpret_cast<float4 *>(smem + Ly.row_off);
+  unsigned short *tileT = reinterpret_cast<unsigned short *>(smem + Ly.tile_off);
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, cp = lane & (kCopies - 1);
+  const int tile_y = blockIdx.x / a.tiles_x, tile_x = blockIdx.x - tile_y * a.tiles_x;
+  const int ty0 = tile_y * BY, tx0 = tile_x * BX;
+  const int H = a.H, Wd = a.Wd;
+
+  // Sentinel rows of both LUT buffers: zero channels (TRUNCATE outside the image).
+  if (tid < 2 * kCopies) {
+    lut[(tid >> 3) * kLutEntries * kCopies + kSentinel * kCopies + (tid & 7)] =
+        make_float4(0.f, 0.f, 0.f, 0.f);
+  }
+
+  // Stage the halo tile, transposed: tileT[ex * PT + ey].  Eight independent
+  // loads per thread are issued before their stores.
+  {
+    const unsigned char *in = static_cast<const unsigned char *>(a.in);
+    const size_t pitch = a.in_pitch;
+    const int total = Ly.HYP * Ly.HXA;
+    for (int base = tid; base < total; base += NT * 8) {
+      unsigned short vals[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int idx = base + u * NT;
+        unsigned short v = kSentinel;
+        if (idx < total) {
+          const int ey = idx / Ly.HXA, ex = idx - ey * Ly.HXA;
+          if (ey < Ly.HY && ex < Ly.HX) {
+            int iy = ty0 + ey - W, ix = tx0 + ex - W;
+            bool inside;
+            if (a.border == FBF_BORDER_REFLECT) {
+              iy = reflect_index(iy, H);
+              ix = reflect_index(ix, Wd);
+              inside = true;
+            } else {
+              inside = iy >= 0 && iy < H && ix >= 0 && ix < Wd;
+            }
+            if (inside) v = __ldg(in + (size_t)iy * pitch + ix);
+          }
+        }
+        vals[u] = v;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int idx = base + u * NT;
+        if (idx < total) {
+          const int ey = idx / Ly.HXA, ex = idx - ey * Ly.HXA;
+          tileT[ex * Ly.PT + ey] = vals[u];
+        }
+      }
+    }
+  }
+  build_lut(lut, 0, a.twoT, a.T, tid, NT);
+  __syncthreads();
+
+  float P[UPW][kRun], Q[UPW][kRun];
+#pragma unroll
+  for (int q = 0; q < UPW; ++q)
+#pragma unroll
+    for (int o = 0; o < kRun; ++o) P[q][o] = Q[q][o] = 0.f;
+
+  for (int n = 0; n < a.K; ++n) {
+    const float4 *L = lut + (n & 1) * kLutEntries * kCopies;
+
+    // Row pass over the BY + 2W halo rows (rows >= HY are padding lanes).
+    for (int u = warp; u < Ly.NG * NXR; u += NW) {
+      const int g = u / NXR, xr = u - g * NXR;
+      const int ey = g * 32 + lane, ox0 = xr * kRun;
+      const unsigned short *tp = tileT + ox0 * Ly.PT + ey;
+      const int PT = Ly.PT;
+      float4 acc[kRun];
+      fir_run(a.w, taps, [&](int p) { return L[tp[p * PT] * kCopies + cp]; }, acc);
+      float4 *rb = rowbuf + ey * Ly.PR + ox0;
+#pragma unroll
+      for (int o = 0; o < kRun; ++o) rb[o] = acc[o];
+    }
+    __syncthreads();
+
+    if (n + 1 < a.K) build_lut(lut + ((n + 1) & 1) * kLutEntries * kCopies, n + 1, a.twoT, a.T, tid, NT);
+
+    // Column pass + demodulation into P, Q.
+    const float dn = a.d[n];
+#pragma unroll
+    for (int q = 0; q < UPW; ++q) {
+      const int u = warp + q * NW;
+      const int cg = u % NCG, yr = u / NCG;
+      const int ox = cg * 32 + lane, oy0 = yr * kRun;
+      const float4 *cpnt = rowbuf + oy0 * Ly.PR + ox;
+      const int PR = Ly.PR;
+      float4 acc[kRun];
+      fir_run(a.w, taps, [&](int p) { return cpnt[p * PR]; }, acc);
+      const unsigned short *cen = tileT + (ox + W) * Ly.PT + oy0 + W;
+#pragma unroll
+      for (int o = 0; o < kRun; ++o) {
+        const float4 c = L[cen[o] * kCopies + cp];
+        P[q][o] = fmaf(dn, fmaf(c.x, acc[o].z, c.y * acc[o].w), P[q][o]);
+        Q[q][o] = fmaf(dn, fmaf(c.x, acc[o].x, c.y * acc[o].y), Q[q][o]);
+      }
+    }
+    __syncthreads();
+  }
+
+  // fhat = P / Q, written once (IEEE division, no clamp).
+  float *out = a.out;
+#pragma unroll
+  for (int q = 0; q < UPW; ++q) {
+    const int u = warp + q * NW;
+    const int cg = u % NCG, yr = u / NCG;
+    const int ix = tx0 + cg * 32 + lane;
+#pragma unroll
+    for (int o = 0; o < kRun; ++o) {
+      const int iy = ty0 + yr * kRun + o;
+      if (iy < H && ix < Wd)
+        *reinterpret_cast<float *>(reinterpret_cast<char *>(out) + (size_t)iy * a.out_pitch +
+                                   (size_t)ix * sizeof(float)) = P[q][o] / Q[q][o];
+    }
+  }
+}
+
+template <int BX, int BY, int NT>
+fbf_status launch_cfg(const FilterArgs &a0, cudaStream_t s) {
+  FilterArgs a = a0;
+  const Layout Ly = make_layout(BX, BY, a.W);
+  a.tiles_x = (a.Wd + BX - 1) / BX;
+  const int tiles_y = (a.H + BY - 1) / BY;
+  a.ntiles = a.tiles_x * tiles_y;
+  auto kern = fbf_fp32_u8_kernel<BX, BY, NT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Ly.bytes);
+  if (e != cudaSuccess) return FBF_ERR_CUDA;
+  kern<<<a.ntiles, NT, Ly.bytes, s>>>(a);
+  return cuda_status(cudaGetLastError());
+}
+
+}  // namespace
+
+fbf_status launch_fp32_u8(const FilterArgs &a, cudaStream_t s) {
+  if (a.W <= 16) return launch_cfg<64, 64, 256>(a, s);
+  return launch_cfg<32, 128, 256>(a, s);
+}
+
+}  // namespace fbf

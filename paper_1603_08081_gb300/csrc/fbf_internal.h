@@ -1,0 +1,51 @@
+// Internal declarations shared by the library's translation units (never
+// installed, never seen by callers of fbf.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include "fbf.h"
+
+#ifndef M_PI
+#define M_PI 3.14159265358979323846
+#endif
+
+namespace fbf {
+
+constexpr int TAPS_MAX = 2 * FBF_WMAX + 1;
+
+// Host helpers (fbf_fit.cpp).
+int resolve_window(fbf_spatial_kernel spatial, double sigma_s, int W);
+void spatial_weights(fbf_spatial_kernel spatial, double sigma_s, int W, float *w1);
+
+// Everything one filter launch needs, passed by value as a __grid_constant__
+// kernel parameter: the taps and coefficients live in the parameter bank, so a
+// call needs no device allocation and concurrent calls cannot race on them.
+struct FilterArgs {
+  const void *in;
+  size_t in_pitch;  // bytes
+  float *out;
+  size_t out_pitch;  // bytes
+  int H, Wd;         // image rows, columns
+  int W;             // half window; taps = 2W + 1
+  int K;             // number of coefficients d_0..d_{K-1}
+  int twoT;          // 2T (integer T, u8 input)
+  float T;           // T as float
+  int border;        // fbf_border
+  int tiles_x;       // tiles per image row
+  int ntiles;        // tiles in the image
+  float w[TAPS_MAX];  // normalised 1-D spatial taps w1[j + W]
+  float d[FBF_KMAX];  // cosine coefficients, eq. (6)
+};
+
+// Common host-side validation + argument packing for the single-image forms.
+fbf_status pack_filter_args(const fbf_params *p, const void *d_in, fbf_dtype dtype, int H,
+                            int Wd, size_t in_pitch, float *d_out, size_t out_pitch,
+                            FilterArgs *a);
+
+fbf_status launch_fp32_u8(const FilterArgs &a, cudaStream_t s);
+
+inline fbf_status cuda_status(cudaError_t e) { return e == cudaSuccess ? FBF_OK : FBF_ERR_CUDA; }
+
+}  // namespace fbf

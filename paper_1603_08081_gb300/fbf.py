@@ -1,0 +1,204 @@
+"""Thin ctypes binding over ``libfbf.so`` (the C ABI declared in ``include/fbf.h``).
+
+Argument marshalling only: every step of the filter runs in the library's CUDA
+kernels or its host FP64 fit.  PyTorch supplies device memory and the current
+stream.  Importing this module loads the library and raises if it has not been
+built; there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+from . import build as _build
+
+KMAX = 256
+WMAX = 32
+
+FBF_OK, FBF_ERR_INVALID_ARGUMENT, FBF_ERR_NOT_CONVERGED, FBF_ERR_RANGE = 0, 1, 2, 3
+FBF_ERR_UNSUPPORTED, FBF_ERR_CUDA, FBF_ERR_TIMEOUT = 4, 5, 6
+FBF_RANGE_GAUSSIAN, FBF_RANGE_EXPONENTIAL = 0, 1
+FBF_SPATIAL_GAUSSIAN, FBF_SPATIAL_BOX = 0, 1
+FBF_BORDER_REFLECT, FBF_BORDER_TRUNCATE = 0, 1
+FBF_U8, FBF_F32 = 0, 1
+FBF_FORM_AUTO, FBF_FORM_FP32, FBF_FORM_TC_FP16, FBF_FORM_TC_BF16 = 0, 1, 2, 3
+
+_NAMES = {"gaussian": 0, "exponential": 1, "box": 1, "reflect": 0, "truncate": 1,
+          "auto": 0, "fp32": 1, "tc_fp16": 2, "tc_bf16": 3}
+
+
+class fbf_coeffs(C.Structure):
+    _fields_ = [("K", C.c_int), ("levels", C.c_int), ("T", C.c_double), ("omega", C.c_double),
+                ("resid_l2", C.c_double), ("resid_linf", C.c_double), ("d", C.c_double * KMAX)]
+
+    @property
+    def coefficients(self):
+        return [self.d[k] for k in range(self.K)]
+
+    def __repr__(self):
+        return "fbf_coeffs(K=%d, T=%g, resid_l2=%.3g, resid_linf=%.3g)" % (
+            self.K, self.T, self.resid_l2, self.resid_linf)
+
+
+class fbf_params(C.Structure):
+    _fields_ = [("spatial", C.c_int), ("sigma_s", C.c_double), ("W", C.c_int), ("border", C.c_int),
+                ("form", C.c_int), ("coeffs", C.POINTER(fbf_coeffs))]
+
+
+class FbfError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__("%s%s" % (what + ": " if what else "", fbf_status_string(status)))
+
+
+def _load():
+    path = _build.lib_path()
+    if not os.path.exists(path):
+        raise ImportError("libfbf.so is not built (%s); run `python -m paper_1603_08081_gb300.build`"
+                          " or __graft_entry__.build()" % path)
+    lib = C.CDLL(path)
+    i, d, p, sz = C.c_int, C.c_double, C.c_void_p, C.c_size_t
+    lib.fbf_fit_coeffs.argtypes = [i, d, d, d, i, i, C.POINTER(fbf_coeffs)]
+    lib.fbf_fit_coeffs.restype = i
+    lib.fbf_filter.argtypes = [C.POINTER(fbf_params), p, i, i, i, sz, p, sz, p]
+    lib.fbf_filter.restype = i
+    lib.fbf_resolve_window.argtypes = [C.POINTER(fbf_params)]
+    lib.fbf_resolve_window.restype = i
+    lib.fbf_device_error.argtypes = [C.POINTER(C.c_uint)]
+    lib.fbf_device_error.restype = i
+    lib.fbf_measure_fp32_peak.argtypes = [i, i, C.POINTER(C.c_double)]
+    lib.fbf_measure_fp32_peak.restype = i
+    lib.fbf_status_string.argtypes = [i]
+    lib.fbf_status_string.restype = C.c_char_p
+    lib.fbf_version.argtypes = []
+    lib.fbf_version.restype = i
+    return lib
+
+
+lib = _load()
+
+
+def _enum(v) -> int:
+    return _NAMES[v.lower()] if isinstance(v, str) else int(v)
+
+
+def fbf_status_string(status: int) -> str:
+    return lib.fbf_status_string(int(status)).decode()
+
+
+def fbf_version() -> int:
+    return int(lib.fbf_version())
+
+
+def fbf_fit_coeffs(kernel="gaussian", sigma_r: float = 30.0, T: float = 255.0, eps: float = 1e-3,
+                   K_fixed: int = 0, levels: int = 0, allow_not_converged: bool = False) -> fbf_coeffs:
+    """Algorithm 2 on the host in FP64 (see fbf.h)."""
+    out = fbf_coeffs()
+    st = lib.fbf_fit_coeffs(_enum(kernel), float(sigma_r), float(T), float(eps), int(K_fixed),
+                            int(levels), C.byref(out))
+    if st != FBF_OK and not (st == FBF_ERR_NOT_CONVERGED and allow_not_converged):
+        raise FbfError(st, "fbf_fit_coeffs")
+    return out
+
+
+def make_params(coeffs: fbf_coeffs, sigma_s: float = 3.0, W: int = 0, spatial="gaussian",
+                border="reflect", form="fp32") -> fbf_params:
+    p = fbf_params()
+    p.spatial = _enum(spatial)
+    p.sigma_s = float(sigma_s)
+    p.W = int(W)
+    p.border = _enum(border)
+    p.form = _enum(form)
+    p.coeffs = C.pointer(coeffs)
+    p._keep = coeffs  # keep the struct alive with the params
+    return p
+
+
+def fbf_resolve_window(params: fbf_params) -> int:
+    return int(lib.fbf_resolve_window(C.byref(params)))
+
+
+def _stream_handle(stream):
+    import torch
+
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(int(stream.cuda_stream))
+
+
+def fbf_filter(params: fbf_params, x, out=None, stream=None):
+    """Filter a 2-D CUDA tensor (uint8 or float32).  Returns the float32 output.
+
+    Rows may be padded (any row stride); columns must be contiguous.
+    """
+    import torch
+
+    if x.dim() != 2 or not x.is_cuda:
+        raise ValueError("fbf_filter expects a 2-D CUDA tensor")
+    if x.dtype == torch.uint8:
+        dt, esz = FBF_U8, 1
+    elif x.dtype == torch.float32:
+        dt, esz = FBF_F32, 4
+    else:
+        raise TypeError("fbf_filter: dtype must be uint8 or float32")
+    if x.stride(1) != 1:
+        x = x.contiguous()
+    H, Wd = x.shape
+    if out is None:
+        out = torch.empty((H, Wd), dtype=torch.float32, device=x.device)
+    if out.dtype != torch.float32 or out.dim() != 2 or out.shape != x.shape or out.stride(1) != 1:
+        raise ValueError("fbf_filter: out must be float32 (H, W) with contiguous rows")
+    st = lib.fbf_filter(C.byref(params), C.c_void_p(x.data_ptr()), dt, H, Wd,
+                        x.stride(0) * esz, C.c_void_p(out.data_ptr()), out.stride(0) * 4,
+                        _stream_handle(stream))
+    if st != FBF_OK:
+        raise FbfError(st, "fbf_filter")
+    return out
+
+
+def fbf_device_error() -> int:
+    v = C.c_uint(0)
+    st = lib.fbf_device_error(C.byref(v))
+    if st != FBF_OK:
+        raise FbfError(st, "fbf_device_error")
+    return int(v.value)
+
+
+def fbf_measure_fp32_peak(device: int = 0, packed=None) -> float:
+    """Measured FP32 FMA throughput in TFLOP/s (max of scalar and packed when
+    packed is None)."""
+    vals = []
+    for pk in ((0, 1) if packed is None else (int(bool(packed)),)):
+        v = C.c_double(0.0)
+        st = lib.fbf_measure_fp32_peak(int(device), pk, C.byref(v))
+        if st != FBF_OK:
+            raise FbfError(st, "fbf_measure_fp32_peak")
+        vals.append(v.value)
+    return max(vals)
+
+
+def bilateral_filter(x, sigma_s: float = 3.0, sigma_r: float = 30.0, eps: float = 1e-3,
+                     T: float | None = None, kernel="gaussian", K: int = 0, W: int = 0,
+                     spatial="gaussian", border="reflect", form="fp32", levels: int = 0):
+    """Convenience: fit the coefficients (host) and filter ``x``.
+
+    ``x`` may be a CUDA tensor, or a CPU tensor (pinned for speed), in which case
+    it is copied to the current device and the result is copied back.
+    """
+    import torch
+
+    if T is None:
+        T = 255.0 if x.dtype == torch.uint8 else 1.0
+    if levels == 0 and T != math.floor(T):
+        levels = 256
+    c = fbf_fit_coeffs(kernel, sigma_r, T, eps, K, levels)
+    p = make_params(c, sigma_s, W, spatial, border, form)
+    if x.is_cuda:
+        return fbf_filter(p, x)
+    xd = x.to("cuda", non_blocking=True)
+    y = fbf_filter(p, xd)
+    host = torch.empty(y.shape, dtype=y.dtype, pin_memory=True)
+    host.copy_(y, non_blocking=True)
+    torch.cuda.current_stream().synchronize()
+    return host
