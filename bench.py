@@ -71,7 +71,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self._t = threading.Thread(target=self._read, daemon=True)
             self._t.start()
@@ -365,11 +365,11 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--form", default="fp32", choices=["fp32", "auto", "tc_fp16", "tc_bf16"])
-    ap.add_argument("--slab-rows", type=int, default=24, help="rows of the CPU-baseline sample")
+    ap.add_argument("--slab-rows", type=int, default=384, help="rows of the CPU-baseline sample")
     ap.add_argument("--ref-rows", type=int, default=8, help="rows per setting per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", type=int, default=None,

@@ -55,6 +55,11 @@ fbf_status pack_filter_args(const fbf_params *p, const void *d_in, fbf_dtype dty
   a->twoT = dtype == FBF_U8 ? 2 * (int)c->T : 0;
   a->border = (int)p->border;
   spatial_weights(p->spatial, p->sigma_s, W, a->w);
+  for (int j = 0; j < 2 * W + 1; ++j) {
+    unsigned int b;
+    std::memcpy(&b, &a->w[j], sizeof(b));
+    a->w2[j] = (unsigned long long)b | ((unsigned long long)b << 32);
+  }
   for (int k = 0; k < c->K; ++k) a->d[k] = (float)c->d[k];
   return FBF_OK;
 }

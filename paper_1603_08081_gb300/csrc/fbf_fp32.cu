@@ -14,6 +14,9 @@
 //   row pass   1-D FIR with the 2W+1 taps along x over the BY + 2W halo rows
 //              (lane = row, each thread slides along x producing 8 outputs with
 //              an 8-register rotating window), results to a shared row buffer;
+//              the four channels travel as two packed f32x2 pairs, so every
+//              tap is two fma.rn.f32x2 per output (half the issue slots of
+//              scalar FFMA at the same FMA-pipe rate);
 //   col pass   1-D FIR along y (lane = column, 8 outputs per thread);
 //   demod      P += d_n (cos th_i Fr + sin th_i Fi),  Q += d_n (cos th_i Gr +
 //              sin th_i Gi) in registers (the real part of c_n e^{-in w f} Fbar_n
@@ -40,10 +43,10 @@ struct Layout {
 };
 
 // Shared-memory layout for a BX x BY tile with half window W:
-//   [LUT buffer 0][LUT buffer 1]   float4[257 * 8] each
+//   [LUT buffer 0][LUT buffer 1]   float4[257 * 8] each (one buffer when nbuf == 1)
 //   [row buffer]                   float4[(HYP + 1) * PR], PR = BX + 1 (odd)
 //   [tile]                         u16[HXA * PT], column-major, PT/2 odd
-__host__ __device__ inline Layout make_layout(int BX, int BY, int W) {
+__host__ __device__ inline Layout make_layout(int BX, int BY, int W, int nbuf) {
   Layout L;
   L.HY = BY + 2 * W;
   L.NG = (L.HY + 31) / 32;
@@ -52,7 +55,7 @@ __host__ __device__ inline Layout make_layout(int BX, int BY, int W) {
   L.HXA = L.HX + kRun;
   L.PT = L.HYP + 2;
   L.PR = BX + 1;
-  const size_t lut = 2ull * kLutEntries * kCopies * sizeof(float4);
+  const size_t lut = (size_t)nbuf * kLutEntries * kCopies * sizeof(float4);
   L.row_off = lut;
   L.tile_off = L.row_off + (size_t)(L.HYP + 1) * L.PR * sizeof(float4);
   const size_t tile = (size_t)L.HXA * L.PT * sizeof(unsigned short);
@@ -67,12 +70,20 @@ __device__ __forceinline__ int reflect_index(int i, int n) {
   return m < n ? m : p - 1 - m;
 }
 
-__device__ __forceinline__ void fma4(float4 &acc, float w, const float4 &v) {
-  acc.x = fmaf(w, v.x, acc.x);
-  acc.y = fmaf(w, v.y, acc.y);
-  acc.z = fmaf(w, v.z, acc.z);
-  acc.w = fmaf(w, v.w, acc.w);
+typedef unsigned long long u64;
+
+// Four channels of one pixel as two f32x2 pairs: a = (cos, sin), b = (f cos, f sin).
+struct Quad {
+  u64 a, b;
+};
+
+// d = w * v + d on both halves of an f32x2 pair.
+__device__ __forceinline__ void fma2(u64 &d, u64 w, u64 v) {
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(w), "l"(v));
 }
+
+__device__ __forceinline__ float lo_f(u64 x) { return __uint_as_float((unsigned)x); }
+__device__ __forceinline__ float hi_f(u64 x) { return __uint_as_float((unsigned)(x >> 32)); }
 
 // Table of (cos, sin, v cos, v sin)(n omega v) for v = 0..255, 8 copies each;
 // lane l of a quarter-warp reads copy l.  Copies are written rotated so the 8
@@ -94,51 +105,60 @@ __device__ __forceinline__ void build_lut(float4 *L, int n, int twoT, float T, i
 // p == j (mod kRun); after tap k the position k is dead and is replaced by
 // k + kRun.  Taps run in chunks of kRun (static register names) plus a tail
 // with warp-uniform guards.  The last load reads position taps - 1 + kRun,
-// which callers keep inside their buffers.
+// which callers keep inside their buffers.  w2[k] holds tap k in both halves.
 template <class Load>
-__device__ __forceinline__ void fir_run(const float *w, int taps, Load load, float4 (&acc)[kRun]) {
-  float4 v[kRun];
+__device__ __forceinline__ void fir_run(const u64 *w2, int taps, Load load, Quad (&acc)[kRun]) {
+  Quad v[kRun];
 #pragma unroll
   for (int j = 0; j < kRun; ++j) {
     v[j] = load(j);
-    acc[j] = make_float4(0.f, 0.f, 0.f, 0.f);
+    acc[j].a = 0ull;
+    acc[j].b = 0ull;
   }
   int k = 0;
   for (; k + kRun <= taps; k += kRun) {
 #pragma unroll
     for (int j = 0; j < kRun; ++j) {
-      const float wk = w[k + j];
+      const u64 wk = w2[k + j];
 #pragma unroll
-      for (int o = 0; o < kRun; ++o) fma4(acc[o], wk, v[(o + j) & (kRun - 1)]);
+      for (int o = 0; o < kRun; ++o) {
+        fma2(acc[o].a, wk, v[(o + j) & (kRun - 1)].a);
+        fma2(acc[o].b, wk, v[(o + j) & (kRun - 1)].b);
+      }
       v[j] = load(k + j + kRun);
     }
   }
 #pragma unroll
   for (int j = 0; j < kRun; ++j) {
     if (k + j < taps) {
-      const float wk = w[k + j];
+      const u64 wk = w2[k + j];
 #pragma unroll
-      for (int o = 0; o < kRun; ++o) fma4(acc[o], wk, v[(o + j) & (kRun - 1)]);
+      for (int o = 0; o < kRun; ++o) {
+        fma2(acc[o].a, wk, v[(o + j) & (kRun - 1)].a);
+        fma2(acc[o].b, wk, v[(o + j) & (kRun - 1)].b);
+      }
       v[j] = load(k + j + kRun);
     }
   }
 }
 
-template <int BX, int BY, int NT>
+template <int BX, int BY, int NT, int NBUF>
 __global__ void __launch_bounds__(NT, 1) fbf_fp32_u8_kernel(const __grid_constant__ FilterArgs a) {
   static_assert(BX % 32 == 0 && BY % kRun == 0 && NT % 32 == 0, "tile shape");
+  static_assert(NBUF == 1 || NBUF == 2, "one or two table buffers");
   constexpr int NW = NT / 32;
   constexpr int NXR = BX / kRun;       // row-pass x runs
   constexpr int NCG = BX / 32;         // column-pass column groups
   constexpr int NYR = BY / kRun;       // column-pass y runs
   constexpr int UPW = NCG * NYR / NW;  // column-pass units per warp
   static_assert(NCG * NYR % NW == 0, "column units must divide evenly among warps");
+  constexpr int kLutStride = kLutEntries * kCopies;  // float4 per table buffer
 
   extern __shared__ __align__(128) unsigned char smem[];
   const int W = a.W, taps = 2 * W + 1;
-  const Layout Ly = make_layout(BX, BY, W);
+  const Layout Ly = make_layout(BX, BY, W, NBUF);
   float4 *lut = reinterpret_cast<float4 *>(smem);
-  float4 *rowbuf = reinterpret_cast<float4 *>(smem + Ly.row_off);
+  ulonglong2 *rowbuf = reinterpret_cast<ulonglong2 *>(smem + Ly.row_off);
   unsigned short *tileT = reinterpret_cast<unsigned short *>(smem + Ly.tile_off);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, cp = lane & (kCopies - 1);
@@ -146,9 +166,9 @@ __global__ void __launch_bounds__(NT, 1) fbf_fp32_u8_kernel(const __grid_constan
   const int ty0 = tile_y * BY, tx0 = tile_x * BX;
   const int H = a.H, Wd = a.Wd;
 
-  // Sentinel rows of both LUT buffers: zero channels (TRUNCATE outside the image).
-  if (tid < 2 * kCopies) {
-    lut[(tid >> 3) * kLutEntries * kCopies + kSentinel * kCopies + (tid & 7)] =
+  // Sentinel entry of every table buffer: zero channels (TRUNCATE outside the image).
+  if (tid < NBUF * kCopies) {
+    lut[(tid / kCopies) * kLutStride + kSentinel * kCopies + (tid % kCopies)] =
         make_float4(0.f, 0.f, 0.f, 0.f);
   }
 
@@ -201,7 +221,7 @@ __global__ void __launch_bounds__(NT, 1) fbf_fp32_u8_kernel(const __grid_constan
     for (int o = 0; o < kRun; ++o) P[q][o] = Q[q][o] = 0.f;
 
   for (int n = 0; n < a.K; ++n) {
-    const float4 *L = lut + (n & 1) * kLutEntries * kCopies;
+    const ulonglong2 *L = reinterpret_cast<const ulonglong2 *>(lut + (NBUF == 2 ? (n & 1) * kLutStride : 0));
 
     // Row pass over the BY + 2W halo rows (rows >= HY are padding lanes).
     for (int u = warp; u < Ly.NG * NXR; u += NW) {
@@ -209,15 +229,21 @@ __global__ void __launch_bounds__(NT, 1) fbf_fp32_u8_kernel(const __grid_constan
       const int ey = g * 32 + lane, ox0 = xr * kRun;
       const unsigned short *tp = tileT + ox0 * Ly.PT + ey;
       const int PT = Ly.PT;
-      float4 acc[kRun];
-      fir_run(a.w, taps, [&](int p) { return L[tp[p * PT] * kCopies + cp]; }, acc);
-      float4 *rb = rowbuf + ey * Ly.PR + ox0;
+      Quad acc[kRun];
+      fir_run(a.w2, taps,
+              [&](int p) {
+                const ulonglong2 e = L[tp[p * PT] * kCopies + cp];
+                return Quad{e.x, e.y};
+              },
+              acc);
+      ulonglong2 *rb = rowbuf + ey * Ly.PR + ox0;
 #pragma unroll
-      for (int o = 0; o < kRun; ++o) rb[o] = acc[o];
+      for (int o = 0; o < kRun; ++o) rb[o] = make_ulonglong2(acc[o].a, acc[o].b);
     }
     __syncthreads();
 
-    if (n + 1 < a.K) build_lut(lut + ((n + 1) & 1) * kLutEntries * kCopies, n + 1, a.twoT, a.T, tid, NT);
+    if (NBUF == 2 && n + 1 < a.K)
+      build_lut(lut + ((n + 1) & 1) * kLutStride, n + 1, a.twoT, a.T, tid, NT);
 
     // Column pass + demodulation into P, Q.
     const float dn = a.d[n];
@@ -226,19 +252,29 @@ __global__ void __launch_bounds__(NT, 1) fbf_fp32_u8_kernel(const __grid_constan
       const int u = warp + q * NW;
       const int cg = u % NCG, yr = u / NCG;
       const int ox = cg * 32 + lane, oy0 = yr * kRun;
-      const float4 *cpnt = rowbuf + oy0 * Ly.PR + ox;
+      const ulonglong2 *cpnt = rowbuf + oy0 * Ly.PR + ox;
       const int PR = Ly.PR;
-      float4 acc[kRun];
-      fir_run(a.w, taps, [&](int p) { return cpnt[p * PR]; }, acc);
+      Quad acc[kRun];
+      fir_run(a.w2, taps,
+              [&](int p) {
+                const ulonglong2 e = cpnt[p * PR];
+                return Quad{e.x, e.y};
+              },
+              acc);
       const unsigned short *cen = tileT + (ox + W) * Ly.PT + oy0 + W;
 #pragma unroll
       for (int o = 0; o < kRun; ++o) {
-        const float4 c = L[cen[o] * kCopies + cp];
-        P[q][o] = fmaf(dn, fmaf(c.x, acc[o].z, c.y * acc[o].w), P[q][o]);
-        Q[q][o] = fmaf(dn, fmaf(c.x, acc[o].x, c.y * acc[o].y), Q[q][o]);
+        const ulonglong2 c = L[cen[o] * kCopies + cp];
+        const float cs = lo_f(c.x), sn = hi_f(c.x);
+        P[q][o] = fmaf(dn, fmaf(cs, lo_f(acc[o].b), sn * hi_f(acc[o].b)), P[q][o]);
+        Q[q][o] = fmaf(dn, fmaf(cs, lo_f(acc[o].a), sn * hi_f(acc[o].a)), Q[q][o]);
       }
     }
     __syncthreads();
+    if (NBUF == 1 && n + 1 < a.K) {
+      build_lut(lut, n + 1, a.twoT, a.T, tid, NT);
+      __syncthreads();
+    }
   }
 
   // fhat = P / Q, written once (IEEE division, no clamp).
@@ -258,14 +294,14 @@ __global__ void __launch_bounds__(NT, 1) fbf_fp32_u8_kernel(const __grid_constan
   }
 }
 
-template <int BX, int BY, int NT>
+template <int BX, int BY, int NT, int NBUF>
 fbf_status launch_cfg(const FilterArgs &a0, cudaStream_t s) {
   FilterArgs a = a0;
-  const Layout Ly = make_layout(BX, BY, a.W);
+  const Layout Ly = make_layout(BX, BY, a.W, NBUF);
   a.tiles_x = (a.Wd + BX - 1) / BX;
   const int tiles_y = (a.H + BY - 1) / BY;
   a.ntiles = a.tiles_x * tiles_y;
-  auto kern = fbf_fp32_u8_kernel<BX, BY, NT>;
+  auto kern = fbf_fp32_u8_kernel<BX, BY, NT, NBUF>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Ly.bytes);
   if (e != cudaSuccess) return FBF_ERR_CUDA;
   kern<<<a.ntiles, NT, Ly.bytes, s>>>(a);
@@ -274,9 +310,13 @@ fbf_status launch_cfg(const FilterArgs &a0, cudaStream_t s) {
 
 }  // namespace
 
+// Tile shapes: 64 x 96 outputs with two table buffers for W <= 16 (<= 227 KB
+// of shared memory), 32 x 192 with one buffer for 17 <= W <= 32 (<= 222 KB).
+// Both keep the padded halo rows of the row pass at <= 1.33x the output rows
+// and split the row and column units evenly over 8 warps.
 fbf_status launch_fp32_u8(const FilterArgs &a, cudaStream_t s) {
-  if (a.W <= 16) return launch_cfg<64, 64, 256>(a, s);
-  return launch_cfg<32, 128, 256>(a, s);
+  if (a.W <= 16) return launch_cfg<64, 96, 256, 2>(a, s);
+  return launch_cfg<32, 192, 256, 1>(a, s);
 }
 
 }  // namespace fbf

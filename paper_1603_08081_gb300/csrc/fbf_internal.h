@@ -37,6 +37,7 @@ struct FilterArgs {
   int ntiles;        // tiles in the image
   float w[TAPS_MAX];  // normalised 1-D spatial taps w1[j + W]
   float d[FBF_KMAX];  // cosine coefficients, eq. (6)
+  unsigned long long w2[TAPS_MAX];  // each tap duplicated into both halves of an f32x2 pair
 };
 
 // Common host-side validation + argument packing for the single-image forms.
