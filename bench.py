@@ -6,13 +6,19 @@ sigma_s in {3, 5, 10} x sigma_r in {20, 40}, Gaussian spatial and range kernels,
 coefficients fitted to eps = 1e-3 (K = 17 for sigma_r = 20, K = 9 for 40),
 REFLECT border.  The coefficient fit is host work done once and reported apart.
 
+Forms: fp32 (fused FP32 FMA kernel), tc_fp16 and tc_bf16 (tensor-core
+kernels); all three are timed (interleaved step by step) and the headline
+`form` is the fastest whose output stays within 0.5 gray of the FP64 oracle on
+the CPU-baseline slab.
+
 Printed: ONE JSON line (rank 0).  `value` is whole-job Mpixel/s with inputs
 resident in HBM; `e2e` is the same metric through the public Python API with
 pinned host buffers (H2D of the image and D2H of every output inside the timed
 region).  The L2 is flushed (256 MiB write) between timed steps, outside the
-per-step events.  `roofline` is for the dominant kernel launch (largest share
-of the step), FP32-pipe bound, against an FFMA peak measured in the same
-process.  `cpu_baseline` times the FP64 oracle (Algorithm 1 form) on a
+per-step events.  `roofline` is for the headline form's dominant launch (largest
+share of the step): FP32-pipe bound for fp32 (against an FMA peak measured in
+the same process), tensor-pipe for the tensor-core forms (issued MMA flops
+against the measured bf16 peak).  `cpu_baseline` times the FP64 oracle (Algorithm 1 form) on a
 bounded row slab of the same workload and reports its agreement with the GPU
 output on that slab (the max-error condition of the metric).
 
@@ -157,39 +163,54 @@ def oracle_slab(img, ss, sr, rows):
     return out, time.perf_counter() - t0
 
 
-def cpu_baseline(img, slab_rows: int, gpu_outs=None):
-    """Oracle (FP64 Algorithm 1) on rows [0, slab_rows) of every setting; the
-    slab includes the top border.  Returns the baseline dict and the max error
-    of the GPU outputs on the same slabs (when given)."""
+def cpu_baseline(img, slab_rows: int):
+    """Oracle (FP64 Algorithm 1) on rows [0, slab_rows) of every setting (the
+    slab includes the top border).  Returns the baseline dict and the oracle
+    slabs, against which the GPU outputs of the same rows are compared."""
     import oracle as O
 
-    total_t, total_px, max_err = 0.0, 0, 0.0
-    per = []
-    for i, (ss, sr) in enumerate(SETTINGS):
+    total_t, total_px = 0.0, 0
+    slabs = []
+    for (ss, sr) in SETTINGS:
         out, dt = oracle_slab(img, ss, sr, (0, slab_rows))
         total_t += dt
         total_px += out.size
-        if gpu_outs is not None:
-            e = float(np.max(np.abs(gpu_outs[i][:slab_rows].astype(np.float64) - out)))
-            max_err = max(max_err, e)
-            per.append(e)
+        slabs.append(out)
     res = {"value": total_px / total_t / 1e6, "unit": "Mpixel/s", "cores": O.num_threads(),
            "kind": "oracle",
-           "sample": "FP64 Algorithm-1 oracle on rows 0..%d of the 2048x2048 image, all 6 settings"
-                     " (%d pixels, %.1f s)" % (slab_rows - 1, total_px, total_t)}
-    return res, (max_err if gpu_outs is not None else None), per
-
-
-# ------------------------------------------------------------- FFMA peak ---
-
-def ffma_peak_tflops(torch):
-    """FP32 FMA-pipe throughput measured with the library's FFMA probe kernel."""
-    from paper_1603_08081_gb300 import fbf
-
-    return fbf.fbf_measure_fp32_peak()
+           "sample": "FP64 Algorithm-1 oracle on rows 0..%d of the 2048x2048 image, all %d settings"
+                     " (%d pixels, %.1f s)" % (slab_rows - 1, len(SETTINGS), total_px, total_t)}
+    return res, slabs
 
 
 # ------------------------------------------------------------------ main ---
+
+FORMS_ALL = ["fp32", "tc_fp16", "tc_bf16"]
+FORM_DTYPE = {"fp32": "f32", "tc_fp16": "f16", "tc_bf16": "bf16"}
+FORM_KERNEL = {"fp32": "fbf_fp32_u8_kernel", "tc_fp16": "fbf_tc_u8_kernel<0,2,..>",
+               "tc_bf16": "fbf_tc_u8_kernel<1,3,..>"}
+
+
+def tc_issued_flops(K: int, W: int, form: str) -> float:
+    """Dense MMA flops the tensor-core kernel issues for one 2048x2048 launch
+    (mirrors its tiling: 32-column tiles, 96 rows for W <= 16 else 64; per
+    harmonic 4 channels x 2 output blocks x kc chunks for the row pass and
+    BY/16 x kc for the column pass; 2 or 3 split products per step)."""
+    nsplit = 3 if form == "tc_bf16" else 2
+    BY = 96 if W <= 16 else 64
+    kc = (16 + 2 * W + 15) // 16
+    tiles = math.ceil(W_IMG / 32) * math.ceil(H / BY)
+    mmas = (4 * 2 * kc + (BY // 16) * kc) * nsplit
+    return tiles * K * mmas * 2.0 * 128 * 16 * 16
+
+
+def tensor_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["bf16_tflops"]), "MEASURED_PEAKS.json bf16_tflops (burst; fp16 same nominal rate) (of measured)"
+    except Exception:
+        return 1900.0, "profiling-recipe fallback 1.9 PFLOP/s bf16 burst (of fallback)"
+
 
 def run_ours(args):
     import torch
@@ -200,71 +221,107 @@ def run_ours(args):
     from paper_1603_08081_gb300 import fbf
     from paper_1603_08081_gb300.synth import make_image
 
+    forms = FORMS_ALL if args.form == "all" else [args.form]
     img = make_image(H, W_IMG, SEED)
     t0 = time.perf_counter()
     coeffs = [fbf.fbf_fit_coeffs("gaussian", sr, T, EPS) for (_, sr) in SETTINGS]
     fit_ms = (time.perf_counter() - t0) * 1e3 / len(SETTINGS)
-    params = [fbf.make_params(c, ss, 0, "gaussian", "reflect", args.form)
-              for c, (ss, _) in zip(coeffs, SETTINGS)]
-    Ws = [fbf.fbf_resolve_window(p) for p in params]
+    params = {f: [fbf.make_params(c, ss, 0, "gaussian", "reflect", f)
+                  for c, (ss, _) in zip(coeffs, SETTINGS)] for f in forms}
+    Ws = [fbf.fbf_resolve_window(p) for p in params[forms[0]]]
 
     stream = torch.cuda.Stream(device=dev)
     x = torch.from_numpy(img).to(dev)
-    outs = [torch.empty((H, W_IMG), dtype=torch.float32, device=dev) for _ in SETTINGS]
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     n_set = len(SETTINGS)
+    outs = {f: [torch.empty((H, W_IMG), dtype=torch.float32, device=dev) for _ in SETTINGS] for f in forms}
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
 
-    def step(evs=None):
-        for i, p in enumerate(params):
+    def step(f, evs=None):
+        for i, p in enumerate(params[f]):
             if evs is not None:
                 evs[i][0].record(stream)
-            fbf.fbf_filter(p, x, out=outs[i], stream=stream)
+            fbf.fbf_filter(p, x, out=outs[f][i], stream=stream)
             if evs is not None:
                 evs[i][1].record(stream)
 
     with torch.cuda.stream(stream):
         for _ in range(max(args.warmup, 3)):
-            step()
+            for f in forms:
+                step(f)
     torch.cuda.synchronize(dev)
 
-    ev = [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(n_set)]
-          for _ in range(args.steps)]
-    per_launch = np.zeros((args.steps, n_set))
+    ev = {f: [[[torch.cuda.Event(enable_timing=True) for _ in range(2)] for _ in range(n_set)]
+              for _ in range(args.steps)] for f in forms}
     dist_barrier(world)
     torch.cuda.synchronize(dev)
     with ClockSampler(local) as clk:
         for s in range(args.steps):
-            with torch.cuda.stream(stream):
-                flush.zero_()
-            step(ev[s])
+            for f in forms:  # forms interleaved step by step, L2 flushed before each
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+                step(f, ev[f][s])
         torch.cuda.synchronize(dev)
     dist_barrier(world)
-    for s in range(args.steps):
-        for i in range(n_set):
-            per_launch[s, i] = ev[s][i][0].elapsed_time(ev[s][i][1])
-    step_ms = per_launch.sum(axis=1)
-    total_ms = float(step_ms.sum())
-    total_ms = dist_max(total_ms, world, dev)
+
     px_step = n_set * H * W_IMG
-    value = world * px_step * args.steps / (total_ms * 1e-3) / 1e6
+    fp32_peak = fbf.fbf_measure_fp32_peak(local)
+    tpeak, tpeak_src = tensor_peak()
+    per_form = {}
+    for f in forms:
+        per_launch = np.array([[ev[f][s][i][0].elapsed_time(ev[f][s][i][1]) for i in range(n_set)]
+                               for s in range(args.steps)])
+        total_ms = dist_max(float(per_launch.sum()), world, dev)
+        mean_launch = per_launch.mean(axis=0)
+        dom = int(np.argmax(mean_launch))
+        per_setting = []
+        for i, (ss, sr) in enumerate(SETTINGS):
+            alg = algorithmic_flops_per_pixel(coeffs[i].K, Ws[i]) * H * W_IMG / (mean_launch[i] * 1e-3) / 1e12
+            row = {"sigma_s": ss, "sigma_r": sr, "K": coeffs[i].K, "W": Ws[i],
+                   "ms": round(float(mean_launch[i]), 4),
+                   "mpix_s": round(H * W_IMG / (mean_launch[i] * 1e-3) / 1e6, 1),
+                   "fir_tflops_algorithmic": round(alg, 2)}
+            if f != "fp32":
+                row["mma_tflops_issued"] = round(tc_issued_flops(coeffs[i].K, Ws[i], f)
+                                                 / (mean_launch[i] * 1e-3) / 1e12, 2)
+            per_setting.append(row)
+        K_dom, W_dom = coeffs[dom].K, Ws[dom]
+        launch = "sigma_s=%g sigma_r=%g K=%d W=%d" % (SETTINGS[dom][0], SETTINGS[dom][1], K_dom, W_dom)
+        t_dom = mean_launch[dom] * 1e-3
+        if f == "fp32":
+            ach = algorithmic_flops_per_pixel(K_dom, W_dom) * H * W_IMG / t_dom / 1e12
+            roof = {"bound": "alu", "kernel": FORM_KERNEL[f], "launch": launch, "achieved": round(ach, 3),
+                    "peak": round(fp32_peak, 3), "unit": "TFLOP/s", "frac": round(ach / fp32_peak, 4),
+                    "traffic": None,
+                    "peak_source": "FP32 FMA probe (fbf_measure_fp32_peak) in this process (of measured)"}
+        else:
+            ach = tc_issued_flops(K_dom, W_dom, f) / t_dom / 1e12
+            alg = algorithmic_flops_per_pixel(K_dom, W_dom) * H * W_IMG / t_dom / 1e12
+            roof = {"bound": "tensor", "kernel": FORM_KERNEL[f], "launch": launch, "achieved": round(ach, 3),
+                    "peak": round(tpeak, 1), "unit": "TFLOP/s", "frac": round(ach / tpeak, 4),
+                    "traffic": None, "peak_source": tpeak_src,
+                    "fir_equivalent_tflops": round(alg, 3),
+                    "fir_equivalent_frac_of_fp32_peak": round(alg / fp32_peak, 4)}
+        per_form[f] = {"value": world * px_step * args.steps / (total_ms * 1e-3) / 1e6,
+                       "ms_per_step": total_ms / args.steps, "per_setting": per_setting, "roofline": roof}
 
-    # Dominant launch: the setting with the largest mean time.
-    mean_launch = per_launch.mean(axis=0)
-    dom = int(np.argmax(mean_launch))
-    K_dom, W_dom = coeffs[dom].K, Ws[dom]
-    flops = algorithmic_flops_per_pixel(K_dom, W_dom) * H * W_IMG
-    achieved = flops / (mean_launch[dom] * 1e-3) / 1e12
-    peak = fbf.fbf_measure_fp32_peak(local)
-    per_setting = []
-    for i, (ss, sr) in enumerate(SETTINGS):
-        per_setting.append({
-            "sigma_s": ss, "sigma_r": sr, "K": coeffs[i].K, "W": Ws[i],
-            "ms": round(float(mean_launch[i]), 4),
-            "mpix_s": round(H * W_IMG / (mean_launch[i] * 1e-3) / 1e6, 1),
-            "fp32_tflops_algorithmic": round(algorithmic_flops_per_pixel(coeffs[i].K, Ws[i]) * H * W_IMG
-                                             / (mean_launch[i] * 1e-3) / 1e12, 2)})
+    errs = {}
+    cb = None
+    if rank == 0 and not args.no_cpu_baseline:
+        torch.cuda.synchronize(dev)
+        outs_np = {f: [o.cpu().numpy() for o in outs[f]] for f in forms}
+        cb, ref_slabs = cpu_baseline(img.astype(np.float64), args.slab_rows)
+        for f in forms:
+            per = [float(np.max(np.abs(outs_np[f][i][:args.slab_rows].astype(np.float64) - ref_slabs[i])))
+                   for i in range(n_set)]
+            errs[f] = max(per)
+            for i, e in enumerate(per):
+                per_form[f]["per_setting"][i]["max_err_vs_oracle"] = round(e, 6)
+            per_form[f]["max_err_vs_oracle"] = round(errs[f], 6)
+    ok_forms = [f for f in forms if errs.get(f, 0.0) <= 0.5]
+    head = max(ok_forms or forms, key=lambda f: per_form[f]["value"])
 
-    # End to end through the public API: pinned host image in, every output back.
+    # End to end through the public API (headline form): pinned host image in,
+    # every output back.
     host_in = torch.from_numpy(img).pin_memory()
     host_outs = [torch.empty((H, W_IMG), dtype=torch.float32).pin_memory() for _ in SETTINGS]
     e2e_steps = max(2, min(args.steps, 5))
@@ -272,8 +329,8 @@ def run_ours(args):
     def e2e_step():
         with torch.cuda.stream(stream):
             xd = host_in.to(dev, non_blocking=True)
-            for i, p in enumerate(params):
-                y = fbf.fbf_filter(p, xd, out=outs[i], stream=stream)
+            for i, p in enumerate(params[head]):
+                y = fbf.fbf_filter(p, xd, out=outs[head][i], stream=stream)
                 host_outs[i].copy_(y, non_blocking=True)
         stream.synchronize()
 
@@ -287,37 +344,33 @@ def run_ours(args):
     e2e_s = dist_max(time.perf_counter() - t0, world, dev)
     e2e_val = world * px_step * e2e_steps / e2e_s / 1e6
 
+    hf = per_form[head]
     result = {
-        "metric": METRIC, "value": round(value, 1), "unit": "Mpixel/s", "n_gpus": world,
+        "metric": METRIC, "value": round(hf["value"], 1), "unit": "Mpixel/s", "n_gpus": world,
         "steps": args.steps, "warmup": max(args.warmup, 3),
-        "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "form": args.form,
+        "ms_per_step": round(hf["ms_per_step"], 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": FORM_DTYPE[head], "data": "synthetic",
+        "form": head,
         "config": {"workload": WORKLOAD, "image": "2048x2048 u8", "settings": len(SETTINGS),
                    "eps": EPS, "T": T, "border": "reflect", "spatial": "gaussian",
+                   "forms_timed": forms,
                    "l2": "flushed between steps (256 MiB write, outside the timed events)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": hf["roofline"],
+        "forms": {f: {"value": round(per_form[f]["value"], 1), "ms_per_step": round(per_form[f]["ms_per_step"], 4),
+                      "max_err_vs_oracle": per_form[f].get("max_err_vs_oracle"),
+                      "roofline": per_form[f]["roofline"], "per_setting": per_form[f]["per_setting"]}
+                  for f in forms},
         "fit_ms_per_setting": round(fit_ms, 3),
-        "per_setting": per_setting,
-        "roofline": {"bound": "alu", "kernel": "fbf_fp32_u8_kernel",
-                     "launch": "sigma_s=%g sigma_r=%g K=%d W=%d" % (SETTINGS[dom][0], SETTINGS[dom][1], K_dom, W_dom),
-                     "achieved": round(achieved, 3), "peak": round(peak, 3), "unit": "TFLOP/s",
-                     "frac": round(achieved / peak, 4), "traffic": None,
-                     "peak_source": "FP32 FFMA probe measured in this process (of measured)"},
         "e2e": {"value": round(e2e_val, 1), "unit": "Mpixel/s",
                 "h2d_bytes_per_step": H * W_IMG, "d2h_bytes_per_step": n_set * H * W_IMG * 4},
-        "gpu_launches": n_set * args.steps,
+        "gpu_launches": n_set * args.steps * len(forms),
         "clocks": clk.summary(),
     }
-    if rank == 0 and not args.no_cpu_baseline:
-        torch.cuda.synchronize(dev)
-        gpu_outs = [o.cpu().numpy() for o in outs]
-        cb, max_err, per_err = cpu_baseline(img.astype(np.float64), args.slab_rows, gpu_outs)
+    if cb is not None:
         result["cpu_baseline"] = cb
-        result["max_err_vs_oracle"] = round(max_err, 6)
-        result["accuracy_ok"] = bool(max_err <= 0.5)
-        for i, e in enumerate(per_err):
-            result["per_setting"][i]["max_err_vs_oracle"] = round(e, 6)
+        result["max_err_vs_oracle"] = round(errs[head], 6)
+        result["accuracy_ok"] = bool(errs[head] <= 0.5)
     if rank == 0:
         print(json.dumps(result), flush=True)
     if world > 1:
@@ -368,7 +421,8 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--form", default="fp32", choices=["fp32", "auto", "tc_fp16", "tc_bf16"])
+    ap.add_argument("--form", default="all", choices=["all"] + FORMS_ALL,
+                    help="forms to time (default all; the headline is the fastest within 0.5 gray)")
     ap.add_argument("--slab-rows", type=int, default=384, help="rows of the CPU-baseline sample")
     ap.add_argument("--ref-rows", type=int, default=8, help="rows per setting per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")

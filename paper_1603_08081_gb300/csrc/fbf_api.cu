@@ -78,7 +78,8 @@ extern "C" fbf_status fbf_filter(const fbf_params *p, const void *d_in, fbf_dtyp
   if (form != FBF_FORM_AUTO && form != FBF_FORM_FP32 && form != FBF_FORM_TC_FP16 && form != FBF_FORM_TC_BF16)
     return FBF_ERR_INVALID_ARGUMENT;
   if (dtype != FBF_U8) return FBF_ERR_UNSUPPORTED;
-  if (form == FBF_FORM_TC_FP16 || form == FBF_FORM_TC_BF16) return FBF_ERR_UNSUPPORTED;
+  if (form == FBF_FORM_TC_FP16) return launch_tc_u8(a, 0, stream);
+  if (form == FBF_FORM_TC_BF16) return launch_tc_u8(a, 1, stream);
   return launch_fp32_u8(a, stream);
 }
 
@@ -88,6 +89,8 @@ extern "C" fbf_status fbf_device_error(unsigned int *code) {
   unsigned int v = 0, zero = 0;
   if (cudaMemcpyFromSymbol(&v, g_fbf_device_error, sizeof(v)) != cudaSuccess) return FBF_ERR_CUDA;
   if (cudaMemcpyToSymbol(g_fbf_device_error, &zero, sizeof(zero)) != cudaSuccess) return FBF_ERR_CUDA;
-  *code = v;
+  unsigned int vt = 0;
+  if (tc_read_clear_error(&vt) != FBF_OK) return FBF_ERR_CUDA;
+  *code = v | vt;
   return FBF_OK;
 }

@@ -46,6 +46,8 @@ fbf_status pack_filter_args(const fbf_params *p, const void *d_in, fbf_dtype dty
                             FilterArgs *a);
 
 fbf_status launch_fp32_u8(const FilterArgs &a, cudaStream_t s);
+fbf_status launch_tc_u8(const FilterArgs &a, int bf16, cudaStream_t s);
+fbf_status tc_read_clear_error(unsigned int *code);
 
 inline fbf_status cuda_status(cudaError_t e) { return e == cudaSuccess ? FBF_OK : FBF_ERR_CUDA; }
 

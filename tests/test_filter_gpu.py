@@ -1,5 +1,5 @@
-"""GPU parity of the fused FP32 filter (fbf_filter through the C ABI) against
-the FP64 oracle, element by element.
+"""GPU parity of the device filter forms (fbf_filter through the C ABI: FP32,
+tensor-core FP16, tensor-core BF16) against the FP64 oracle, element by element.
 
 Tolerance.  The contract is max-abs <= 0.5 gray level against the FP64 oracle
 with the same coefficients and border.  The FP32 form is held to a tighter
@@ -18,6 +18,12 @@ pytestmark = pytest.mark.gpu
 
 TOL_CONTRACT = 0.5
 TOL_FP32 = 0.05
+# Tensor-core forms: data split into hi + lo 16-bit parts (and the weights too
+# for BF16); an FP64 emulation of this arithmetic on the 2048x2048 image stays
+# below 1e-3 gray, so 0.02 leaves a 20x margin while catching layout errors.
+TOL_TC = 0.02
+FORMS = ["fp32", "tc_fp16", "tc_bf16"]
+TOL = {"fp32": TOL_FP32, "tc_fp16": TOL_TC, "tc_bf16": TOL_TC}
 
 
 @pytest.fixture(scope="module")
@@ -33,7 +39,7 @@ def fbf():
 
 
 def _gpu(fbf, img, coeffs, sigma_s, W=0, spatial="gaussian", border="reflect", stream=None,
-         pad=0, offset=0):
+         pad=0, offset=0, form="fp32"):
     import torch
 
     H, Wd = img.shape
@@ -43,7 +49,7 @@ def _gpu(fbf, img, coeffs, sigma_s, W=0, spatial="gaussian", border="reflect", s
         x = buf[:, offset:offset + Wd]
     else:
         x = torch.from_numpy(np.ascontiguousarray(img)).cuda()
-    p = fbf.make_params(coeffs, sigma_s, W, spatial, border, "fp32")
+    p = fbf.make_params(coeffs, sigma_s, W, spatial, border, form)
     y = fbf.fbf_filter(p, x, stream=stream)
     torch.cuda.synchronize()
     return y.cpu().numpy().astype(np.float64)
@@ -64,83 +70,90 @@ def _check(got, ref, tol=TOL_FP32):
     return err.max()
 
 
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("border", ["reflect", "truncate"])
-def test_small_plain_config_256(fbf, border):
+def test_small_plain_config_256(fbf, border, form):
     """256x256, Gaussian sigma_s = 3 (W = 9), sigma_r = 30, eps = 1e-2 (K = 10)."""
     img = make_image(256, 256, 1000)
     c = fbf.fbf_fit_coeffs("gaussian", 30.0, 255.0, 1e-2)
     assert c.K == 10
-    got = _gpu(fbf, img, c, 3.0, border=border)
-    _check(got, _oracle_full(img, c, 3.0, 9, "gaussian", border))
+    got = _gpu(fbf, img, c, 3.0, border=border, form=form)
+    _check(got, _oracle_full(img, c, 3.0, 9, "gaussian", border), TOL[form])
 
 
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("shape", [(1, 1), (1, 300), (300, 1), (7, 5), (65, 64), (130, 197),
                                    (64, 64), (129, 33)])
 @pytest.mark.parametrize("border", ["reflect", "truncate"])
-def test_ragged_and_tiny_images(fbf, shape, border):
+def test_ragged_and_tiny_images(fbf, shape, border, form):
     """Sizes off the tile grid, single rows/columns, windows wider than the image."""
     img = make_image(*shape, seed=17)
     c = fbf.fbf_fit_coeffs("gaussian", 20.0, 255.0, 1e-3)
     for sigma_s in (3.0, 7.0):  # W = 9 (64x64 tiles) and W = 21 (32x128 tiles)
         W = int(np.ceil(3 * sigma_s))
-        got = _gpu(fbf, img, c, sigma_s, border=border)
-        _check(got, _oracle_full(img, c, sigma_s, W, "gaussian", border))
+        got = _gpu(fbf, img, c, sigma_s, border=border, form=form)
+        _check(got, _oracle_full(img, c, sigma_s, W, "gaussian", border), TOL[form])
 
 
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("W", [0, 1, 2, 5, 8, 15, 16, 17, 23, 30, 31, 32])
-def test_every_window_tail(fbf, W):
+def test_every_window_tail(fbf, W, form):
     """All tap-count residues mod 8 and both tile configurations (box and Gaussian)."""
     img = make_image(96, 150, seed=W)
     c = fbf.fbf_fit_coeffs("gaussian", 30.0, 255.0, 1e-3)
     for spatial, ss in (("box", 1.0), ("gaussian", max(W, 1) / 3.0)):
         if spatial == "box" and W == 0:
             continue
-        got = _gpu(fbf, img, c, ss, W=W if W > 0 else 1, spatial=spatial)
-        _check(got, _oracle_full(img, c, ss, W if W > 0 else 1, spatial, "reflect"))
+        got = _gpu(fbf, img, c, ss, W=W if W > 0 else 1, spatial=spatial, form=form)
+        _check(got, _oracle_full(img, c, ss, W if W > 0 else 1, spatial, "reflect"), TOL[form])
 
 
-def test_orders_from_one_to_255(fbf):
+@pytest.mark.parametrize("form", FORMS)
+def test_orders_from_one_to_255(fbf, form):
     img = make_image(80, 90, seed=3)
     for c in (fbf.fbf_fit_coeffs("gaussian", 1e12, 255.0, 1e-6),        # K = 1: spatial FIR
               fbf.fbf_fit_coeffs("exponential", 20.0, 255.0, 0.0, 40),   # fixed K = 40
               fbf.fbf_fit_coeffs("exponential", 20.0, 255.0, 1e-3)):     # K = 255
-        got = _gpu(fbf, img, c, 2.0)
-        _check(got, _oracle_full(img, c, 2.0, 6, "gaussian", "reflect"))
+        got = _gpu(fbf, img, c, 2.0, form=form)
+        _check(got, _oracle_full(img, c, 2.0, 6, "gaussian", "reflect"), TOL[form])
 
 
-def test_constant_and_extreme_images(fbf):
+@pytest.mark.parametrize("form", FORMS)
+def test_constant_and_extreme_images(fbf, form):
     c = fbf.fbf_fit_coeffs("gaussian", 30.0, 255.0, 1e-3)
     for v in (0, 1, 128, 255):
         img = np.full((70, 90), v, np.uint8)
-        got = _gpu(fbf, img, c, 3.0)
+        got = _gpu(fbf, img, c, 3.0, form=form)
         assert np.max(np.abs(got - v)) <= 1e-3 * max(1, v)
     rng = np.random.default_rng(5)
     img = rng.choice(np.array([0, 255], np.uint8), size=(64, 80))  # every difference is +-T
-    got = _gpu(fbf, img, c, 2.0)
-    _check(got, _oracle_full(img, c, 2.0, 6, "gaussian", "reflect"))
+    got = _gpu(fbf, img, c, 2.0, form=form)
+    _check(got, _oracle_full(img, c, 2.0, 6, "gaussian", "reflect"), TOL[form])
     img = (np.arange(256, dtype=np.uint8)[None, :].repeat(40, 0))  # all 256 levels
-    got = _gpu(fbf, img, c, 3.0, border="truncate")
-    _check(got, _oracle_full(img, c, 3.0, 9, "gaussian", "truncate"))
+    got = _gpu(fbf, img, c, 3.0, border="truncate", form=form)
+    _check(got, _oracle_full(img, c, 3.0, 9, "gaussian", "truncate"), TOL[form])
 
 
-def test_pitch_offset_and_stream(fbf):
+@pytest.mark.parametrize("form", FORMS)
+def test_pitch_offset_and_stream(fbf, form):
     import torch
 
     img = make_image(100, 123, seed=8)
     c = fbf.fbf_fit_coeffs("gaussian", 40.0, 255.0, 1e-3)
     ref = _oracle_full(img, c, 5.0, 15, "gaussian", "reflect")
     s = torch.cuda.Stream()
-    _check(_gpu(fbf, img, c, 5.0, pad=37, offset=3, stream=s), ref)
-    _check(_gpu(fbf, img, c, 5.0, pad=5, offset=0), ref)
+    _check(_gpu(fbf, img, c, 5.0, pad=37, offset=3, stream=s, form=form), ref, TOL[form])
+    _check(_gpu(fbf, img, c, 5.0, pad=5, offset=0, form=form), ref, TOL[form])
 
 
-def test_subpixel_bound_against_direct_filter(fbf):
+@pytest.mark.parametrize("form", FORMS)
+def test_subpixel_bound_against_direct_filter(fbf, form):
     """eps = 1e-5 gives K = 14 and bound (12) = 0.288 < 0.5 at sigma_s = 3: the GPU
     output is provably within a sub-pixel of the exact bilateral filter, eq. (1)."""
     img = make_image(256, 256, 1000)
     c = fbf.fbf_fit_coeffs("gaussian", 30.0, 255.0, 1e-5)
     assert c.K == 14
-    got = _gpu(fbf, img, c, 3.0)
+    got = _gpu(fbf, img, c, 3.0, form=form)
     w1 = O.weights_1d(O.SPATIAL_GAUSSIAN, 3.0, 9)
     bound = O.bound12(255.0, 1e-5, w1[9] ** 2)
     assert bound < 0.5
@@ -157,19 +170,20 @@ def _sample_points(H, W, n, seed):
     return np.array(ys), np.array(xs)
 
 
+@pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("sigma_s", [3.0, 5.0, 10.0])
 @pytest.mark.parametrize("sigma_r", [20.0, 40.0])
-def test_full_size_2048_sampled(fbf, sigma_s, sigma_r):
+def test_full_size_2048_sampled(fbf, sigma_s, sigma_r, form):
     """2048x2048, eps = 1e-3, the benchmark's launch configuration: sampled pixels
     (random + corners + edges) against eq. (9) summed directly in FP64."""
     img = make_image(2048, 2048, 1100)
     c = fbf.fbf_fit_coeffs("gaussian", sigma_r, 255.0, 1e-3)
-    got = _gpu(fbf, img, c, sigma_s)
+    got = _gpu(fbf, img, c, sigma_s, form=form)
     W = int(np.ceil(3 * sigma_s))
     ys, xs = _sample_points(2048, 2048, 600, seed=int(sigma_s * 10 + sigma_r))
     w1 = O.weights_1d(O.SPATIAL_GAUSSIAN, sigma_s, W)
     ref = O.direct_sbf(img, w1, O.BORDER_REFLECT, np.array(c.coefficients), 255.0,
                        points=(ys, xs))[0]
-    _check(got[ys, xs], ref)
+    _check(got[ys, xs], ref, TOL[form])
     assert np.all(np.isfinite(got))
     assert got.min() >= -1.0 and got.max() <= 256.0
