@@ -29,6 +29,7 @@
 
 #include <cuda_runtime.h>
 
+#include "fbf_common.cuh"
 #include "fbf_internal.h"
 
 namespace fbf {
@@ -67,13 +68,6 @@ __host__ __device__ inline Layout make_layout(int BX, int BY, int W, int nbuf, i
   const size_t tile = (size_t)L.HXA * L.PT * sizeof(unsigned short);
   L.bytes = L.tile_off + ((tile + 127) & ~(size_t)127);
   return L;
-}
-
-__device__ __forceinline__ int reflect_index(int i, int n) {
-  const int p = 2 * n;
-  int m = i % p;
-  if (m < 0) m += p;
-  return m < n ? m : p - 1 - m;
 }
 
 #ifndef FBF_FIR_PACKED
@@ -195,45 +189,11 @@ __global__ void __launch_bounds__(NT, 1) fbf_fp32_u8_kernel(const __grid_constan
         make_float4(0.f, 0.f, 0.f, 0.f);
   }
 
-  // Stage the halo tile, transposed: tileT[ex * PT + ey].  Eight independent
-  // loads per thread are issued before their stores.
-  {
-    const unsigned char *in = static_cast<const unsigned char *>(a.in);
-    const size_t pitch = a.in_pitch;
-    const int total = Ly.HYP * Ly.HXA;
-    for (int base = tid; base < total; base += NT * 8) {
-      unsigned short vals[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int idx = base + u * NT;
-        unsigned short v = kSentinel * kCopies * sizeof(float4);
-        if (idx < total) {
-          const int ey = idx / Ly.HXA, ex = idx - ey * Ly.HXA;
-          if (ey < Ly.HY && ex < Ly.HX) {
-            int iy = ty0 + ey - W, ix = tx0 + ex - W;
-            bool inside;
-            if (a.border == FBF_BORDER_REFLECT) {
-              iy = reflect_index(iy, H);
-              ix = reflect_index(ix, Wd);
-              inside = true;
-            } else {
-              inside = iy >= 0 && iy < H && ix >= 0 && ix < Wd;
-            }
-            if (inside) v = (unsigned short)(__ldg(in + (size_t)iy * pitch + ix) * (kCopies * sizeof(float4)));
-          }
-        }
-        vals[u] = v;
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int idx = base + u * NT;
-        if (idx < total) {
-          const int ey = idx / Ly.HXA, ex = idx - ey * Ly.HXA;
-          tileT[ex * Ly.PT + ey] = vals[u];
-        }
-      }
-    }
-  }
+  // Stage the halo tile, transposed: tileT[ex * PT + ey] (byte offsets into a table buffer).
+  static_assert(BX + 2 * WCAP + kRun <= 128, "staging covers at most 128 ext columns");
+  stage_tile<NT>(static_cast<const unsigned char *>(a.in), a.in_pitch, H, Wd, a.border, ty0 - W, tx0 - W,
+                 Ly.HY, Ly.HX, Ly.HYP, Ly.HXA, tileT, Ly.PT, (unsigned short)(kCopies * sizeof(float4)),
+                 (unsigned short)(kSentinel * kCopies * sizeof(float4)));
   build_lut(lut, 0, a.twoT, a.T, tid, NT);
   __syncthreads();
 

@@ -7,9 +7,10 @@
 // rows fit the 128 TMEM lanes (BY = 96 for W <= 16, 64 for W <= 32).  For each
 // harmonic n:
 //
-//   modulate  thread (lane r, half h) gathers (cos, sin, f cos, f sin)(n w f)
-//             for ext row r and half of the ext columns from the per-harmonic
-//             table, splits each value into hi + lo 16-bit parts and writes
+//   modulate  thread (lane r, half h) gathers, for ext row r and half of the
+//             ext columns, the per-harmonic table entry of each pixel value:
+//             (cos, sin, f cos, f sin)(n w f) already split into hi + lo 16-bit
+//             parts, pairs neighbouring columns with byte permutes and writes
 //             them with tcgen05.st into TMEM: A1[c][part] (lane = ext row,
 //             K = ext column, two 16-bit elements per 32-bit column);
 //   row MMA   D1[c] (lane = ext row, 32 columns = outputs x) = sum over
@@ -34,6 +35,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include "fbf_common.cuh"
 #include "fbf_internal.h"
 #include "fbf_tc_ptx.cuh"
 
@@ -47,7 +49,11 @@ using namespace tc;
 constexpr int kCopies = 8;
 constexpr int kLutEntries = 257;
 constexpr int kSentinel = 256;
-constexpr int kLutStride = kLutEntries * kCopies;  // float4 per table buffer
+constexpr int kLutStride = kLutEntries * kCopies;  // entries per table buffer
+// Per harmonic and pixel value v two tables, 8 interleaved copies each:
+//   lut16[v]: uint4 of 16-bit (hi c | hi s<<16, hi fc | hi fs<<16, lo c | lo s<<16, lo fc | lo fs<<16)
+//   lutf[v]:  float2 (cos, sin) in FP32 for the demodulation.
+// The staged tile holds v * 128, the byte offset of v's row in lut16 (half of it in lutf).
 constexpr int kBX = 32;                             // output columns per tile
 constexpr int kLanes = 128;                         // TMEM lanes = halo rows per tile
 constexpr int kPT = kLanes + 2;                     // tile pitch (u16), PT/2 odd
@@ -57,45 +63,32 @@ constexpr uint32_t kMaxPolls = 1u << 22;
 constexpr int kNT = 256;
 
 struct TcLayout {
-  int kc;   // 16-wide K chunks meeting the band of one 16-output block
+  int kcr;  // 16-wide K chunks meeting the band of one NBR-output block (row pass)
+  int kcc;  // the same for one NBC-output block (column pass)
   int KX;   // K extent of the row pass (ext columns, multiple of 16)
   int A1C;  // TMEM columns per (channel, part) of A1 = KX / 2
-  size_t lut_off, a2_off, b_off, tile_off, bar_off, bytes;
+  size_t lut16_off, lutf_off, a2_off, br_off, bc_off, tile_off, bar_off, bytes;
 };
 
-__host__ __device__ inline TcLayout tc_layout(int W, int wcap) {
+// Shared memory: [lut16 (one buffer)][lutf (two buffers)][A2 hi | lo]
+// [row Toeplitz blocks][column Toeplitz blocks][tile][barrier, TMEM address, flags].
+__host__ __device__ inline TcLayout tc_layout(int W, int wcap, int nbr, int nbc) {
   TcLayout L;
-  L.kc = (16 + 2 * W + 15) / 16;
-  L.KX = 16 * (kBX / 16 - 1 + L.kc);
+  L.kcr = (nbr + 2 * W + 15) / 16;
+  L.kcc = (nbc + 2 * W + 15) / 16;
+  L.KX = kBX - nbr + 16 * L.kcr;
   L.A1C = L.KX / 2;
-  const int kcmax = (16 + 2 * wcap + 15) / 16;
-  const int KXmax = 16 * (kBX / 16 - 1 + kcmax);
-  L.lut_off = 0;
-  L.a2_off = L.lut_off + 2ull * kLutStride * sizeof(float4);
-  L.b_off = L.a2_off + 2ull * kA2Part;
-  L.tile_off = L.b_off + (size_t)kcmax * 2 * 512;
+  const int kcr_max = (nbr + 2 * wcap + 15) / 16, kcc_max = (nbc + 2 * wcap + 15) / 16;
+  const int KXmax = kBX - nbr + 16 * kcr_max;
+  L.lut16_off = 0;
+  L.lutf_off = L.lut16_off + (size_t)kLutStride * sizeof(uint4);
+  L.a2_off = L.lutf_off + 2ull * kLutStride * sizeof(float2);
+  L.br_off = L.a2_off + 2ull * kA2Part;
+  L.bc_off = L.br_off + (size_t)kcr_max * 2 * nbr * 32;
+  L.tile_off = L.bc_off + (size_t)kcc_max * 2 * nbc * 32;
   L.bar_off = L.tile_off + (((size_t)KXmax * kPT * 2 + 127) & ~(size_t)127);
   L.bytes = L.bar_off + 64;
   return L;
-}
-
-__device__ __forceinline__ int reflect_index(int i, int n) {
-  const int p = 2 * n;
-  int m = i % p;
-  if (m < 0) m += p;
-  return m < n ? m : p - 1 - m;
-}
-
-__device__ __forceinline__ void build_lut(float4 *L, int n, int twoT, float T, int tid) {
-  for (int v = tid; v < 256; v += kNT) {
-    const int m = (n * v) % twoT;
-    float sn, cs;
-    sincospif((float)m / T, &sn, &cs);
-    const float fv = (float)v;
-    const float4 e = make_float4(cs, sn, fv * cs, fv * sn);
-#pragma unroll
-    for (int j = 0; j < kCopies; ++j) L[v * kCopies + ((j + v) & (kCopies - 1))] = e;
-  }
 }
 
 // Two floats -> packed 16-bit pair (first in the low half) plus the residuals.
@@ -131,270 +124,336 @@ __device__ __forceinline__ float from16(unsigned short x) {
   return __half2float(*reinterpret_cast<const __half *>(&x));
 }
 
-__device__ __forceinline__ void tmem_st_x4(uint32_t taddr, uint32_t r0, uint32_t r1, uint32_t r2, uint32_t r3) {
-  asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr), "r"(r0), "r"(r1),
-               "r"(r2), "r"(r3)
-               : "memory");
+// Per-harmonic tables (see above); copies written rotated so the 8 stores of one
+// value land in 8 different bank groups.
+template <int BF>
+__device__ __forceinline__ void build_lut(uint4 *L16, float2 *Lf, int n, int twoT, float T, int tid) {
+  for (int v = tid; v < 256; v += kNT) {
+    const int m = (n * v) % twoT;  // exact phase index: n*omega*v = pi * m / T (mod 2 pi)
+    float sn, cs;
+    sincospif((float)m / T, &sn, &cs);
+    const float fv = (float)v;
+    uint4 e;
+    split2<BF>(cs, sn, e.x, e.z);
+    split2<BF>(fv * cs, fv * sn, e.y, e.w);
+    const float2 f = make_float2(cs, sn);
+#pragma unroll
+    for (int j = 0; j < kCopies; ++j) {
+      L16[v * kCopies + ((j + v) & (kCopies - 1))] = e;
+      Lf[v * kCopies + ((j + v) & (kCopies - 1))] = f;
+    }
+  }
+}
+
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
+  uint32_t d;
+  asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+  return d;
+}
+
+// Toeplitz blocks for output blocks of NB: block i (K chunk offset i) holds
+// element (n, k) = w[16 i + k - n] inside the band and 0 outside, K-major
+// without swizzle ((n % 8) * 16 + (n / 8) * 256 + (k % 8) * 2 + (k / 8) * 128);
+// part 0 is the 16-bit weight, part 1 its residual.
+template <int BF, int NB>
+__device__ __forceinline__ void build_toeplitz(unsigned char *B, int nblocks, int W, const float *w, int tid) {
+  for (int e = tid; e < nblocks * NB * 16; e += kNT) {
+    const int i = e / (NB * 16), rem = e - i * NB * 16, n = rem >> 4, k = rem & 15;
+    const int t = 16 * i + k - n;
+    const float wv = (t >= 0 && t <= 2 * W) ? w[t] : 0.f;
+    const unsigned short hi = to16<BF>(wv);
+    const unsigned short lo = to16<BF>(wv - from16<BF>(hi));
+    const int off = (n & 7) * 16 + (n >> 3) * 256 + (k & 7) * 2 + (k >> 3) * 128;
+    *reinterpret_cast<unsigned short *>(B + (size_t)(2 * i) * NB * 32 + off) = hi;
+    *reinterpret_cast<unsigned short *>(B + (size_t)(2 * i + 1) * NB * 32 + off) = lo;
+  }
 }
 
 // BF: 0 = FP16, 1 = BF16.  NSPLIT: 2 = data hi/lo x weights hi; 3 = plus data hi x weights lo.
-// BY: output rows per tile (BY + 2 * WCAP <= 128).
-template <int BF, int NSPLIT, int BY, int WCAP>
+// BY: output rows per tile (BY + 2 * WCAP <= 128).  NBR / NBC: MMA N (output
+// block) of the row / column pass; bigger blocks issue fewer, larger MMAs at the
+// price of more zero taps inside each block.
+template <int BF, int NSPLIT, int BY, int WCAP, int NBR, int NBC, int PIPE>
 __global__ void __launch_bounds__(kNT, 1) fbf_tc_u8_kernel(const __grid_constant__ FilterArgs a) {
   static_assert(BY + 2 * WCAP <= kLanes && BY % 32 == 0, "halo rows must fit the TMEM lanes");
+  static_assert(kBX % NBR == 0 && BY % NBC == 0 && NBR % 16 == 0 && NBC % 16 == 0, "output blocks");
+  static_assert(BY - NBC + 16 * ((NBC + 2 * WCAP + 15) / 16) <= kLanes, "column-pass K fits A2");
+  // A1 (8 regions of KX/2 columns) must fit below D1: 256 columns when
+  // pipelined (D1 at 256, D2 at 384), 384 otherwise (D1 at 384, D2 over A1).
+  static_assert(4 * (kBX - NBR + 16 * ((NBR + 2 * WCAP + 15) / 16)) <= (PIPE ? 256 : 384), "A1 fits below D1");
   constexpr int BYH = BY / 2;  // output rows per thread in the demodulation
+  constexpr int NP = NSPLIT;   // products per (chunk, output block)
+  // MMAs are issued by lane 0 of several warps (a single issuing thread would
+  // spend ~50 cycles per small MMA); every issuer owns whole accumulator blocks.
+  constexpr int kRowIssuers = 4;                                 // one per channel
+  constexpr int kColBlocks = BY / NBC;
+  constexpr int kColIssuers = kColBlocks < 4 ? kColBlocks : 4;  // output blocks j = w, w + 4, ...
   extern __shared__ __align__(1024) unsigned char smem[];
   const int W = a.W;
-  const TcLayout Ly = tc_layout(W, WCAP);
-  float4 *lut = reinterpret_cast<float4 *>(smem + Ly.lut_off);
+  const TcLayout Ly = tc_layout(W, WCAP, NBR, NBC);
+  uint4 *lut16 = reinterpret_cast<uint4 *>(smem + Ly.lut16_off);
+  float2 *lutf = reinterpret_cast<float2 *>(smem + Ly.lutf_off);
   unsigned char *A2 = smem + Ly.a2_off;
-  unsigned char *Bt = smem + Ly.b_off;
   unsigned short *tileT = reinterpret_cast<unsigned short *>(smem + Ly.tile_off);
-  uint64_t *mbar = reinterpret_cast<uint64_t *>(smem + Ly.bar_off);
+  uint64_t *mbarR = reinterpret_cast<uint64_t *>(smem + Ly.bar_off);      // row MMAs done
+  uint64_t *mbarC = reinterpret_cast<uint64_t *>(smem + Ly.bar_off + 8);  // column MMAs done
   uint32_t *tmem_base_s = reinterpret_cast<uint32_t *>(smem + Ly.bar_off + 16);
   int *abort_s = reinterpret_cast<int *>(smem + Ly.bar_off + 32);
 
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, cp = lane & (kCopies - 1);
   const int q = warp & 3, h = warp >> 2;  // TMEM lane quadrant, half
   const int tile_y = blockIdx.x / a.tiles_x, tile_x = blockIdx.x - tile_y * a.tiles_x;
   const int ty0 = tile_y * BY, tx0 = tile_x * kBX;
   const int H = a.H, Wd = a.Wd, HY = BY + 2 * W;
-  const int kc = Ly.kc, A1C = Ly.A1C;
+  const int kcr = Ly.kcr, kcc = Ly.kcc, A1C = Ly.A1C;
 
   if (warp == 0) {
     tmem_alloc(tmem_base_s, 512);
     tmem_relinquish();
   }
   if (tid == 0) {
-    mbar_init(mbar, 1);
+    mbar_init(mbarR, kRowIssuers);  // one commit per issuing warp
+    mbar_init(mbarC, kColIssuers);
     mbar_fence_init();
     *abort_s = 0;
   }
-  if (tid < 2 * kCopies)
-    lut[(tid / kCopies) * kLutStride + kSentinel * kCopies + (tid % kCopies)] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (tid < kCopies) lut16[kSentinel * kCopies + tid] = make_uint4(0u, 0u, 0u, 0u);
+  if (tid < 2 * kCopies)  // sentinel rows: zero channels
+    lutf[(tid / kCopies) * kLutStride + kSentinel * kCopies + (tid % kCopies)] = make_float2(0.f, 0.f);
+  build_toeplitz<BF, NBR>(smem + Ly.br_off, kcr, W, a.w, tid);
+  build_toeplitz<BF, NBC>(smem + Ly.bc_off, kcc, W, a.w, tid);
 
-  // Toeplitz blocks T_i (16 x 16, K-major, no swizzle): element (n, k) = w[16 i + k - n]
-  // inside the band, 0 outside; part 0 = hi, part 1 = lo residual of the weights.
-  for (int e = tid; e < kc * 256; e += kNT) {
-    const int i = e >> 8, n = (e >> 4) & 15, k = e & 15;
-    const int t = 16 * i + k - n;
-    const float wv = (t >= 0 && t <= 2 * W) ? a.w[t] : 0.f;
-    const unsigned short hi = to16<BF>(wv);
-    const unsigned short lo = to16<BF>(wv - from16<BF>(hi));
-    const int off = (n & 7) * 16 + (n >> 3) * 256 + (k & 7) * 2 + (k >> 3) * 128;
-    *reinterpret_cast<unsigned short *>(Bt + (size_t)i * 1024 + off) = hi;
-    *reinterpret_cast<unsigned short *>(Bt + (size_t)i * 1024 + 512 + off) = lo;
-  }
-
-  // Halo tile, transposed, as byte offsets into a table buffer (sentinel outside).
-  {
-    const unsigned char *in = static_cast<const unsigned char *>(a.in);
-    const size_t pitch = a.in_pitch;
-    const int KX = Ly.KX, total = kLanes * KX;
-    const int HX = kBX + 2 * W;
-    for (int base = tid; base < total; base += kNT * 8) {
-      unsigned short vals[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int idx = base + u * kNT;
-        unsigned short v = kSentinel * kCopies * sizeof(float4);
-        if (idx < total) {
-          const int ey = idx / KX, ex = idx - ey * KX;
-          if (ey < HY && ex < HX) {
-            int iy = ty0 + ey - W, ix = tx0 + ex - W;
-            bool inside;
-            if (a.border == FBF_BORDER_REFLECT) {
-              iy = reflect_index(iy, H);
-              ix = reflect_index(ix, Wd);
-              inside = true;
-            } else {
-              inside = iy >= 0 && iy < H && ix >= 0 && ix < Wd;
-            }
-            if (inside) v = (unsigned short)(__ldg(in + (size_t)iy * pitch + ix) * (kCopies * sizeof(float4)));
-          }
-        }
-        vals[u] = v;
-      }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) {
-        const int idx = base + u * kNT;
-        if (idx < total) {
-          const int ey = idx / KX, ex = idx - ey * KX;
-          tileT[ex * kPT + ey] = vals[u];
-        }
-      }
-    }
-  }
-  build_lut(lut, 0, a.twoT, a.T, tid);
+  // Halo tile (128 ext rows x KX ext columns), transposed, as byte offsets v * 128.
+  stage_tile<kNT>(static_cast<const unsigned char *>(a.in), a.in_pitch, H, Wd, a.border, ty0 - W, tx0 - W, HY,
+                  kBX + 2 * W, kLanes, Ly.KX, tileT, kPT, (unsigned short)(kCopies * sizeof(uint4)),
+                  (unsigned short)(kSentinel * kCopies * sizeof(uint4)));
+  build_lut<BF>(lut16, lutf, 0, a.twoT, a.T, tid);
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
   const uint32_t tmem = *tmem_base_s;
   const uint32_t lane_base = (uint32_t)(32 * q) << 16;
-  const uint32_t kA1 = 0, kD1 = 384, kD2 = 0;  // TMEM column bases (D2 reuses A1's columns)
-  constexpr uint32_t idesc_row = idesc_f16(128, 16, BF, 0, 0);
-  constexpr uint32_t idesc_col = idesc_f16(128, 16, BF, 1, 0);
-  const uint32_t b_s = smem_u32(Bt), a2_s = smem_u32(A2);
+  // TMEM column bases: pipelined, A1 | D1 | D2 are disjoint; otherwise D2 reuses A1.
+  const uint32_t kA1 = 0, kD1 = PIPE ? 256 : 384, kD2 = PIPE ? 384 : 0;
+  constexpr uint32_t idesc_row = idesc_f16(128, NBR, BF, 0, 0);
+  constexpr uint32_t idesc_col = idesc_f16(128, NBC, BF, 1, 0);
+  // Descriptor bases; offsets below 256 KB are added to the low address field.
+  const uint64_t br_desc = smem_desc(smem_u32(smem + Ly.br_off), 128, 256);
+  const uint64_t bc_desc = smem_desc(smem_u32(smem + Ly.bc_off), 128, 256);
+  const uint64_t a2_desc = smem_desc(smem_u32(A2), kA2Group, 128);
 
   float part[BYH];
 #pragma unroll
   for (int j = 0; j < BYH; ++j) part[j] = 0.f;
-  uint32_t phase = 0;
+  uint32_t phR = 0, phC = 0;
   bool ok = true;
 
-  for (int n = 0; n < a.K && ok; ++n) {
-    const char *Lc = reinterpret_cast<const char *>(lut + (n & 1) * kLutStride + (lane & (kCopies - 1)));
+  const char *L16 = reinterpret_cast<const char *>(lut16 + cp);
+  // Table byte offsets (lutf) of this thread's BYH demodulation pixels, packed
+  // two per register; the same for every harmonic of the tile.
+  uint32_t cen_pk[BYH / 2];
+  {
+    const int x = 8 * q + (lane >> 2);
+    const unsigned short *cen = tileT + (x + W) * kPT + W + h * BYH;
+#pragma unroll
+    for (int j = 0; j < BYH / 2; ++j) cen_pk[j] = (uint32_t)(cen[2 * j] >> 1) | ((uint32_t)(cen[2 * j + 1] >> 1) << 16);
+  }
+  auto cen_off = [&](int j) -> uint32_t { return (j & 1) ? (cen_pk[j >> 1] >> 16) : (cen_pk[j >> 1] & 0xFFFFu); };
 
-    // ---- modulate: ext row r = 32 q + lane, columns [h * A1C/2, (h+1) * A1C/2) in pairs.
-    {
-      const int r = 32 * q + lane;
-      const int c0 = h * (A1C / 2), c1 = (h + 1) * (A1C / 2);
-      for (int col = c0; col < c1; col += 4) {
-        uint32_t hi[4][4], lo[4][4];  // [channel][column]
+  // ---- modulate harmonic n: ext row r = 32 q + lane, TMEM columns [h * A1C/2, (h+1) * A1C/2).
+  auto modulate = [&]() {
+    const unsigned short *tcol = tileT + 32 * q + lane;
+    const int c0 = h * (A1C / 2), c1 = (h + 1) * (A1C / 2);
+    for (int col = c0; col < c1; col += 4) {
+      uint4 e[8];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int u = 2 * (col + j);
-          const float4 e0 = *reinterpret_cast<const float4 *>(Lc + tileT[u * kPT + r]);
-          const float4 e1 = *reinterpret_cast<const float4 *>(Lc + tileT[(u + 1) * kPT + r]);
-          split2<BF>(e0.x, e1.x, hi[0][j], lo[0][j]);
-          split2<BF>(e0.y, e1.y, hi[1][j], lo[1][j]);
-          split2<BF>(e0.z, e1.z, hi[2][j], lo[2][j]);
-          split2<BF>(e0.w, e1.w, hi[3][j], lo[3][j]);
-        }
+      for (int j = 0; j < 8; ++j) e[j] = *reinterpret_cast<const uint4 *>(L16 + tcol[(2 * col + j) * kPT]);
+      uint32_t v[8][4];  // [channel * 2 + part][column]
 #pragma unroll
-        for (int c = 0; c < 4; ++c) {
-          const uint32_t t_hi = tmem + lane_base + kA1 + (uint32_t)((2 * c) * A1C + col);
-          const uint32_t t_lo = tmem + lane_base + kA1 + (uint32_t)((2 * c + 1) * A1C + col);
-          tmem_st_x4(t_hi, hi[c][0], hi[c][1], hi[c][2], hi[c][3]);
-          tmem_st_x4(t_lo, lo[c][0], lo[c][1], lo[c][2], lo[c][3]);
-        }
+      for (int j = 0; j < 4; ++j) {
+        const uint4 a0 = e[2 * j], a1 = e[2 * j + 1];
+        v[0][j] = prmt(a0.x, a1.x, 0x5410);  // cos hi
+        v[2][j] = prmt(a0.x, a1.x, 0x7632);  // sin hi
+        v[4][j] = prmt(a0.y, a1.y, 0x5410);  // f cos hi
+        v[6][j] = prmt(a0.y, a1.y, 0x7632);  // f sin hi
+        v[1][j] = prmt(a0.z, a1.z, 0x5410);  // cos lo
+        v[3][j] = prmt(a0.z, a1.z, 0x7632);  // sin lo
+        v[5][j] = prmt(a0.w, a1.w, 0x5410);  // f cos lo
+        v[7][j] = prmt(a0.w, a1.w, 0x7632);  // f sin lo
       }
-      tmem_st_wait();
+#pragma unroll
+      for (int cp2 = 0; cp2 < 8; ++cp2)
+        tmem_st_x4(tmem + lane_base + kA1 + (uint32_t)(cp2 * A1C + col), v[cp2][0], v[cp2][1], v[cp2][2],
+                   v[cp2][3]);
     }
-    fence_before_sync();
-    __syncthreads();
+    tmem_st_wait();
+  };
 
-    // ---- row MMAs (one thread), then build the next table while they run.
-    if (tid == 0) {
-      fence_after_sync();
-#pragma unroll 1
-      for (int c = 0; c < 4; ++c)
-#pragma unroll 1
-        for (int j = 0; j < kBX / 16; ++j)
-#pragma unroll 1
-          for (int i = 0; i < kc; ++i) {
-            const uint32_t d = tmem + kD1 + (uint32_t)(c * 32 + j * 16);
-            const uint32_t ahi = tmem + kA1 + (uint32_t)((2 * c) * A1C + (j + i) * 8);
-            const uint32_t alo = tmem + kA1 + (uint32_t)((2 * c + 1) * A1C + (j + i) * 8);
-            const uint64_t bhi = smem_desc(b_s + i * 1024, 128, 256);
-            mma_ts(d, ahi, bhi, idesc_row, i > 0 ? 1u : 0u);
-            mma_ts(d, alo, bhi, idesc_row, 1u);
-            if (NSPLIT == 3) mma_ts(d, ahi, smem_desc(b_s + i * 1024 + 512, 128, 256), idesc_row, 1u);
-          }
-      mma_commit(mbar);
-    }
-    if (n + 1 < a.K) build_lut(lut + ((n + 1) & 1) * kLutStride, n + 1, a.twoT, a.T, tid);
-    if (!mbar_wait_bounded(mbar, phase, kMaxPolls)) *abort_s = 1;
-    phase ^= 1;
+  // ---- row MMAs: lane 0 of warp c issues channel c (its own accumulators).
+  const bool row_issuer = lane == 0 && warp < kRowIssuers;
+  const bool col_issuer = lane == 0 && warp < kColIssuers;
+  auto issue_row = [&]() {
     fence_after_sync();
-    if (__syncthreads_or(*abort_s)) {
-      ok = false;
-      break;
-    }
-
-    // ---- re-split the row-pass result into the column pass's A operand.
-    // Thread: ext row r, channels 2h and 2h+1; A2[m = c*32 + x][r] is MN-major:
-    // (m % 8) * 2 + (r % 8) * 16 + (m / 8) * 128 + (r / 8) * kA2Group.
-    {
-      const int r = 32 * q + lane;
-      unsigned char *rowp = A2 + (r & 7) * 16 + (r >> 3) * kA2Group;
+    const int c = warp;
+#pragma unroll 1
+    for (int i = 0; i < kcr; ++i)
 #pragma unroll
-      for (int cc = 0; cc < 2; ++cc) {
-        const int c = 2 * h + cc;
+      for (int pp = 0; pp < NP; ++pp) {
+        const int ap = pp == 1 ? 1 : 0;  // data part: hi, lo, hi
+        const int bp = pp == 2 ? 1 : 0;  // weight part: hi, hi, lo
+        const uint64_t bd = br_desc + (uint64_t)(((2 * i + bp) * NBR * 32) >> 4);
 #pragma unroll
-        for (int half16 = 0; half16 < 2; ++half16) {
-          uint32_t v[16];
-          tmem_ld_x16(tmem + lane_base + kD1 + (uint32_t)(c * 32 + half16 * 16), v);
-          tmem_ld_wait();
-#pragma unroll
-          for (int g = 0; g < 2; ++g) {  // 8 consecutive m = one 16-byte row of a core matrix
-            uint4 vh, vl;
-            split2<BF>(__uint_as_float(v[8 * g + 0]), __uint_as_float(v[8 * g + 1]), vh.x, vl.x);
-            split2<BF>(__uint_as_float(v[8 * g + 2]), __uint_as_float(v[8 * g + 3]), vh.y, vl.y);
-            split2<BF>(__uint_as_float(v[8 * g + 4]), __uint_as_float(v[8 * g + 5]), vh.z, vl.z);
-            split2<BF>(__uint_as_float(v[8 * g + 6]), __uint_as_float(v[8 * g + 7]), vh.w, vl.w);
-            const int mg = c * 4 + half16 * 2 + g;  // M group of 8
-            *reinterpret_cast<uint4 *>(rowp + mg * 128) = vh;
-            *reinterpret_cast<uint4 *>(rowp + kA2Part + mg * 128) = vl;
-          }
-        }
+        for (int j = 0; j < kBX / NBR; ++j)
+          mma_ts(tmem + kD1 + (uint32_t)(c * 32 + j * NBR),
+                 tmem + kA1 + (uint32_t)((2 * c + ap) * A1C + (j * NBR / 16 + i) * 8), bd, idesc_row,
+                 (i > 0 || pp > 0) ? 1u : 0u);
       }
+    mma_commit(mbarR);
+  };
+
+  // ---- re-split the row-pass result into the column pass's A operand.
+  // Thread: ext row r, outputs x in [16 h, 16 h + 16), all four channels;
+  // A2[m = 4 x + c][r] is MN-major:
+  // (m % 8) * 2 + (r % 8) * 16 + (m / 8) * 128 + (r / 8) * kA2Group.
+  auto resplit = [&]() {
+    const int r = 32 * q + lane;
+    unsigned char *rowp = A2 + (r & 7) * 16 + (r >> 3) * kA2Group;
+    uint32_t v[4][16];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) tmem_ld_x16(tmem + lane_base + kD1 + (uint32_t)(32 * c + 16 * h), v[c]);
+#pragma unroll
+    for (int c = 0; c < 4; ++c) tmem_ld_wait_dep(v[c]);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {  // m = 64 h + 8 k + (0..7): x = 16 h + 2 k + {0, 1}, c = 0..3
+      uint4 vh, vl;
+      split2<BF>(__uint_as_float(v[0][2 * k]), __uint_as_float(v[1][2 * k]), vh.x, vl.x);
+      split2<BF>(__uint_as_float(v[2][2 * k]), __uint_as_float(v[3][2 * k]), vh.y, vl.y);
+      split2<BF>(__uint_as_float(v[0][2 * k + 1]), __uint_as_float(v[1][2 * k + 1]), vh.z, vl.z);
+      split2<BF>(__uint_as_float(v[2][2 * k + 1]), __uint_as_float(v[3][2 * k + 1]), vh.w, vl.w);
+      const int mg = 8 * h + k;
+      *reinterpret_cast<uint4 *>(rowp + mg * 128) = vh;
+      *reinterpret_cast<uint4 *>(rowp + kA2Part + mg * 128) = vl;
     }
     fence_proxy_async_smem();
+  };
+
+  // ---- column MMAs: lane 0 of warp w issues output blocks j = w, w + 4, ...
+  auto issue_col = [&]() {
+    fence_after_sync();
+#pragma unroll 1
+    for (int j = warp; j < kColBlocks; j += kColIssuers)
+#pragma unroll 1
+      for (int i = 0; i < kcc; ++i)
+#pragma unroll
+        for (int pp = 0; pp < NP; ++pp) {
+          const int ap = pp == 1 ? 1 : 0;
+          const int bp = pp == 2 ? 1 : 0;
+          const uint64_t bd = bc_desc + (uint64_t)(((2 * i + bp) * NBC * 32) >> 4);
+          const uint32_t ao = (uint32_t)(ap * kA2Part + (j * NBC / 16 + i) * 2 * kA2Group);
+          mma_ss(tmem + kD2 + (uint32_t)(j * NBC), a2_desc + (uint64_t)(ao >> 4), bd, idesc_col,
+                 (i > 0 || pp > 0) ? 1u : 0u);
+        }
+    mma_commit(mbarC);
+  };
+
+  // ---- demodulate harmonic n: lane m = 32 q + lane = 4 x + c, rows y in
+  // [h * BYH, (h+1) * BYH); the four lanes of one x read the same table entry.
+  auto demod = [&](int n) {
+    const int x = 8 * q + (lane >> 2), c = lane & 3;
+    const float dn = a.d[n];
+    const char *Lf = reinterpret_cast<const char *>(lutf + (n & 1) * kLutStride + ((lane >> 2) & (kCopies - 1)));
+    uint32_t v[BYH / 16][16];
+#pragma unroll
+    for (int g = 0; g < BYH / 16; ++g) tmem_ld_x16(tmem + lane_base + kD2 + (uint32_t)(h * BYH + 16 * g), v[g]);
+    float t[BYH];
+#pragma unroll
+    for (int j = 0; j < BYH; ++j) {
+      const float2 cs = *reinterpret_cast<const float2 *>(Lf + cen_off(j));
+      t[j] = dn * ((c & 1) ? cs.y : cs.x);  // cos for G_r, F_r; sin for G_i, F_i
+    }
+#pragma unroll
+    for (int g = 0; g < BYH / 16; ++g) tmem_ld_wait_dep(v[g]);
+#pragma unroll
+    for (int g = 0; g < BYH / 16; ++g)
+#pragma unroll
+      for (int j = 0; j < 16; ++j) part[16 * g + j] = fmaf(t[16 * g + j], __uint_as_float(v[g][j]), part[16 * g + j]);
+  };
+
+  // Bounded wait on an MMA barrier, then a CTA-wide agreement on failure.
+  auto wait_mma = [&](uint64_t *m, uint32_t &ph) -> bool {
+    if (!mbar_wait_bounded(m, ph, kMaxPolls)) *abort_s = 1;
+    ph ^= 1;
+    fence_after_sync();
+    return __syncthreads_or(*abort_s) == 0;
+  };
+
+  if (!PIPE) {
+    // Serial schedule: modulate -> row MMAs (tables for n+1 built meanwhile) ->
+    // re-split -> column MMAs -> demodulate.
+    for (int n = 0; n < a.K && ok; ++n) {
+      modulate();
+      fence_before_sync();
+      __syncthreads();
+      if (row_issuer) issue_row();
+      if (n + 1 < a.K) build_lut<BF>(lut16, lutf + ((n + 1) & 1) * kLutStride, n + 1, a.twoT, a.T, tid);
+      if (!(ok = wait_mma(mbarR, phR))) break;
+      resplit();
+      fence_before_sync();
+      __syncthreads();
+      if (col_issuer) issue_col();
+      if (!(ok = wait_mma(mbarC, phC))) break;
+      demod(n);
+      fence_before_sync();
+      __syncthreads();
+    }
+  } else {
+    // Pipelined schedule: the column MMAs of harmonic n run while harmonic n+1
+    // is modulated, and the row MMAs of n+1 run while n is demodulated and the
+    // tables of n+2 are built.
+    modulate();
     fence_before_sync();
     __syncthreads();
-
-    // ---- column MMAs.
-    if (tid == 0) {
-      fence_after_sync();
-#pragma unroll 1
-      for (int j = 0; j < BY / 16; ++j)
-#pragma unroll 1
-        for (int i = 0; i < kc; ++i) {
-          const uint32_t d = tmem + kD2 + (uint32_t)(j * 16);
-          const uint32_t ao = (uint32_t)((j + i) * 2 * kA2Group);
-          const uint64_t ahi = smem_desc(a2_s + ao, kA2Group, 128);
-          const uint64_t alo = smem_desc(a2_s + kA2Part + ao, kA2Group, 128);
-          const uint64_t bhi = smem_desc(b_s + i * 1024, 128, 256);
-          mma_ss(d, ahi, bhi, idesc_col, i > 0 ? 1u : 0u);
-          mma_ss(d, alo, bhi, idesc_col, 1u);
-          if (NSPLIT == 3) mma_ss(d, ahi, smem_desc(b_s + i * 1024 + 512, 128, 256), idesc_col, 1u);
-        }
-      mma_commit(mbar);
+    if (row_issuer) issue_row();
+    if (a.K > 1) build_lut<BF>(lut16, lutf + kLutStride, 1, a.twoT, a.T, tid);
+    ok = wait_mma(mbarR, phR);
+    if (ok) {
+      resplit();
+      fence_before_sync();
+      __syncthreads();
     }
-    if (!mbar_wait_bounded(mbar, phase, kMaxPolls)) *abort_s = 1;
-    phase ^= 1;
-    fence_after_sync();
-    if (__syncthreads_or(*abort_s)) {
-      ok = false;
-      break;
-    }
-
-    // ---- demodulate: lane m = c * 32 + x (c = q), rows y in [h * BYH, (h+1) * BYH).
-    {
-      const int x = lane;
-      const float dn = a.d[n];
-      const int trig = q & 1;  // 0: cos (G_r, F_r), 1: sin (G_i, F_i)
-      const unsigned short *cen = tileT + (x + W) * kPT + W + h * BYH;
-#pragma unroll
-      for (int y0 = 0; y0 < BYH; y0 += 16) {
-        uint32_t v[16];
-        tmem_ld_x16(tmem + lane_base + kD2 + (uint32_t)(h * BYH + y0), v);
-        tmem_ld_wait();
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const float2 cs = *reinterpret_cast<const float2 *>(Lc + cen[y0 + j]);
-          const float t = trig ? cs.y : cs.x;
-          part[y0 + j] = fmaf(dn * t, __uint_as_float(v[j]), part[y0 + j]);
-        }
+    for (int n = 0; n < a.K && ok; ++n) {
+      if (col_issuer) issue_col();  // C(n): A2 -> D2
+      if (n + 1 < a.K) modulate();  // A1 <- harmonic n+1 (R(n) has finished)
+      fence_before_sync();
+      __syncthreads();
+      if (n + 1 < a.K && row_issuer) issue_row();  // R(n+1): A1 -> D1
+      if (!(ok = wait_mma(mbarC, phC))) break;
+      demod(n);  // D2, table n
+      fence_before_sync();
+      __syncthreads();
+      if (n + 2 < a.K) build_lut<BF>(lut16, lutf + (n & 1) * kLutStride, n + 2, a.twoT, a.T, tid);
+      if (n + 1 < a.K) {
+        if (!(ok = wait_mma(mbarR, phR))) break;
+        resplit();  // D1 -> A2 (C(n) has finished)
+        fence_before_sync();
+        __syncthreads();
       }
     }
-    fence_before_sync();
-    __syncthreads();
   }
 
   // ---- combine the four channel partials and write fhat = P / Q.
   if (ok) {
     float *comb = reinterpret_cast<float *>(A2);  // [c][y][x], 4 * BY * 32 floats
+    const int x = 8 * q + (lane >> 2), c = lane & 3;
 #pragma unroll
-    for (int j = 0; j < BYH; ++j) comb[(q * BY + h * BYH + j) * kBX + lane] = part[j];
+    for (int j = 0; j < BYH; ++j) comb[(c * BY + h * BYH + j) * kBX + x] = part[j];
     __syncthreads();
     for (int e = tid; e < BY * kBX; e += kNT) {
-      const int y = e / kBX, x = e - y * kBX;
-      const int iy = ty0 + y, ix = tx0 + x;
+      const int y = e / kBX, xx = e - y * kBX;
+      const int iy = ty0 + y, ix = tx0 + xx;
       if (iy < H && ix < Wd) {
-        const float Q = comb[(0 * BY + y) * kBX + x] + comb[(1 * BY + y) * kBX + x];
-        const float P = comb[(2 * BY + y) * kBX + x] + comb[(3 * BY + y) * kBX + x];
+        const float Q = comb[(0 * BY + y) * kBX + xx] + comb[(1 * BY + y) * kBX + xx];
+        const float P = comb[(2 * BY + y) * kBX + xx] + comb[(3 * BY + y) * kBX + xx];
         *reinterpret_cast<float *>(reinterpret_cast<char *>(a.out) + (size_t)iy * a.out_pitch +
                                    (size_t)ix * sizeof(float)) = P / Q;
       }
@@ -407,14 +466,27 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc_u8_kernel(const __grid_constant
   if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
-template <int BF, int NSPLIT, int BY, int WCAP>
+#ifndef FBF_TC_NBR
+#define FBF_TC_NBR 32
+#endif
+#ifndef FBF_TC_NBC_96
+#define FBF_TC_NBC_96 32
+#endif
+#ifndef FBF_TC_NBC_64
+#define FBF_TC_NBC_64 16
+#endif
+#ifndef FBF_TC_PIPE
+#define FBF_TC_PIPE 1  // W <= 16: pipelined schedule (A1, D1, D2 disjoint in TMEM)
+#endif
+
+template <int BF, int NSPLIT, int BY, int WCAP, int NBR, int NBC, int PIPE>
 fbf_status launch_tc_cfg(const FilterArgs &a0, cudaStream_t s) {
   FilterArgs a = a0;
-  const TcLayout Ly = tc_layout(a.W, WCAP);
+  const TcLayout Ly = tc_layout(a.W, WCAP, NBR, NBC);
   a.tiles_x = (a.Wd + kBX - 1) / kBX;
   const int tiles_y = (a.H + BY - 1) / BY;
   a.ntiles = a.tiles_x * tiles_y;
-  auto kern = fbf_tc_u8_kernel<BF, NSPLIT, BY, WCAP>;
+  auto kern = fbf_tc_u8_kernel<BF, NSPLIT, BY, WCAP, NBR, NBC, PIPE>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Ly.bytes) != cudaSuccess)
     return FBF_ERR_CUDA;
   kern<<<a.ntiles, kNT, Ly.bytes, s>>>(a);
@@ -426,8 +498,12 @@ fbf_status launch_tc_cfg(const FilterArgs &a0, cudaStream_t s) {
 // bf16 != 0: BF16 operands with split weights (3 products per step);
 // otherwise FP16 operands, split data, single weights (2 products).
 fbf_status launch_tc_u8(const FilterArgs &a, int bf16, cudaStream_t s) {
-  if (a.W <= 16) return bf16 ? launch_tc_cfg<1, 3, 96, 16>(a, s) : launch_tc_cfg<0, 2, 96, 16>(a, s);
-  if (a.W <= 32) return bf16 ? launch_tc_cfg<1, 3, 64, 32>(a, s) : launch_tc_cfg<0, 2, 64, 32>(a, s);
+  if (a.W <= 16)
+    return bf16 ? launch_tc_cfg<1, 3, 96, 16, FBF_TC_NBR, FBF_TC_NBC_96, FBF_TC_PIPE>(a, s)
+                : launch_tc_cfg<0, 2, 96, 16, FBF_TC_NBR, FBF_TC_NBC_96, FBF_TC_PIPE>(a, s);
+  if (a.W <= 32)
+    return bf16 ? launch_tc_cfg<1, 3, 64, 32, FBF_TC_NBR, FBF_TC_NBC_64, 0>(a, s)
+                : launch_tc_cfg<0, 2, 64, 32, FBF_TC_NBR, FBF_TC_NBC_64, 0>(a, s);
   return FBF_ERR_RANGE;
 }
 
