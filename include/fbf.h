@@ -133,7 +133,7 @@ fbf_status fbf_fit_coeffs(fbf_range_kernel kernel, double sigma_r, double T, dou
  *              in_pitch bytes (>= Wd * element size)
  *   dtype      FBF_U8: values 0..255, coeffs->T must be an integer >= 1
  *              (the phase n*omega*f is reduced exactly in integers);
- *              FBF_F32: any finite values (a separate path; see status)
+ *              FBF_F32: any finite values, any T > 0; FP32 form only, W <= 16
  *   d_out      device FP32 output, H x Wd, row pitch out_pitch bytes; must not
  *              overlap d_in
  *   stream     CUDA stream (0 = legacy default stream)
@@ -144,6 +144,30 @@ fbf_status fbf_fit_coeffs(fbf_range_kernel kernel, double sigma_r, double T, dou
  */
 fbf_status fbf_filter(const fbf_params *p, const void *d_in, fbf_dtype dtype, int H, int Wd,
                       size_t in_pitch, float *d_out, size_t out_pitch, cudaStream_t stream);
+
+/*
+ * fbf_filter_backward -- gradient of L = sum_i g(i) fhat(i) with respect to the
+ * input image f, where fhat is eq. (9) computed by fbf_filter (FP32 form,
+ * FBF_F32 input).  T, omega and the coefficients are constants.
+ *
+ * With a = g / Q and b = g fhat / Q, f(m) enters eq. (9) both as a neighbour
+ * and as the centre; per harmonic n the derivative takes the forward channels
+ * Fbar_n, Gbar_n (recomputed per tile, not stored) and the transposed
+ * convolutions of a e^{-i n w f} and b e^{-i n w f}: eight real channels.
+ * Under REFLECT the transposed border is exact (mirrored contributions are
+ * folded back onto their source pixels).
+ *
+ *   d_in       FP32 image (H x Wd), row pitch `pitch` bytes (multiple of 4)
+ *   d_gout     FP32 upstream gradient g, same shape and pitch
+ *   d_out_fwd  ignored (may be NULL): Q is needed, so the forward is recomputed
+ *   d_gin      FP32 output dL/df, same shape and pitch
+ * Allocates its scratch (8 bytes per pixel, plus (H+2W)(Wd+2W) floats under
+ * REFLECT) stream-ordered with cudaMallocAsync / cudaFreeAsync on `stream`.
+ * W <= 16.  Returns FBF_ERR_UNSUPPORTED for the tensor-core forms.
+ */
+fbf_status fbf_filter_backward(const fbf_params *p, const float *d_in, const float *d_gout,
+                               const float *d_out_fwd, float *d_gin, int H, int Wd, size_t pitch,
+                               cudaStream_t stream);
 
 /* Half window actually used for the parameters (W, or ceil(3 sigma_s) when
  * W <= 0), or -1 when invalid.  Host only. */

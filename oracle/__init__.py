@@ -65,6 +65,8 @@ def _load():
             lib.orc_alg1.restype = i
             lib.orc_grad_direct.argtypes = [dp, dp, i, i, dp, i, i, dp, i, d, dp]
             lib.orc_grad_direct.restype = None
+            lib.orc_grad_at.argtypes = [dp, dp, i, i, dp, i, i, dp, i, d, ip, ip, lp, dp]
+            lib.orc_grad_at.restype = None
             _lib = lib
     return _lib
 
@@ -217,6 +219,21 @@ def grad_direct(f, g, w1, border: int, d, T: float):
     out = np.empty((H, Wd), np.float64)
     _load().orc_grad_direct(_dp(f), _dp(g), H, Wd, _dp(w1), W, int(border), _dp(d), len(d),
                             float(T), _dp(out))
+    return out
+
+
+def grad_at(f, g, w1, border: int, d, T: float, points):
+    """The gradient of grad_direct evaluated at the given pixels only."""
+    f = _img(f)
+    g = _img(g)
+    H, Wd = f.shape
+    w1 = np.ascontiguousarray(w1, np.float64)
+    W = (len(w1) - 1) // 2
+    d = np.ascontiguousarray(d, np.float64)
+    ys, xs, n = _points(points)
+    out = np.empty(n, np.float64)
+    _load().orc_grad_at(_dp(f), _dp(g), H, Wd, _dp(w1), W, int(border), _dp(d), len(d), float(T),
+                        _ip(ys), _ip(xs), n, _dp(out))
     return out
 
 

@@ -18,6 +18,7 @@
  *                      range kernel, or eq. (9) with phi_N
  *   orc_alg1           Algorithm 1 in the paper's complex notation, eqs. (4)-(5)
  *   orc_grad_direct    d/df(m) of sum_i g(i) fhat(i), fhat from eq. (9)
+ *   orc_grad_at        the same derivative at sampled pixels only
  *
  * The fit uses Householder QR, deliberately not the modified Gram-Schmidt
  * recursion of Algorithm 2, so the two are independent: the least-squares
@@ -428,4 +429,83 @@ void orc_grad_direct(const double *f, const double *g, int H, int Wd, const doub
   free(P);
   free(Q);
   free(out);
+}
+
+/* The same derivative as orc_grad_direct, evaluated only at the npts pixels
+ * (ys[p], xs[p]), for images too large for the full computation.  For a
+ * sampled m it enumerates the pairs (i, j) whose (mapped) neighbour index
+ * i - j is m: under REFLECT every extended position q in [-W, H+W) x [-W, Wd+W)
+ * that reflects onto m and every i in the image with i - q in [-W, W]^2; under
+ * TRUNCATE q = m only.  a(i) = g(i)/Q(i), b(i) = g(i) fhat(i)/Q(i) come from
+ * eq. (9) evaluated directly at each i.  Adds the centre term of i = m. */
+static void orc_pq_at(const double *f, int H, int Wd, const double *w1, int W, int border, const double *d,
+                      int K, double T, long iy, long ix, double *P, double *Q) {
+  double fc = f[iy * Wd + ix], num = 0.0, den = 0.0;
+  for (int jy = -W; jy <= W; ++jy) {
+    long sy = iy - jy;
+    if (border == ORC_BORDER_REFLECT) sy = orc_reflect(sy, H);
+    else if (sy < 0 || sy >= H) continue;
+    for (int jx = -W; jx <= W; ++jx) {
+      long sx = ix - jx;
+      if (border == ORC_BORDER_REFLECT) sx = orc_reflect(sx, Wd);
+      else if (sx < 0 || sx >= Wd) continue;
+      double u = f[sy * Wd + sx], ph = orc_phi_n(d, K, T, u - fc), wj = w1[jy + W] * w1[jx + W];
+      num += wj * ph * u;
+      den += wj * ph;
+    }
+  }
+  *P = num;
+  *Q = den;
+}
+
+void orc_grad_at(const double *f, const double *g, int H, int Wd, const double *w1, int W, int border,
+                 const double *d, int K, double T, const int *ys, const int *xs, long npts, double *out) {
+#pragma omp parallel for schedule(dynamic, 1)
+  for (long p = 0; p < npts; ++p) {
+    long my = ys[p], mx = xs[p];
+    double fm = f[my * Wd + mx], acc = 0.0;
+    /* 1-D preimages of my / mx among the extended positions */
+    long qy[64], qx[64];
+    int ny = 0, nx = 0;
+    if (border == ORC_BORDER_REFLECT) {
+      for (long q = -W; q < H + W && ny < 64; ++q)
+        if (orc_reflect(q, H) == my) qy[ny++] = q;
+      for (long q = -W; q < Wd + W && nx < 64; ++q)
+        if (orc_reflect(q, Wd) == mx) qx[nx++] = q;
+    } else {
+      qy[ny++] = my;
+      qx[nx++] = mx;
+    }
+    for (int a1 = 0; a1 < ny; ++a1)
+      for (int a2 = 0; a2 < nx; ++a2)
+        for (int jy = -W; jy <= W; ++jy)
+          for (int jx = -W; jx <= W; ++jx) {
+            long iy = qy[a1] + jy, ix = qx[a2] + jx; /* i - j = q */
+            if (iy < 0 || iy >= H || ix < 0 || ix >= Wd) continue;
+            double Pi, Qi;
+            orc_pq_at(f, H, Wd, w1, W, border, d, K, T, iy, ix, &Pi, &Qi);
+            double gi = g[iy * Wd + ix], ai = gi / Qi, bi = gi * (Pi / Qi) / Qi;
+            double t = fm - f[iy * Wd + ix], wj = w1[jy + W] * w1[jx + W];
+            double ph = orc_phi_n(d, K, T, t), dph = orc_dphi_n(d, K, T, t);
+            acc += wj * (ai * (ph + fm * dph) - bi * dph);
+          }
+    /* centre term, i = m */
+    double Pm, Qm;
+    orc_pq_at(f, H, Wd, w1, W, border, d, K, T, my, mx, &Pm, &Qm);
+    double gm = g[my * Wd + mx], am = gm / Qm, bm = gm * (Pm / Qm) / Qm;
+    for (int jy = -W; jy <= W; ++jy) {
+      long sy = my - jy;
+      if (border == ORC_BORDER_REFLECT) sy = orc_reflect(sy, H);
+      else if (sy < 0 || sy >= H) continue;
+      for (int jx = -W; jx <= W; ++jx) {
+        long sx = mx - jx;
+        if (border == ORC_BORDER_REFLECT) sx = orc_reflect(sx, Wd);
+        else if (sx < 0 || sx >= Wd) continue;
+        double u = f[sy * Wd + sx], t = u - fm, wj = w1[jy + W] * w1[jx + W];
+        double dph = orc_dphi_n(d, K, T, t);
+        acc += wj * (-am * u * dph + bm * dph);
+      }
+    }
+    out[p] = acc;
+  }
 }

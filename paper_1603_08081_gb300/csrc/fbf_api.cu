@@ -77,10 +77,33 @@ extern "C" fbf_status fbf_filter(const fbf_params *p, const void *d_in, fbf_dtyp
   const fbf_form form = p->form;
   if (form != FBF_FORM_AUTO && form != FBF_FORM_FP32 && form != FBF_FORM_TC_FP16 && form != FBF_FORM_TC_BF16)
     return FBF_ERR_INVALID_ARGUMENT;
-  if (dtype != FBF_U8) return FBF_ERR_UNSUPPORTED;
+  if (dtype == FBF_F32) {
+    if (form == FBF_FORM_TC_FP16 || form == FBF_FORM_TC_BF16) return FBF_ERR_UNSUPPORTED;
+    if (a.W > f32_wmax()) return FBF_ERR_RANGE;
+    return launch_fp32_f32(a, stream);
+  }
   if (form == FBF_FORM_TC_FP16) return launch_tc_u8(a, 0, stream);
   if (form == FBF_FORM_TC_BF16) return launch_tc_u8(a, 1, stream);
   return launch_fp32_u8(a, stream);
+}
+
+extern "C" fbf_status fbf_filter_backward(const fbf_params *p, const float *d_in, const float *d_gout,
+                                          const float *d_out_fwd, float *d_gin, int H, int Wd, size_t pitch,
+                                          cudaStream_t stream) {
+  (void)d_out_fwd;  // the forward is recomputed: Q is needed, not only fhat
+  FilterArgs a;
+  fbf_status st = pack_filter_args(p, d_in, FBF_F32, H, Wd, pitch, d_gin, pitch, &a);
+  if (st != FBF_OK) return st;
+  if (H == 0 || Wd == 0) return FBF_OK;
+  if (!d_gout) return FBF_ERR_INVALID_ARGUMENT;
+  if (p->form != FBF_FORM_AUTO && p->form != FBF_FORM_FP32) return FBF_ERR_UNSUPPORTED;
+  if (a.W > f32_wmax()) return FBF_ERR_RANGE;
+  const size_t bytes = backward_scratch_bytes(H, Wd, a.W, a.border);
+  void *scratch = nullptr;
+  if (cudaMallocAsync(&scratch, bytes, stream) != cudaSuccess) return FBF_ERR_CUDA;
+  st = launch_backward(a, d_gout, pitch, d_gin, pitch, scratch, stream);
+  if (cudaFreeAsync(scratch, stream) != cudaSuccess && st == FBF_OK) st = FBF_ERR_CUDA;
+  return st;
 }
 
 extern "C" fbf_status fbf_device_error(unsigned int *code) {

@@ -1,0 +1,348 @@
+// FP32-input forward filter and the hand-written adjoint (gradient with respect
+// to the input image) of the shiftable bilateral filter.
+//
+// Forward (eq. (9) via Algorithm 1) for float images: the modulated channels
+// (cos, sin, f cos, f sin)(n w f) cannot come from an 8-bit table, so each
+// harmonic first writes them for every halo-tile pixel (sincospi of n f / T)
+// into a transposed shared-memory channel tile; the row and column passes are
+// the same rotating-window FIR as the uint8 kernel.
+//
+// Adjoint.  With fhat = P / Q, L = sum_i g(i) fhat(i), a = g / Q, b = g fhat / Q,
+// phi_N(t) = Re sum_n d_n e^{i n w t} (eq. (6)) and
+//   Fbar_n = w * (f e^{i n w f}),  Gbar_n = w * e^{i n w f}        (eq. (5)),
+//   Abar_n = w^T * (a e^{-i n w f}),  Bbar_n = w^T * (b e^{-i n w f}),
+// the derivative of eq. (9) with respect to f(m) is
+//   dL/df(m) = Re sum_n d_n [ e^{i n w f_m} ((1 + i n w f_m) Abar_n(m) - i n w Bbar_n(m))
+//                            - i n w e^{-i n w f_m} (a(m) Fbar_n(m) - b(m) Gbar_n(m)) ],
+// the first bracket from f(m) as a neighbour, the second from f(m) as the
+// centre.  w^T is the transpose of the bordered convolution: under TRUNCATE a
+// zero-padded correlation (= convolution, w is symmetric); under REFLECT the
+// zero-padded correlation evaluated on the extended grid [-W, H+W) x [-W, Wd+W)
+// and folded back onto the mirrored source pixels.  Because the demodulation
+// factor depends only on the source pixel, the whole per-position sum can be
+// formed on the extended grid first and folded once at the end.
+//
+// Pass 1 (this file's forward kernel with g given) writes (a, b) per pixel to
+// a scratch map; pass 2 recomputes the forward channels per tile (no storage of
+// the 4K channels) next to the four adjoint channels, eight real channels per
+// harmonic in two FIR sweeps; pass 3 folds (REFLECT only).
+#include <cuda_runtime.h>
+
+#include "fbf_common.cuh"
+#include "fbf_fp32_kernel.cuh"
+#include "fbf_internal.h"
+
+namespace fbf {
+namespace {
+
+constexpr int kBT = 32;       // output tile edge
+constexpr int kWcapF = 16;    // compiled window limit of the FP32-input kernels
+constexpr int kNTf = 256;
+constexpr int kHYP = 64;      // padded halo rows: 32 + 2 * 16
+constexpr int kHXA = 32 + 2 * kWcapF + kRun;  // halo columns incl. the FIR over-read
+constexpr int kPR = kBT + 1;  // row buffer pitch (odd, in 16-byte units)
+
+enum { kModeForward = 0, kModeAdjoint = 1 };
+
+struct F32Args {
+  const float *g;     // upstream gradient (forward with ab != null, adjoint)
+  float2 *ab;         // forward: (a, b) map out (nullable); adjoint: in
+  float *gext;        // adjoint: extended-grid gradient (REFLECT) or the gradient (TRUNCATE)
+  size_t g_pitch;     // bytes
+  int ext_off;        // adjoint: W under REFLECT (grid origin at -W), 0 under TRUNCATE
+  int ext_h, ext_w;   // adjoint: grid size
+  size_t gext_pitch;  // bytes
+};
+
+struct F32Smem {
+  ulonglong2 chan[kHXA * kHYP];        // transposed channel tile, 4 channels per pixel
+  ulonglong2 rowbuf[(kHYP + 1) * kPR];  // row-pass output
+  float fT[kHXA * kHYP];               // halo tile of f (forward border semantics), NaN = absent
+  float2 abT[kHXA * kHYP];             // adjoint: halo tile of (a, b), zero outside the image
+};
+
+__device__ __forceinline__ float ldf(const float *base, size_t pitch, int y, int x) {
+  return __ldg(reinterpret_cast<const float *>(reinterpret_cast<const char *>(base) + (size_t)y * pitch) + x);
+}
+
+// MODE forward: out = fhat (nullable), ab = (g/Q, g fhat/Q) (nullable).
+// MODE adjoint: gext = per-position gradient on the grid described by F32Args.
+template <int MODE>
+__global__ void __launch_bounds__(kNTf, 1) fbf_f32_kernel(const __grid_constant__ FilterArgs a,
+                                                          const __grid_constant__ F32Args x) {
+  constexpr int NW = kNTf / 32, NXR = kBT / kRun, NYR = kBT / kRun;
+  constexpr int UPW = NYR / NW;  // column units per warp (1 column group of 32)
+  static_assert(NYR % NW == 0 || NW % NYR == 0, "units");
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  F32Smem &S = *reinterpret_cast<F32Smem *>(smem_raw);
+
+  const int W = a.W, taps = 2 * W + 1;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int H = a.H, Wd = a.Wd;
+  const int tile_y = blockIdx.x / a.tiles_x, tile_x = blockIdx.x - tile_y * a.tiles_x;
+  const int off = MODE == kModeAdjoint ? x.ext_off : 0;
+  const int py0 = tile_y * kBT - off, px0 = tile_x * kBT - off;  // image coords of output (0, 0)
+  const int HY = kBT + 2 * W, HX = kBT + 2 * W;
+  const bool reflect = a.border == FBF_BORDER_REFLECT;
+  const float invT = 1.0f / a.T;
+
+  // Stage f (forward border semantics) and, for the adjoint, (a, b) (zero outside).
+  for (int e = tid; e < kHXA * kHYP; e += kNTf) {
+    const int ex = e / kHYP, ey = e - ex * kHYP;
+    float fv = __int_as_float(0x7fc00000);  // absent
+    float2 abv = make_float2(0.f, 0.f);
+    if (ey < HY && ex < HX) {
+      int iy = py0 - W + ey, ix = px0 - W + ex;
+      const bool inside = iy >= 0 && iy < H && ix >= 0 && ix < Wd;
+      if (MODE == kModeAdjoint && inside) abv = x.ab[(size_t)iy * Wd + ix];
+      if (reflect) {
+        fv = ldf(static_cast<const float *>(a.in), a.in_pitch, reflect_index(iy, H), reflect_index(ix, Wd));
+      } else if (inside) {
+        fv = ldf(static_cast<const float *>(a.in), a.in_pitch, iy, ix);
+      }
+    }
+    S.fT[ex * kHYP + ey] = fv;
+    if (MODE == kModeAdjoint) S.abT[ex * kHYP + ey] = abv;
+  }
+  __syncthreads();
+
+  float acc[UPW > 0 ? UPW : 1][kRun][2];  // forward: P, Q; adjoint: neighbour, centre terms
+#pragma unroll
+  for (int u = 0; u < (UPW > 0 ? UPW : 1); ++u)
+#pragma unroll
+    for (int o = 0; o < kRun; ++o) acc[u][o][0] = acc[u][o][1] = 0.f;
+
+  // One FIR sweep of the four channels in S.chan: row pass to S.rowbuf, column
+  // pass into `res` for this thread's column units.
+  auto sweep = [&](Quad (&res)[UPW > 0 ? UPW : 1][kRun]) {
+    for (int u = warp; u < (kHYP / 32) * NXR; u += NW) {
+      const int g = u / NXR, xr = u - g * NXR;
+      const int ey = g * 32 + lane, ox0 = xr * kRun;
+      const ulonglong2 *cp = S.chan + ox0 * kHYP + ey;
+      Quad accq[kRun];
+      fir_run<0>(a.w2, taps,
+                 [&](int p) {
+                   const ulonglong2 e = cp[p * kHYP];
+                   return Quad{e.x, e.y};
+                 },
+                 accq);
+      ulonglong2 *rb = S.rowbuf + ey * kPR + ox0;
+#pragma unroll
+      for (int o = 0; o < kRun; ++o) rb[o] = make_ulonglong2(accq[o].a, accq[o].b);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < (UPW > 0 ? UPW : 1); ++q) {
+      const int yr = warp + q * NW;
+      if (yr < NYR) {
+        const ulonglong2 *cpn = S.rowbuf + yr * kRun * kPR + lane;
+        fir_run<0>(a.w2, taps,
+                   [&](int p) {
+                     const ulonglong2 e = cpn[p * kPR];
+                     return Quad{e.x, e.y};
+                   },
+                   res[q]);
+      }
+    }
+  };
+
+  for (int n = 0; n < a.K; ++n) {
+    const float dn = a.d[n];
+    const float nw = (float)n * 3.14159265358979323846f * invT;  // n * omega
+    // ---- forward channels (cos, sin, f cos, f sin)(n w f) of every halo pixel.
+    for (int e = tid; e < kHXA * kHYP; e += kNTf) {
+      const float fv = S.fT[e];
+      float sn = 0.f, cs = 0.f, fval = 0.f;
+      if (fv == fv) {  // present
+        sincospif((float)n * fv * invT, &sn, &cs);
+        fval = fv;
+      }
+      S.chan[e] = make_ulonglong2(pack_f(cs, sn), pack_f(fval * cs, fval * sn));
+    }
+    __syncthreads();
+    Quad fwd[UPW > 0 ? UPW : 1][kRun];
+    sweep(fwd);
+    // Centre phase (cos, sin)(n w f) of every output pixel of this thread.
+#pragma unroll
+    for (int q = 0; q < (UPW > 0 ? UPW : 1); ++q) {
+      const int yr = warp + q * NW;
+      if (yr >= NYR) continue;
+#pragma unroll
+      for (int o = 0; o < kRun; ++o) {
+        const ulonglong2 c = S.chan[(lane + W) * kHYP + yr * kRun + o + W];
+        const float cs = lo_f(c.x), sn = hi_f(c.x);
+        const float Gr = lo_f(fwd[q][o].a), Gi = hi_f(fwd[q][o].a);
+        const float Fr = lo_f(fwd[q][o].b), Fi = hi_f(fwd[q][o].b);
+        if (MODE == kModeForward) {
+          acc[q][o][0] = fmaf(dn, fmaf(cs, Fr, sn * Fi), acc[q][o][0]);  // P
+          acc[q][o][1] = fmaf(dn, fmaf(cs, Gr, sn * Gi), acc[q][o][1]);  // Q
+        } else {
+          // centre term: d_n n w (cos V_i - sin V_r), V = a Fbar - b Gbar
+          const float2 abv = S.abT[(lane + W) * kHYP + yr * kRun + o + W];
+          const float Vr = abv.x * Fr - abv.y * Gr, Vi = abv.x * Fi - abv.y * Gi;
+          acc[q][o][1] = fmaf(dn * nw, cs * Vi - sn * Vr, acc[q][o][1]);
+        }
+      }
+    }
+    __syncthreads();
+    if (MODE == kModeAdjoint) {
+      // ---- adjoint channels: (a cos, -a sin, b cos, -b sin)(n w f), zero outside the image.
+      for (int e = tid; e < kHXA * kHYP; e += kNTf) {
+        const float fv = S.fT[e];
+        const float2 abv = S.abT[e];
+        float sn = 0.f, cs = 0.f;
+        if (fv == fv) sincospif((float)n * fv * invT, &sn, &cs);
+        S.chan[e] = make_ulonglong2(pack_f(abv.x * cs, -abv.x * sn), pack_f(abv.y * cs, -abv.y * sn));
+      }
+      __syncthreads();
+      Quad adj[UPW > 0 ? UPW : 1][kRun];
+      sweep(adj);
+#pragma unroll
+      for (int q = 0; q < (UPW > 0 ? UPW : 1); ++q) {
+        const int yr = warp + q * NW;
+        if (yr >= NYR) continue;
+#pragma unroll
+        for (int o = 0; o < kRun; ++o) {
+          const float fm = S.fT[(lane + W) * kHYP + yr * kRun + o + W];
+          float sn = 0.f, cs = 0.f;
+          if (fm == fm) sincospif((float)n * fm * invT, &sn, &cs);
+          const float Ar = lo_f(adj[q][o].a), Ai = hi_f(adj[q][o].a);
+          const float Br = lo_f(adj[q][o].b), Bi = hi_f(adj[q][o].b);
+          // u = (1 + i n w f) A - i n w B;  Re[(cos + i sin) u]
+          const float ur = Ar - nw * fm * Ai + nw * Bi;
+          const float ui = Ai + nw * fm * Ar - nw * Br;
+          acc[q][o][0] = fmaf(dn, cs * ur - sn * ui, acc[q][o][0]);
+        }
+      }
+      __syncthreads();
+    }
+  }
+
+  // ---- outputs
+#pragma unroll
+  for (int q = 0; q < (UPW > 0 ? UPW : 1); ++q) {
+    const int yr = warp + q * NW;
+    if (yr >= NYR) continue;
+#pragma unroll
+    for (int o = 0; o < kRun; ++o) {
+      const int oy = yr * kRun + o, ox = lane;
+      if (MODE == kModeForward) {
+        const int iy = py0 + oy, ix = px0 + ox;
+        if (iy < H && ix < Wd) {
+          const float P = acc[q][o][0], Q = acc[q][o][1];
+          const float fh = P / Q;
+          if (a.out)
+            *reinterpret_cast<float *>(reinterpret_cast<char *>(a.out) + (size_t)iy * a.out_pitch +
+                                       (size_t)ix * sizeof(float)) = fh;
+          if (x.ab) {
+            const float gv = ldf(x.g, x.g_pitch, iy, ix);
+            x.ab[(size_t)iy * Wd + ix] = make_float2(gv / Q, gv * fh / Q);
+          }
+        }
+      } else {
+        const int gy = tile_y * kBT + oy, gx = tile_x * kBT + ox;  // grid coordinates
+        if (gy < x.ext_h && gx < x.ext_w) {
+          const int iy = gy - off, ix = gx - off;
+          const bool inside = iy >= 0 && iy < H && ix >= 0 && ix < Wd;
+          const float v = acc[q][o][0] + (inside ? acc[q][o][1] : 0.f);
+          *reinterpret_cast<float *>(reinterpret_cast<char *>(x.gext) + (size_t)gy * x.gext_pitch +
+                                     (size_t)gx * sizeof(float)) = v;
+        }
+      }
+    }
+  }
+}
+
+// grad(m) = sum over extended positions p with reflect(p) = m of gext(p).
+__global__ void fbf_fold_kernel(const float *__restrict__ gext, size_t gext_pitch, int W, int H, int Wd,
+                                float *grad, size_t grad_pitch) {
+  const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+  if (ix >= Wd) return;
+  for (int iy = blockIdx.y; iy < H; iy += gridDim.y) {
+  float s = 0.f;
+  // Preimages of m in [-W, N + W): p = m + 2kN and p = -1 - m + 2kN.
+  const int ky = W / (2 * H) + 1, kx = W / (2 * Wd) + 1;
+  for (int sy = 0; sy < 2; ++sy)
+    for (int k1 = -ky; k1 <= ky; ++k1) {
+      const int py = (sy ? -1 - iy : iy) + 2 * k1 * H;
+      if (py < -W || py >= H + W) continue;
+      for (int sx = 0; sx < 2; ++sx)
+        for (int k2 = -kx; k2 <= kx; ++k2) {
+          const int px = (sx ? -1 - ix : ix) + 2 * k2 * Wd;
+          if (px < -W || px >= Wd + W) continue;
+          s += *(reinterpret_cast<const float *>(reinterpret_cast<const char *>(gext) + (size_t)(py + W) * gext_pitch) +
+                 (px + W));
+        }
+    }
+  *reinterpret_cast<float *>(reinterpret_cast<char *>(grad) + (size_t)iy * grad_pitch + (size_t)ix * sizeof(float)) = s;
+  }
+}
+
+template <int MODE>
+fbf_status launch_f32(const FilterArgs &a0, const F32Args &x, int grid_h, int grid_w, cudaStream_t s) {
+  FilterArgs a = a0;
+  a.tiles_x = (grid_w + kBT - 1) / kBT;
+  a.ntiles = a.tiles_x * ((grid_h + kBT - 1) / kBT);
+  auto kern = fbf_f32_kernel<MODE>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(F32Smem)) != cudaSuccess)
+    return FBF_ERR_CUDA;
+  kern<<<a.ntiles, kNTf, sizeof(F32Smem), s>>>(a, x);
+  return cuda_status(cudaGetLastError());
+}
+
+}  // namespace
+
+int f32_wmax() { return kWcapF; }
+
+fbf_status launch_fp32_f32(const FilterArgs &a, cudaStream_t s) {
+  if (a.W > kWcapF) return FBF_ERR_RANGE;
+  F32Args x{};
+  return launch_f32<kModeForward>(a, x, a.H, a.Wd, s);
+}
+
+size_t backward_scratch_bytes(int H, int Wd, int W, int border) {
+  const size_t ab = (size_t)H * Wd * sizeof(float2);
+  const size_t ge = border == FBF_BORDER_REFLECT ? (size_t)(H + 2 * W) * (Wd + 2 * W) * sizeof(float) : 0;
+  return ((ab + 255) & ~(size_t)255) + ge;
+}
+
+fbf_status launch_backward(const FilterArgs &a, const float *g, size_t g_pitch, float *gin, size_t gin_pitch,
+                           void *scratch, cudaStream_t s) {
+  if (a.W > kWcapF) return FBF_ERR_RANGE;
+  const int H = a.H, Wd = a.Wd, W = a.W;
+  float2 *ab = static_cast<float2 *>(scratch);
+  const size_t ab_bytes = (((size_t)H * Wd * sizeof(float2)) + 255) & ~(size_t)255;
+  // Pass 1: forward with (a, b) out.
+  F32Args x1{};
+  x1.g = g;
+  x1.g_pitch = g_pitch;
+  x1.ab = ab;
+  FilterArgs af = a;
+  af.out = nullptr;
+  fbf_status st = launch_f32<kModeForward>(af, x1, H, Wd, s);
+  if (st != FBF_OK) return st;
+  // Pass 2: adjoint on the extended grid (REFLECT) or the image (TRUNCATE).
+  F32Args x2{};
+  x2.ab = ab;
+  if (a.border == FBF_BORDER_REFLECT) {
+    x2.ext_off = W;
+    x2.ext_h = H + 2 * W;
+    x2.ext_w = Wd + 2 * W;
+    x2.gext = reinterpret_cast<float *>(static_cast<char *>(scratch) + ab_bytes);
+    x2.gext_pitch = (size_t)x2.ext_w * sizeof(float);
+  } else {
+    x2.ext_off = 0;
+    x2.ext_h = H;
+    x2.ext_w = Wd;
+    x2.gext = gin;
+    x2.gext_pitch = gin_pitch;
+  }
+  st = launch_f32<kModeAdjoint>(a, x2, x2.ext_h, x2.ext_w, s);
+  if (st != FBF_OK || a.border != FBF_BORDER_REFLECT) return st;
+  // Pass 3: fold the extended grid back onto the image.
+  dim3 grid((Wd + 127) / 128, H < 65535 ? H : 65535);
+  fbf_fold_kernel<<<grid, 128, 0, s>>>(x2.gext, x2.gext_pitch, W, H, Wd, gin, gin_pitch);
+  return cuda_status(cudaGetLastError());
+}
+
+}  // namespace fbf

@@ -83,11 +83,9 @@ struct Quad {
 
 __device__ __forceinline__ float lo_f(u64 x) { return __uint_as_float((unsigned)x); }
 __device__ __forceinline__ float hi_f(u64 x) { return __uint_as_float((unsigned)(x >> 32)); }
-#if !FBF_FIR_PACKED
 __device__ __forceinline__ u64 pack_f(float lo, float hi) {
   return (u64)__float_as_uint(lo) | ((u64)__float_as_uint(hi) << 32);
 }
-#endif
 
 
 // d = w * v + d on both halves of an f32x2 pair (one fma.rn.f32x2, or two

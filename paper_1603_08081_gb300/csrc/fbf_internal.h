@@ -49,6 +49,13 @@ fbf_status launch_fp32_u8(const FilterArgs &a, cudaStream_t s);
 fbf_status launch_tc_u8(const FilterArgs &a, int bf16, cudaStream_t s);
 fbf_status tc_read_clear_error(unsigned int *code);
 
+// FP32-input forward and the adjoint (fbf_f32.cu); W <= f32_wmax().
+int f32_wmax();
+fbf_status launch_fp32_f32(const FilterArgs &a, cudaStream_t s);
+size_t backward_scratch_bytes(int H, int Wd, int W, int border);
+fbf_status launch_backward(const FilterArgs &a, const float *g, size_t g_pitch, float *gin, size_t gin_pitch,
+                           void *scratch, cudaStream_t s);
+
 inline fbf_status cuda_status(cudaError_t e) { return e == cudaSuccess ? FBF_OK : FBF_ERR_CUDA; }
 
 }  // namespace fbf

@@ -63,6 +63,8 @@ def _load():
     lib.fbf_fit_coeffs.restype = i
     lib.fbf_filter.argtypes = [C.POINTER(fbf_params), p, i, i, i, sz, p, sz, p]
     lib.fbf_filter.restype = i
+    lib.fbf_filter_backward.argtypes = [C.POINTER(fbf_params), p, p, p, p, i, i, sz, p]
+    lib.fbf_filter_backward.restype = i
     lib.fbf_resolve_window.argtypes = [C.POINTER(fbf_params)]
     lib.fbf_resolve_window.restype = i
     lib.fbf_device_error.argtypes = [C.POINTER(C.c_uint)]
@@ -155,6 +157,55 @@ def fbf_filter(params: fbf_params, x, out=None, stream=None):
     if st != FBF_OK:
         raise FbfError(st, "fbf_filter")
     return out
+
+
+def fbf_filter_backward(params: fbf_params, x, g, grad=None, stream=None):
+    """dL/dx for L = sum(g * fbf_filter(params, x)); x and g float32 CUDA (H, W)."""
+    import torch
+
+    if x.dtype != torch.float32 or g.dtype != torch.float32 or not (x.is_cuda and g.is_cuda):
+        raise TypeError("fbf_filter_backward: x and g must be float32 CUDA tensors")
+    x = x.contiguous()
+    g = g.contiguous()
+    if g.shape != x.shape or x.dim() != 2:
+        raise ValueError("fbf_filter_backward: x and g must have the same 2-D shape")
+    if grad is None:
+        grad = torch.empty_like(x)
+    H, Wd = x.shape
+    st = lib.fbf_filter_backward(C.byref(params), C.c_void_p(x.data_ptr()), C.c_void_p(g.data_ptr()), None,
+                                 C.c_void_p(grad.data_ptr()), H, Wd, x.stride(0) * 4, _stream_handle(stream))
+    if st != FBF_OK:
+        raise FbfError(st, "fbf_filter_backward")
+    return grad
+
+
+def _autograd_function():
+    import torch
+
+    class FBFFunction(torch.autograd.Function):
+        """Differentiable shiftable bilateral filter (in x only): forward is
+        fbf_filter (FP32 form, float input), backward the hand-written adjoint."""
+
+        @staticmethod
+        def forward(ctx, x, params):
+            ctx.params = params
+            ctx.save_for_backward(x)
+            return fbf_filter(params, x.contiguous())
+
+        @staticmethod
+        def backward(ctx, g):
+            (x,) = ctx.saved_tensors
+            return fbf_filter_backward(ctx.params, x, g.contiguous().float()), None
+
+    return FBFFunction
+
+
+def __getattr__(name):
+    if name == "FBFFunction":
+        fn = _autograd_function()
+        globals()["FBFFunction"] = fn
+        return fn
+    raise AttributeError(name)
 
 
 def fbf_device_error() -> int:

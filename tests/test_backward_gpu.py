@@ -1,0 +1,160 @@
+"""GPU parity of the float-input forward and of the hand-written adjoint
+(fbf_filter_backward through the C ABI) against the FP64 oracle.
+
+Tolerances.  Forward: 0.5 gray contract scaled to the image range (T = 1 here:
+0.5 / 255), and the FP32 regression bound 1e-4 * T.  Gradient: FP32 sums of
+eight channels per harmonic with weights n*omega up to ~40; relative rounding
+~1e-6 per term, so 1e-3 of the largest gradient entry leaves a wide margin.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1603_08081_gb300.synth import make_grad, make_image_f32
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fbf():
+    import torch  # noqa: F401
+
+    from paper_1603_08081_gb300 import build
+
+    build.build()
+    from paper_1603_08081_gb300 import fbf as mod
+
+    return mod
+
+
+def _fit(fbf, sigma_r=0.1, T=1.0, eps=1e-3, levels=256):
+    return fbf.fbf_fit_coeffs("gaussian", sigma_r, T, eps, 0, levels)
+
+
+def _w1(sigma_s, W):
+    return O.weights_1d(O.SPATIAL_GAUSSIAN, sigma_s, W)
+
+
+def _bd(border):
+    return O.BORDER_REFLECT if border == "reflect" else O.BORDER_TRUNCATE
+
+
+def _cuda(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).cuda()
+
+
+@pytest.mark.parametrize("border", ["reflect", "truncate"])
+@pytest.mark.parametrize("shape,sigma_s", [((64, 64), 4.0), ((37, 53), 2.0), ((5, 7), 3.0), ((100, 33), 5.0),
+                                           ((1, 40), 1.0)])
+def test_float_forward_matches_oracle(fbf, border, shape, sigma_s):
+    import torch
+
+    img = make_image_f32(*shape, seed=1400)
+    c = _fit(fbf)
+    W = int(np.ceil(3 * sigma_s))
+    p = fbf.make_params(c, sigma_s, 0, "gaussian", border, "fp32")
+    y = fbf.fbf_filter(p, _cuda(img))
+    torch.cuda.synchronize()
+    ref = O.alg1(img.astype(np.float64), _w1(sigma_s, W), _bd(border), np.array(c.coefficients), 1.0)[0]
+    err = np.abs(y.cpu().numpy() - ref).max()
+    assert err <= 0.5 / 255 and err <= 1e-4, err
+
+
+def test_float_forward_arbitrary_T(fbf):
+    import torch
+
+    img = make_image_f32(48, 50, seed=3) * np.float32(2.5)
+    c = fbf.fbf_fit_coeffs("gaussian", 0.3, 2.5, 1e-4, 0, 300)
+    p = fbf.make_params(c, 2.0)
+    y = fbf.fbf_filter(p, _cuda(img))
+    torch.cuda.synchronize()
+    ref = O.alg1(img.astype(np.float64), _w1(2.0, 6), O.BORDER_REFLECT, np.array(c.coefficients), 2.5)[0]
+    assert np.abs(y.cpu().numpy() - ref).max() <= 2.5e-4
+
+
+@pytest.mark.parametrize("border", ["reflect", "truncate"])
+@pytest.mark.parametrize("shape,sigma_s,W", [((24, 30), 1.0, 3), ((17, 13), 2.0, 6), ((40, 36), 4.0, 12),
+                                             ((6, 9), 2.0, 6), ((9, 4), 1.0, 16)])
+def test_backward_matches_oracle_gradient(fbf, border, shape, sigma_s, W):
+    """Full FP64 gradient of sum(g * fhat), eq. (9), incl. windows wider than the image."""
+    import torch
+
+    img = make_image_f32(*shape, seed=1401)
+    g = make_grad(*shape, seed=1499)
+    c = _fit(fbf)
+    p = fbf.make_params(c, sigma_s, W, "gaussian", border, "fp32")
+    gr = fbf.fbf_filter_backward(p, _cuda(img), _cuda(g))
+    torch.cuda.synchronize()
+    ref = O.grad_direct(img.astype(np.float64), g.astype(np.float64), _w1(sigma_s, W), _bd(border),
+                        np.array(c.coefficients), 1.0)
+    got = gr.cpu().numpy()
+    assert np.all(np.isfinite(got))
+    assert np.abs(got - ref).max() <= 1e-3 * np.abs(ref).max(), (np.abs(got - ref).max(), np.abs(ref).max())
+
+
+def test_backward_512_sampled(fbf):
+    """One 512x512 image of the differentiation workload (sigma_s = 4, W = 12,
+    sigma_r = 0.1, T = 1, 256 levels, eps = 1e-3 -> K = 13): sampled pixels
+    (random, corners, edges) against the FP64 gradient at those pixels."""
+    import torch
+
+    img = make_image_f32(512, 512, seed=1400)
+    g = make_grad(512, 512, seed=1499)
+    c = _fit(fbf)
+    assert c.K == 13
+    p = fbf.make_params(c, 4.0)
+    gr = fbf.fbf_filter_backward(p, _cuda(img), _cuda(g))
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(7)
+    ys = np.concatenate([rng.integers(0, 512, 24), [0, 0, 511, 511, 5, 256, 500]])
+    xs = np.concatenate([rng.integers(0, 512, 24), [0, 511, 0, 511, 256, 3, 256]])
+    ref = O.grad_at(img.astype(np.float64), g.astype(np.float64), _w1(4.0, 12), O.BORDER_REFLECT,
+                    np.array(c.coefficients), 1.0, (ys, xs))
+    got = gr.cpu().numpy()[ys, xs]
+    scale = np.abs(gr.cpu().numpy()).max()
+    assert np.abs(got - ref).max() <= 1e-3 * scale
+
+
+def test_autograd_function_and_finite_differences(fbf):
+    """FBFFunction backward equals fbf_filter_backward, and agrees with central
+    differences of the GPU forward (FP32, h = 1e-3) at a few pixels."""
+    import torch
+
+    img = make_image_f32(32, 40, seed=1402).astype(np.float64)
+    g = make_grad(32, 40, seed=1499)
+    c = _fit(fbf)
+    p = fbf.make_params(c, 2.0)
+    x = _cuda(img).requires_grad_(True)
+    y = fbf.FBFFunction.apply(x, p)
+    (y * _cuda(g)).sum().backward()
+    direct = fbf.fbf_filter_backward(p, _cuda(img), _cuda(g))
+    torch.cuda.synchronize()
+    assert torch.allclose(x.grad, direct, rtol=0, atol=1e-6)
+    h = 1e-3
+    for (i, j) in ((0, 0), (5, 7), (16, 20), (31, 39), (10, 0)):
+        vals = []
+        for s in (h, -h):
+            im = img.copy()
+            im[i, j] += s
+            out = fbf.fbf_filter(p, _cuda(im))
+            torch.cuda.synchronize()
+            vals.append(float((out.double().cpu().numpy() * g).sum()))
+        fd = (vals[0] - vals[1]) / (2 * h)
+        assert abs(fd - float(direct[i, j])) <= 2e-2 * max(1.0, abs(fd)), (i, j, fd, float(direct[i, j]))
+
+
+def test_backward_rejects_tensor_core_forms_and_big_windows(fbf):
+    import ctypes as C
+
+    c = _fit(fbf)
+    x = _cuda(np.zeros((8, 8)))
+    p = fbf.make_params(c, 2.0, 0, "gaussian", "reflect", "tc_fp16")
+    st = fbf.lib.fbf_filter_backward(C.byref(p), C.c_void_p(x.data_ptr()), C.c_void_p(x.data_ptr()), None,
+                                     C.c_void_p(x.data_ptr()), 8, 8, 32, None)
+    assert st == fbf.FBF_ERR_UNSUPPORTED
+    p = fbf.make_params(c, 6.0)  # W = 18 > 16
+    st = fbf.lib.fbf_filter_backward(C.byref(p), C.c_void_p(x.data_ptr()), C.c_void_p(x.data_ptr()), None,
+                                     C.c_void_p(x.data_ptr()), 8, 8, 32, None)
+    assert st == fbf.FBF_ERR_RANGE

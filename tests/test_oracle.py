@@ -290,3 +290,19 @@ def test_gradient_against_central_differences(border):
             num[i, j] = (np.sum(g * O.direct_sbf(fp, w1, border, fit.d, 1.0)[0])
                          - np.sum(g * O.direct_sbf(fm, w1, border, fit.d, 1.0)[0])) / (2 * h)
     assert np.max(np.abs(gr - num)) <= 1e-6 * max(1.0, np.max(np.abs(num)))
+
+
+@pytest.mark.parametrize("border", [O.BORDER_REFLECT, O.BORDER_TRUNCATE])
+@pytest.mark.parametrize("shape,W", [((9, 11), 2), ((6, 5), 4), ((12, 10), 3)])
+def test_gradient_at_points_equals_full_gradient(border, shape, W):
+    """The sampled-pixel gradient enumerates the same pairs as the full one
+    (including windows wider than the image, where pixels reflect repeatedly)."""
+    rng = np.random.default_rng(1)
+    f = rng.uniform(0.1, 0.9, size=shape)
+    g = rng.normal(size=shape)
+    w1 = O.weights_1d(O.SPATIAL_GAUSSIAN, 1.5, W)
+    fit = O.fit(O.RANGE_GAUSSIAN, 0.1, 1.0, 1e-3, levels=256)
+    full = O.grad_direct(f, g, w1, border, fit.d, 1.0)
+    ys, xs = np.mgrid[0:shape[0], 0:shape[1]]
+    pts = O.grad_at(f, g, w1, border, fit.d, 1.0, (ys.ravel(), xs.ravel()))
+    assert np.max(np.abs(pts - full.ravel())) <= 1e-11 * max(1.0, np.max(np.abs(full)))
