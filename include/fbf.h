@@ -169,6 +169,29 @@ fbf_status fbf_filter_backward(const fbf_params *p, const float *d_in, const flo
                                const float *d_out_fwd, float *d_gin, int H, int Wd, size_t pitch,
                                cudaStream_t stream);
 
+/*
+ * fbf_filter_backward_noalloc -- the same gradient as fbf_filter_backward, for
+ * callers that must not allocate device memory (the paper has no counterpart:
+ * this is a deployment variant).  Typical such callers: an application whose
+ * framework has already reserved the device memory for its own allocator, or a
+ * real-time loop where an allocation call (which may block, synchronise, or
+ * fail under memory pressure) is not allowed.
+ *
+ * Arguments, results and limits are those of fbf_filter_backward.  Scratch comes
+ * from one array of FBF_NOALLOC_SCRATCH_BYTES bytes that the library keeps in
+ * device memory on every GPU that loads it, until the process exits; nothing is
+ * allocated or freed.  A request needing more than that (8 bytes per pixel,
+ * plus (H+2W)(Wd+2W) floats under REFLECT, rounded up to 256 bytes) returns
+ * FBF_ERR_RANGE.  The first call on a device looks up the array's device
+ * address (with that device current); make that first call before any stream
+ * capture.  All calls share the array: calls whose GPU work overlaps (e.g. on
+ * two streams) race and give wrong results; serialise them.
+ */
+#define FBF_NOALLOC_SCRATCH_BYTES (16u << 20)
+fbf_status fbf_filter_backward_noalloc(const fbf_params *p, const float *d_in, const float *d_gout,
+                                       const float *d_out_fwd, float *d_gin, int H, int Wd, size_t pitch,
+                                       cudaStream_t stream);
+
 /* Half window actually used for the parameters (W, or ceil(3 sigma_s) when
  * W <= 0), or -1 when invalid.  Host only. */
 int fbf_resolve_window(const fbf_params *p);

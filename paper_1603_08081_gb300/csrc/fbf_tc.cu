@@ -359,7 +359,7 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc_u8_kernel(const __grid_constant
   // ---- demodulate harmonic n: lane m = 32 q + lane = 4 x + c, rows y in
   // [h * BYH, (h+1) * BYH); the four lanes of one x read the same table entry.
   auto demod = [&](int n) {
-    const int x = 8 * q + (lane >> 2), c = lane & 3;
+    const int c = lane & 3;
     const float dn = a.d[n];
     const char *Lf = reinterpret_cast<const char *>(lutf + (n & 1) * kLutStride + ((lane >> 2) & (kCopies - 1)));
     uint32_t v[BYH / 16][16];

@@ -65,6 +65,8 @@ def _load():
     lib.fbf_filter.restype = i
     lib.fbf_filter_backward.argtypes = [C.POINTER(fbf_params), p, p, p, p, i, i, sz, p]
     lib.fbf_filter_backward.restype = i
+    lib.fbf_filter_backward_noalloc.argtypes = [C.POINTER(fbf_params), p, p, p, p, i, i, sz, p]
+    lib.fbf_filter_backward_noalloc.restype = i
     lib.fbf_resolve_window.argtypes = [C.POINTER(fbf_params)]
     lib.fbf_resolve_window.restype = i
     lib.fbf_device_error.argtypes = [C.POINTER(C.c_uint)]
