@@ -212,7 +212,83 @@ def tensor_peak():
         return 1900.0, "profiling-recipe fallback 1.9 PFLOP/s bf16 burst (of fallback)"
 
 
+def _gen_image(spec):
+    from paper_1603_08081_gb300.synth import make_image
+
+    H_, W_, _, _, seed = spec
+    return make_image(H_, W_, seed)
+
+
+def make_batch_images(specs):
+    """The uneven batch's images, generated in a spawn-started process pool
+    (before any CUDA work in this process)."""
+    import concurrent.futures as cf
+    import multiprocessing as mp
+
+    workers = max(1, min(16, os.cpu_count() or 1))
+    with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(_gen_image, specs))
+
+
+def run_batched(fbf, torch, dev, stream, imgs, specs_raw, steps):
+    """One graph launch over the whole uneven batch vs one fbf_filter per image."""
+    xs = [torch.from_numpy(im).to(dev) for im in imgs]
+    ys = [torch.empty(im.shape, dtype=torch.float32, device=dev) for im in imgs]
+    specs = [dict(sigma_s=ss, sigma_r=sr, eps=EPS) for (_, _, ss, sr, _) in specs_raw]
+    total_px = sum(im.size for im in imgs)
+    with torch.cuda.stream(stream):
+        plan = fbf.fbf_plan_create(xs, ys, specs, "fp32", "reflect")
+    n_items = plan.size()[1]
+    params = {}
+    for f in FORMS_ALL:
+        params[f] = [fbf.make_params(fbf.fbf_fit_coeffs("gaussian", sp["sigma_r"], T, EPS), sp["sigma_s"], 0,
+                                     "gaussian", "reflect", f) for sp in specs]
+
+    def timed(fn):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        return e0.elapsed_time(e1) / steps
+
+    def separate(f):
+        def go():
+            for p, x, y in zip(params[f], xs, ys):
+                fbf.fbf_filter(p, x, out=y, stream=stream)
+        return go
+
+    def separate_best():  # per image, the faster single-image form at that window
+        for k, (x, y) in enumerate(zip(xs, ys)):
+            f = "fp32" if fbf.fbf_resolve_window(params["fp32"][k]) <= 12 else "tc_fp16"
+            fbf.fbf_filter(params[f][k], x, out=y, stream=stream)
+
+    res = {"workload": "64 u8 synthetic images (seeds 1300+i), H, W ~ U[256, 2048], sigma_s ~ U[2, 10], "
+                       "sigma_r ~ U[10, 60] (seed 1399), eps=1e-3, reflect",
+           "pixels": int(total_px), "work_items": n_items}
+    ms = timed(lambda: fbf.fbf_filter_batched(plan, stream))
+    res["graph_persistent_fp32"] = {"ms": round(ms, 3), "mpix_s": round(total_px / ms / 1e3, 1), "launches": 1}
+    for f in FORMS_ALL:
+        ms = timed(separate(f))
+        res["separate_" + f] = {"ms": round(ms, 3), "mpix_s": round(total_px / ms / 1e3, 1), "launches": len(imgs)}
+    ms = timed(separate_best)
+    res["separate_best_form"] = {"ms": round(ms, 3), "mpix_s": round(total_px / ms / 1e3, 1),
+                                 "launches": len(imgs), "rule": "fp32 if W <= 12 else tc_fp16"}
+    plan.destroy()
+    return res
+
+
 def run_ours(args):
+    batch_imgs = batch_specs = None
+    if args.batched:
+        from paper_1603_08081_gb300.synth import make_batch_specs
+
+        batch_specs = make_batch_specs(64, seed=1399)
+        batch_imgs = make_batch_images(batch_specs)
     import torch
 
     world, rank, local = dist_setup()
@@ -344,6 +420,10 @@ def run_ours(args):
     e2e_s = dist_max(time.perf_counter() - t0, world, dev)
     e2e_val = world * px_step * e2e_steps / e2e_s / 1e6
 
+    batched = None
+    if batch_imgs is not None:
+        batched = run_batched(fbf, torch, dev, stream, batch_imgs, batch_specs, max(2, min(args.steps, 10)))
+
     hf = per_form[head]
     result = {
         "metric": METRIC, "value": round(hf["value"], 1), "unit": "Mpixel/s", "n_gpus": world,
@@ -367,6 +447,8 @@ def run_ours(args):
         "gpu_launches": n_set * args.steps * len(forms),
         "clocks": clk.summary(),
     }
+    if batched is not None:
+        result["batched"] = batched
     if cb is not None:
         result["cpu_baseline"] = cb
         result["max_err_vs_oracle"] = round(errs[head], 6)
@@ -426,6 +508,9 @@ def main():
     ap.add_argument("--slab-rows", type=int, default=384, help="rows of the CPU-baseline sample")
     ap.add_argument("--ref-rows", type=int, default=8, help="rows per setting per reference step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batched", dest="batched", action="store_true", default=True,
+                    help="also time the uneven 64-image batch (default on)")
+    ap.add_argument("--no-batched", dest="batched", action="store_false")
     ap.add_argument("--only", type=int, default=None,
                     help="run a single setting (index into the six) -- for profiling")
     args = ap.parse_args()

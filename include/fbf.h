@@ -145,6 +145,46 @@ fbf_status fbf_fit_coeffs(fbf_range_kernel kernel, double sigma_r, double T, dou
 fbf_status fbf_filter(const fbf_params *p, const void *d_in, fbf_dtype dtype, int H, int Wd,
                       size_t in_pitch, float *d_out, size_t out_pitch, cudaStream_t stream);
 
+/* ---- Batched filtering ---------------------------------------------------
+ * Many uint8 images of uneven sizes, each with its own spatial window, range
+ * kernel, sigma_r, T and tolerance (hence its own K), filtered by one
+ * persistent launch captured in a CUDA graph. */
+
+typedef struct fbf_plan fbf_plan; /* owns its device tables and the graph */
+
+typedef struct {
+  const void *d_in;           /* device uint8 image, row pitch in_pitch bytes            */
+  float *d_out;               /* device FP32 output, row pitch out_pitch bytes           */
+  int H, Wd;                  /* rows, columns                                           */
+  size_t in_pitch, out_pitch; /* bytes                                                   */
+  fbf_spatial_kernel spatial;
+  double sigma_s;
+  int W;                      /* half window; <= 0 selects ceil(3 sigma_s); <= 32        */
+  fbf_range_kernel range;
+  double sigma_r, T, eps;     /* as fbf_fit_coeffs (T an integer for uint8 images)       */
+  int K_fixed, levels;        /* as fbf_fit_coeffs                                       */
+} fbf_image_desc;
+
+/*
+ * fbf_plan_create -- fit every image's coefficients (Algorithm 2, host FP64),
+ * upload a table of per-image parameters and a work list of (image, tile)
+ * items sorted by estimated cost, and capture one persistent launch (one CTA
+ * per SM pulling items from a counter) into a CUDA graph on the current
+ * device.  The pointers in `descs` are baked into the plan: the images must
+ * stay allocated while the plan is used.  Allocates device memory
+ * (synchronously) for the tables.  form: AUTO or FP32 (tensor-core forms
+ * return FBF_ERR_UNSUPPORTED).  A fit that misses its tolerance returns
+ * FBF_ERR_NOT_CONVERGED.
+ */
+fbf_status fbf_plan_create(const fbf_image_desc *descs, int n, fbf_form form, fbf_border border,
+                           fbf_plan **out);
+/* Filter every image of the plan: one cudaGraphLaunch on `stream`. */
+fbf_status fbf_filter_batched(fbf_plan *plan, cudaStream_t stream);
+/* Release the plan (the caller synchronises first if a launch is in flight). */
+fbf_status fbf_plan_destroy(fbf_plan *plan);
+/* Number of images and (image, tile) work items of a plan. */
+fbf_status fbf_plan_size(const fbf_plan *plan, int *n_images, int *n_items);
+
 /*
  * fbf_filter_backward -- gradient of L = sum_i g(i) fhat(i) with respect to the
  * input image f, where fhat is eq. (9) computed by fbf_filter (FP32 form,

@@ -157,8 +157,25 @@ __device__ __forceinline__ void fir_run(const u64 *w2, int taps_rt, Load load, Q
   }
 }
 
+// Per-tile parameters of the fused FP32 filter.  w2 / d point into the kernel
+// parameter block (single image) or into shared memory (batched plan).
+struct K1View {
+  const unsigned char *in;
+  size_t in_pitch;
+  float *out;
+  size_t out_pitch;
+  int H, Wd, W, K, twoT, border;
+  float T;
+  const u64 *w2;     // taps, duplicated into f32x2 pairs
+  const float *d;    // cosine coefficients
+};
+
+// One output tile (origin ty0, tx0) of the fused FP32 filter: stage, then for
+// every harmonic modulate / row pass / column pass / demodulate, then write
+// fhat.  `smem` is the dynamic shared memory laid out by make_layout (the
+// caller owns anything placed after Layout::bytes).
 template <int BX, int BY, int NT, int NBUF, int WCAP, int TAPSC>
-__global__ void __launch_bounds__(NT, 1) fbf_fp32_u8_kernel(const __grid_constant__ FilterArgs a) {
+__device__ __forceinline__ void k1_tile(const K1View &a, int ty0, int tx0, unsigned char *smem) {
   static_assert(BX % 32 == 0 && BY % kRun == 0 && NT % 32 == 0, "tile shape");
   static_assert(NBUF == 1 || NBUF == 2, "one or two table buffers");
   constexpr int NW = NT / 32;
@@ -169,7 +186,6 @@ __global__ void __launch_bounds__(NT, 1) fbf_fp32_u8_kernel(const __grid_constan
   static_assert(NCG * NYR % NW == 0, "column units must divide evenly among warps");
   constexpr int kLutStride = kLutEntries * kCopies;  // float4 per table buffer
 
-  extern __shared__ __align__(128) unsigned char smem[];
   const int W = a.W, taps = 2 * W + 1;
   const Layout Ly = make_layout(BX, BY, W, NBUF, WCAP);
   float4 *lut = reinterpret_cast<float4 *>(smem);
@@ -177,8 +193,6 @@ __global__ void __launch_bounds__(NT, 1) fbf_fp32_u8_kernel(const __grid_constan
   unsigned short *tileT = reinterpret_cast<unsigned short *>(smem + Ly.tile_off);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, cp = lane & (kCopies - 1);
-  const int tile_y = blockIdx.x / a.tiles_x, tile_x = blockIdx.x - tile_y * a.tiles_x;
-  const int ty0 = tile_y * BY, tx0 = tile_x * BX;
   const int H = a.H, Wd = a.Wd;
 
   // Sentinel entry of every table buffer: zero channels (TRUNCATE outside the image).
@@ -189,7 +203,7 @@ __global__ void __launch_bounds__(NT, 1) fbf_fp32_u8_kernel(const __grid_constan
 
   // Stage the halo tile, transposed: tileT[ex * PT + ey] (byte offsets into a table buffer).
   static_assert(BX + 2 * WCAP + kRun <= 128, "staging covers at most 128 ext columns");
-  stage_tile<NT>(static_cast<const unsigned char *>(a.in), a.in_pitch, H, Wd, a.border, ty0 - W, tx0 - W,
+  stage_tile<NT>(a.in, a.in_pitch, H, Wd, a.border, ty0 - W, tx0 - W,
                  Ly.HY, Ly.HX, Ly.HYP, Ly.HXA, tileT, Ly.PT, (unsigned short)(kCopies * sizeof(float4)),
                  (unsigned short)(kSentinel * kCopies * sizeof(float4)));
   build_lut(lut, 0, a.twoT, a.T, tid, NT);
@@ -274,6 +288,15 @@ __global__ void __launch_bounds__(NT, 1) fbf_fp32_u8_kernel(const __grid_constan
                                    (size_t)ix * sizeof(float)) = P[q][o] / Q[q][o];
     }
   }
+}
+
+template <int BX, int BY, int NT, int NBUF, int WCAP, int TAPSC>
+__global__ void __launch_bounds__(NT, 1) fbf_fp32_u8_kernel(const __grid_constant__ FilterArgs a) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int tile_y = blockIdx.x / a.tiles_x, tile_x = blockIdx.x - tile_y * a.tiles_x;
+  const K1View v{static_cast<const unsigned char *>(a.in), a.in_pitch, a.out, a.out_pitch, a.H, a.Wd, a.W, a.K,
+                 a.twoT, a.border, a.T, a.w2, a.d};
+  k1_tile<BX, BY, NT, NBUF, WCAP, TAPSC>(v, tile_y * BY, tile_x * BX, smem);
 }
 
 template <int BX, int BY, int NT, int NBUF, int WCAP, int TAPSC = 0>

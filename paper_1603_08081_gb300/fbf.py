@@ -46,6 +46,13 @@ class fbf_params(C.Structure):
                 ("form", C.c_int), ("coeffs", C.POINTER(fbf_coeffs))]
 
 
+class fbf_image_desc(C.Structure):
+    _fields_ = [("d_in", C.c_void_p), ("d_out", C.c_void_p), ("H", C.c_int), ("Wd", C.c_int),
+                ("in_pitch", C.c_size_t), ("out_pitch", C.c_size_t), ("spatial", C.c_int),
+                ("sigma_s", C.c_double), ("W", C.c_int), ("range", C.c_int), ("sigma_r", C.c_double),
+                ("T", C.c_double), ("eps", C.c_double), ("K_fixed", C.c_int), ("levels", C.c_int)]
+
+
 class FbfError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         self.status = status
@@ -67,6 +74,14 @@ def _load():
     lib.fbf_filter_backward.restype = i
     lib.fbf_filter_backward_noalloc.argtypes = [C.POINTER(fbf_params), p, p, p, p, i, i, sz, p]
     lib.fbf_filter_backward_noalloc.restype = i
+    lib.fbf_plan_create.argtypes = [C.POINTER(fbf_image_desc), i, i, i, C.POINTER(p)]
+    lib.fbf_plan_create.restype = i
+    lib.fbf_filter_batched.argtypes = [p, p]
+    lib.fbf_filter_batched.restype = i
+    lib.fbf_plan_destroy.argtypes = [p]
+    lib.fbf_plan_destroy.restype = i
+    lib.fbf_plan_size.argtypes = [p, C.POINTER(i), C.POINTER(i)]
+    lib.fbf_plan_size.restype = i
     lib.fbf_resolve_window.argtypes = [C.POINTER(fbf_params)]
     lib.fbf_resolve_window.restype = i
     lib.fbf_device_error.argtypes = [C.POINTER(C.c_uint)]
@@ -208,6 +223,68 @@ def __getattr__(name):
         globals()["FBFFunction"] = fn
         return fn
     raise AttributeError(name)
+
+
+class Plan:
+    """A batched-filter plan (fbf_plan_create); keeps its images alive."""
+
+    def __init__(self, handle, keep):
+        self.handle = handle
+        self._keep = keep
+
+    def size(self):
+        ni, nt = C.c_int(0), C.c_int(0)
+        st = lib.fbf_plan_size(self.handle, C.byref(ni), C.byref(nt))
+        if st != FBF_OK:
+            raise FbfError(st, "fbf_plan_size")
+        return ni.value, nt.value
+
+    def destroy(self):
+        if self.handle:
+            lib.fbf_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.destroy()
+        except Exception:
+            pass
+
+
+def fbf_plan_create(images, outs, specs, form="fp32", border="reflect"):
+    """images / outs: lists of uint8 / float32 CUDA tensors; specs: list of dicts
+    with sigma_s, sigma_r and optionally W, spatial, range, T, eps, K_fixed, levels."""
+    n = len(images)
+    arr = (fbf_image_desc * max(n, 1))()
+    for k, (x, y, sp) in enumerate(zip(images, outs, specs)):
+        d = arr[k]
+        d.d_in, d.d_out = x.data_ptr(), y.data_ptr()
+        d.H, d.Wd = x.shape
+        d.in_pitch, d.out_pitch = x.stride(0), y.stride(0) * 4
+        d.spatial = _enum(sp.get("spatial", "gaussian"))
+        d.sigma_s = float(sp.get("sigma_s", 3.0))
+        d.W = int(sp.get("W", 0))
+        d.range = _enum(sp.get("range", "gaussian"))
+        d.sigma_r = float(sp["sigma_r"])
+        d.T = float(sp.get("T", 255.0))
+        d.eps = float(sp.get("eps", 1e-3))
+        d.K_fixed = int(sp.get("K_fixed", 0))
+        d.levels = int(sp.get("levels", 0))
+    h = C.c_void_p()
+    st = lib.fbf_plan_create(arr, n, _enum(form), _enum(border), C.byref(h))
+    if st != FBF_OK:
+        raise FbfError(st, "fbf_plan_create")
+    return Plan(h, (list(images), list(outs)))
+
+
+def fbf_filter_batched(plan: Plan, stream=None):
+    st = lib.fbf_filter_batched(plan.handle, _stream_handle(stream))
+    if st != FBF_OK:
+        raise FbfError(st, "fbf_filter_batched")
+
+
+def fbf_plan_destroy(plan: Plan):
+    plan.destroy()
 
 
 def fbf_device_error() -> int:

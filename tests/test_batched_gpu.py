@@ -1,0 +1,98 @@
+"""GPU parity of the batched plan (fbf_plan_create / fbf_filter_batched): every
+image of an uneven batch, each with its own window, range scale and order K,
+against the FP64 oracle and against the single-image FP32 filter."""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1603_08081_gb300.synth import make_batch_specs, make_image
+
+pytestmark = pytest.mark.gpu
+
+TOL_FP32 = 0.05  # same regression bound as the single-image FP32 form (0.5 gray contract)
+
+
+@pytest.fixture(scope="module")
+def fbf():
+    import torch  # noqa: F401
+
+    from paper_1603_08081_gb300 import build
+
+    build.build()
+    from paper_1603_08081_gb300 import fbf as mod
+
+    return mod
+
+
+def _run_plan(fbf, imgs, specs, border="reflect"):
+    import torch
+
+    xs = [torch.from_numpy(im).cuda() for im in imgs]
+    ys = [torch.full(im.shape, float("nan"), dtype=torch.float32, device="cuda") for im in imgs]
+    plan = fbf.fbf_plan_create(xs, ys, specs, "fp32", border)
+    fbf.fbf_filter_batched(plan)
+    torch.cuda.synchronize()
+    return plan, xs, ys
+
+
+@pytest.mark.parametrize("border", ["reflect", "truncate"])
+def test_uneven_batch_matches_oracle(fbf, border):
+    shapes = [(70, 90), (33, 200), (256, 40), (5, 7), (130, 131), (1, 64)]
+    specs = [dict(sigma_s=3.0, sigma_r=30.0), dict(sigma_s=0.7, sigma_r=15.0), dict(sigma_s=6.0, sigma_r=50.0),
+             dict(sigma_s=10.0, sigma_r=20.0), dict(sigma_s=2.0, sigma_r=60.0, eps=1e-2),
+             dict(sigma_s=4.0, sigma_r=25.0, W=3, spatial="box")]
+    imgs = [make_image(h, w, seed=1300 + k) for k, (h, w) in enumerate(shapes)]
+    plan, xs, ys = _run_plan(fbf, imgs, specs, border)
+    ni, nt = plan.size()
+    assert ni == len(imgs) and nt > len(imgs)
+    bd = O.BORDER_REFLECT if border == "reflect" else O.BORDER_TRUNCATE
+    for im, sp, y in zip(imgs, specs, ys):
+        c = fbf.fbf_fit_coeffs("gaussian", sp["sigma_r"], 255.0, sp.get("eps", 1e-3))
+        W = sp.get("W", int(np.ceil(3 * sp["sigma_s"] - 1e-12)))
+        w1 = O.weights_1d(O.SPATIAL_BOX if sp.get("spatial") == "box" else O.SPATIAL_GAUSSIAN, sp["sigma_s"], W)
+        ref = O.alg1(im, w1, bd, np.array(c.coefficients), 255.0)[0]
+        got = y.cpu().numpy()
+        assert np.all(np.isfinite(got))
+        assert np.abs(got - ref).max() <= TOL_FP32
+    plan.destroy()
+
+
+def test_batch_equals_single_image_filter_and_relaunches(fbf):
+    """A 64-image batch shaped like the uneven workload (smaller sizes): each
+    output equals the single-image FP32 filter, and a second graph launch gives
+    the same outputs (the work counter is reset inside the graph)."""
+    import torch
+
+    specs_raw = make_batch_specs(64, seed=1399, lo=48, hi=400)
+    imgs = [make_image(h, w, seed=s) for (h, w, _, _, s) in specs_raw]
+    specs = [dict(sigma_s=ss, sigma_r=sr) for (_, _, ss, sr, _) in specs_raw]
+    plan, xs, ys = _run_plan(fbf, imgs, specs)
+    first = [y.clone() for y in ys]
+    for y in ys:
+        y.fill_(float("nan"))
+    fbf.fbf_filter_batched(plan)
+    torch.cuda.synchronize()
+    for y0, y1 in zip(first, ys):
+        assert torch.equal(y0, y1)
+    for x, y, sp in zip(xs, ys, specs):
+        c = fbf.fbf_fit_coeffs("gaussian", sp["sigma_r"], 255.0, 1e-3)
+        p = fbf.make_params(c, sp["sigma_s"])
+        single = fbf.fbf_filter(p, x)
+        torch.cuda.synchronize()
+        assert torch.max(torch.abs(single - y)).item() <= 1e-4
+    plan.destroy()
+
+
+def test_empty_plan_and_unsupported_form(fbf):
+    import ctypes as C
+
+    import torch
+
+    plan = fbf.fbf_plan_create([], [], [])
+    assert plan.size() == (0, 0)
+    fbf.fbf_filter_batched(plan)
+    torch.cuda.synchronize()
+    plan.destroy()
+    h = C.c_void_p()
+    arr = (fbf.fbf_image_desc * 1)()
+    assert fbf.lib.fbf_plan_create(arr, 1, fbf.FBF_FORM_TC_FP16, 0, C.byref(h)) == fbf.FBF_ERR_UNSUPPORTED
