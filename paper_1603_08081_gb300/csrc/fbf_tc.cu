@@ -27,13 +27,27 @@
 //             own partial: cos for the G_r / F_r channels, sin for G_i / F_i.
 //
 // P = partial(F_r) + partial(F_i), Q = partial(G_r) + partial(G_i) are combined
-// once per tile, and fhat = P / Q is written.  Precision: the data are split
+// once per tile, and fhat = P / Q is written.
+//
+// The kernel is persistent (one CTA per SM walks the tiles blockIdx.x,
+// blockIdx.x + gridDim.x, ...; TMEM, barriers and Toeplitz blocks are set up
+// once).  While a tile is processed, the next tile's halo is prefetched by a
+// 2-D TMA copy (cp.async.bulk.tensor) into a raw shared-memory box, which the
+// next tile transposes into the staged tile.  Under REFLECT only interior tiles
+// (no mirrored pixel in the halo) take the TMA path, border tiles load with
+// reflected indices; under TRUNCATE every tile does (out-of-image box entries
+// become the zero-channel sentinel by their coordinates).  Precision: the data are split
 // hi + lo; FP16 uses one weight part (2 products per step), BF16 splits the
 // weights too (3 products).  Table entries, the phase (exact integer
 // reduction), the K-term accumulation and the ratio stay in FP32.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
+#include <mutex>
 
 #include "fbf_common.cuh"
 #include "fbf_internal.h"
@@ -67,11 +81,13 @@ struct TcLayout {
   int kcc;  // the same for one NBC-output block (column pass)
   int KX;   // K extent of the row pass (ext columns, multiple of 16)
   int A1C;  // TMEM columns per (channel, part) of A1 = KX / 2
-  size_t lut16_off, lutf_off, a2_off, br_off, bc_off, tile_off, bar_off, bytes;
+  size_t lut16_off, lutf_off, a2_off, br_off, bc_off, tile_off, raw_off, bar_off, bytes;
 };
 
-// Shared memory: [lut16 (one buffer)][lutf (two buffers)][A2 hi | lo]
-// [row Toeplitz blocks][column Toeplitz blocks][tile][barrier, TMEM address, flags].
+constexpr int kBoxW = 112;  // TMA box: 112 columns (>= 15 + KX) x 128 rows of bytes
+
+// Shared memory: [lut16 (one buffer)][lutf (three buffers)][A2 hi | lo]
+// [row Toeplitz blocks][column Toeplitz blocks][tile][TMA box][barriers, TMEM address, flags].
 __host__ __device__ inline TcLayout tc_layout(int W, int wcap, int nbr, int nbc) {
   TcLayout L;
   L.kcr = (nbr + 2 * W + 15) / 16;
@@ -82,11 +98,12 @@ __host__ __device__ inline TcLayout tc_layout(int W, int wcap, int nbr, int nbc)
   const int KXmax = kBX - nbr + 16 * kcr_max;
   L.lut16_off = 0;
   L.lutf_off = L.lut16_off + (size_t)kLutStride * sizeof(uint4);
-  L.a2_off = L.lutf_off + 2ull * kLutStride * sizeof(float2);
+  L.a2_off = (L.lutf_off + 3ull * kLutStride * sizeof(float2) + 1023) & ~(size_t)1023;
   L.br_off = L.a2_off + 2ull * kA2Part;
   L.bc_off = L.br_off + (size_t)kcr_max * 2 * nbr * 32;
   L.tile_off = L.bc_off + (size_t)kcc_max * 2 * nbc * 32;
-  L.bar_off = L.tile_off + (((size_t)KXmax * kPT * 2 + 127) & ~(size_t)127);
+  L.raw_off = (L.tile_off + (size_t)KXmax * kPT * 2 + 1023) & ~(size_t)1023;  // TMA destination
+  L.bar_off = L.raw_off + (size_t)kBoxW * kLanes;
   L.bytes = L.bar_off + 64;
   return L;
 }
@@ -174,7 +191,8 @@ __device__ __forceinline__ void build_toeplitz(unsigned char *B, int nblocks, in
 // block) of the row / column pass; bigger blocks issue fewer, larger MMAs at the
 // price of more zero taps inside each block.
 template <int BF, int NSPLIT, int BY, int WCAP, int NBR, int NBC, int PIPE>
-__global__ void __launch_bounds__(kNT, 1) fbf_tc_u8_kernel(const __grid_constant__ FilterArgs a) {
+__global__ void __launch_bounds__(kNT, 1) fbf_tc_u8_kernel(const __grid_constant__ FilterArgs a,
+                                                            const __grid_constant__ CUtensorMap tmap, int use_tma) {
   static_assert(BY + 2 * WCAP <= kLanes && BY % 32 == 0, "halo rows must fit the TMEM lanes");
   static_assert(kBX % NBR == 0 && BY % NBC == 0 && NBR % 16 == 0 && NBC % 16 == 0, "output blocks");
   static_assert(BY - NBC + 16 * ((NBC + 2 * WCAP + 15) / 16) <= kLanes, "column-pass K fits A2");
@@ -199,13 +217,35 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc_u8_kernel(const __grid_constant
   uint64_t *mbarC = reinterpret_cast<uint64_t *>(smem + Ly.bar_off + 8);  // column MMAs done
   uint32_t *tmem_base_s = reinterpret_cast<uint32_t *>(smem + Ly.bar_off + 16);
   int *abort_s = reinterpret_cast<int *>(smem + Ly.bar_off + 32);
+  uint64_t *mbarT = reinterpret_cast<uint64_t *>(smem + Ly.bar_off + 40);  // TMA box landed
+  unsigned char *raw = smem + Ly.raw_off;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, cp = lane & (kCopies - 1);
   const int q = warp & 3, h = warp >> 2;  // TMEM lane quadrant, half
-  const int tile_y = blockIdx.x / a.tiles_x, tile_x = blockIdx.x - tile_y * a.tiles_x;
-  const int ty0 = tile_y * BY, tx0 = tile_x * kBX;
-  const int H = a.H, Wd = a.Wd, HY = BY + 2 * W;
-  const int kcr = Ly.kcr, kcc = Ly.kcc, A1C = Ly.A1C;
+  const int H = a.H, Wd = a.Wd, HY = BY + 2 * W, HX = kBX + 2 * W;
+  const int kcr = Ly.kcr, kcc = Ly.kcc, A1C = Ly.A1C, KX = Ly.KX;
+  const bool reflect = a.border == FBF_BORDER_REFLECT;
+  constexpr unsigned short kScale = kCopies * sizeof(uint4), kSent = kSentinel * kCopies * sizeof(uint4);
+
+  // Whether a tile's halo comes through the TMA box: always under TRUNCATE,
+  // under REFLECT only when no halo pixel is mirrored.
+  auto tma_tile = [&](int t) -> bool {
+    if (!use_tma) return false;
+    if (!reflect) return true;
+    const int ty = t / a.tiles_x, tx = t - ty * a.tiles_x;
+    const int y0 = ty * BY - W, x0 = tx * kBX - W;
+    return y0 >= 0 && y0 + HY <= H && x0 >= 0 && x0 + HX <= Wd;
+  };
+  auto box_x = [&](int t) -> int {  // 16-byte aligned start column of tile t's box
+    const int tx = t - (t / a.tiles_x) * a.tiles_x;
+    const int x0 = tx * kBX - W;
+    return x0 >= 0 ? (x0 & ~15) : -((-x0 + 15) & ~15);
+  };
+  auto issue_tma = [&](int t) {  // one thread
+    const int ty = t / a.tiles_x;
+    mbar_arrive_expect_tx(mbarT, (uint32_t)(kBoxW * kLanes));
+    tma_load_2d(raw, &tmap, box_x(t), ty * BY - W, mbarT);
+  };
 
   if (warp == 0) {
     tmem_alloc(tmem_base_s, 512);
@@ -214,23 +254,20 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc_u8_kernel(const __grid_constant
   if (tid == 0) {
     mbar_init(mbarR, kRowIssuers);  // one commit per issuing warp
     mbar_init(mbarC, kColIssuers);
+    mbar_init(mbarT, 1);
     mbar_fence_init();
     *abort_s = 0;
   }
   if (tid < kCopies) lut16[kSentinel * kCopies + tid] = make_uint4(0u, 0u, 0u, 0u);
-  if (tid < 2 * kCopies)  // sentinel rows: zero channels
+  if (tid < 3 * kCopies)  // sentinel rows: zero channels
     lutf[(tid / kCopies) * kLutStride + kSentinel * kCopies + (tid % kCopies)] = make_float2(0.f, 0.f);
   build_toeplitz<BF, NBR>(smem + Ly.br_off, kcr, W, a.w, tid);
   build_toeplitz<BF, NBC>(smem + Ly.bc_off, kcc, W, a.w, tid);
-
-  // Halo tile (128 ext rows x KX ext columns), transposed, as byte offsets v * 128.
-  stage_tile<kNT>(static_cast<const unsigned char *>(a.in), a.in_pitch, H, Wd, a.border, ty0 - W, tx0 - W, HY,
-                  kBX + 2 * W, kLanes, Ly.KX, tileT, kPT, (unsigned short)(kCopies * sizeof(uint4)),
-                  (unsigned short)(kSentinel * kCopies * sizeof(uint4)));
-  build_lut<BF>(lut16, lutf, 0, a.twoT, a.T, tid);
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
+  if (tid == 0 && blockIdx.x < a.ntiles && tma_tile(blockIdx.x)) issue_tma(blockIdx.x);
+
   const uint32_t tmem = *tmem_base_s;
   const uint32_t lane_base = (uint32_t)(32 * q) << 16;
   // TMEM column bases: pipelined, A1 | D1 | D2 are disjoint; otherwise D2 reuses A1.
@@ -241,29 +278,20 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc_u8_kernel(const __grid_constant
   const uint64_t br_desc = smem_desc(smem_u32(smem + Ly.br_off), 128, 256);
   const uint64_t bc_desc = smem_desc(smem_u32(smem + Ly.bc_off), 128, 256);
   const uint64_t a2_desc = smem_desc(smem_u32(A2), kA2Group, 128);
+  const char *L16 = reinterpret_cast<const char *>(lut16 + cp);
 
   float part[BYH];
-#pragma unroll
-  for (int j = 0; j < BYH; ++j) part[j] = 0.f;
-  uint32_t phR = 0, phC = 0;
-  bool ok = true;
-
-  const char *L16 = reinterpret_cast<const char *>(lut16 + cp);
-  // Table byte offsets (lutf) of this thread's BYH demodulation pixels, packed
-  // two per register; the same for every harmonic of the tile.
-  uint32_t cen_pk[BYH / 2];
-  {
-    const int x = 8 * q + (lane >> 2);
-    const unsigned short *cen = tileT + (x + W) * kPT + W + h * BYH;
-#pragma unroll
-    for (int j = 0; j < BYH / 2; ++j) cen_pk[j] = (uint32_t)(cen[2 * j] >> 1) | ((uint32_t)(cen[2 * j + 1] >> 1) << 16);
-  }
+  uint32_t cen_pk[BYH / 2];  // lutf byte offsets of this thread's demodulation pixels, two per register
   auto cen_off = [&](int j) -> uint32_t { return (j & 1) ? (cen_pk[j >> 1] >> 16) : (cen_pk[j >> 1] & 0xFFFFu); };
+  uint32_t phR = 0, phC = 0, phT = 0;
+  bool ok = true;
+  bool tma_pending = blockIdx.x < a.ntiles && tma_tile(blockIdx.x);  // a box copy is in flight
 
   // ---- modulate harmonic n: ext row r = 32 q + lane, TMEM columns [h * A1C/2, (h+1) * A1C/2).
   auto modulate = [&]() {
     const unsigned short *tcol = tileT + 32 * q + lane;
     const int c0 = h * (A1C / 2), c1 = (h + 1) * (A1C / 2);
+#pragma unroll 2
     for (int col = c0; col < c1; col += 4) {
       uint4 e[8];
 #pragma unroll
@@ -361,7 +389,7 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc_u8_kernel(const __grid_constant
   auto demod = [&](int n) {
     const int c = lane & 3;
     const float dn = a.d[n];
-    const char *Lf = reinterpret_cast<const char *>(lutf + (n & 1) * kLutStride + ((lane >> 2) & (kCopies - 1)));
+    const char *Lf = reinterpret_cast<const char *>(lutf + (n % 3) * kLutStride + ((lane >> 2) & (kCopies - 1)));
     uint32_t v[BYH / 16][16];
 #pragma unroll
     for (int g = 0; g < BYH / 16; ++g) tmem_ld_x16(tmem + lane_base + kD2 + (uint32_t)(h * BYH + 16 * g), v[g]);
@@ -387,80 +415,140 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc_u8_kernel(const __grid_constant
     return __syncthreads_or(*abort_s) == 0;
   };
 
-  if (!PIPE) {
-    // Serial schedule: modulate -> row MMAs (tables for n+1 built meanwhile) ->
-    // re-split -> column MMAs -> demodulate.
-    for (int n = 0; n < a.K && ok; ++n) {
+  for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
+    const int tile_y = tile / a.tiles_x, tile_x = tile - tile_y * a.tiles_x;
+    const int ty0 = tile_y * BY, tx0 = tile_x * kBX;
+
+    // ---- stage this tile: 128 ext rows x KX ext columns, column-major byte offsets v * 128.
+    if (tma_tile(tile)) {
+      if (!mbar_wait_bounded(mbarT, phT, kMaxPolls)) *abort_s = 1;
+      phT ^= 1;
+      tma_pending = false;
+      if (__syncthreads_or(*abort_s)) {
+        ok = false;
+        break;
+      }
+      const int xoff = (tx0 - W) - box_x(tile);
+      for (int ey = warp; ey < kLanes; ey += kNT / 32) {
+        const int iy = ty0 - W + ey;
+        const bool row_ok = ey < HY && iy >= 0 && iy < H;
+#pragma unroll
+        for (int k4 = 0; k4 < 4; ++k4) {
+          const int ex = lane + 32 * k4;
+          if (ex < KX) {
+            const int ix = tx0 - W + ex;
+            const bool in = row_ok && ex < HX && ix >= 0 && ix < Wd;
+            tileT[ex * kPT + ey] = in ? (unsigned short)(raw[ey * kBoxW + xoff + ex] * kScale) : kSent;
+          }
+        }
+      }
+      fence_proxy_async_smem();  // the box is rewritten by the next TMA copy
+    } else {
+      stage_tile<kNT>(static_cast<const unsigned char *>(a.in), a.in_pitch, H, Wd, a.border, ty0 - W, tx0 - W, HY,
+                      HX, kLanes, KX, tileT, kPT, kScale, kSent);
+    }
+    build_lut<BF>(lut16, lutf, 0, a.twoT, a.T, tid);
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    // prefetch the next tile of this CTA while this one is computed
+    const int next = tile + gridDim.x;
+    if (next < a.ntiles && tma_tile(next)) {
+      if (tid == 0) issue_tma(next);
+      tma_pending = true;
+    }
+
+#pragma unroll
+    for (int j = 0; j < BYH; ++j) part[j] = 0.f;
+    {
+      const int x = 8 * q + (lane >> 2);
+      const unsigned short *cen = tileT + (x + W) * kPT + W + h * BYH;
+#pragma unroll
+      for (int j = 0; j < BYH / 2; ++j)
+        cen_pk[j] = (uint32_t)(cen[2 * j] >> 1) | ((uint32_t)(cen[2 * j + 1] >> 1) << 16);
+    }
+
+    if (!PIPE) {
+      // Serial schedule: modulate -> row MMAs (tables for n+1 built meanwhile) ->
+      // re-split -> column MMAs -> demodulate.
+      for (int n = 0; n < a.K && ok; ++n) {
+        modulate();
+        fence_before_sync();
+        __syncthreads();
+        if (row_issuer) issue_row();
+        if (n + 1 < a.K) build_lut<BF>(lut16, lutf + ((n + 1) % 3) * kLutStride, n + 1, a.twoT, a.T, tid);
+        if (!(ok = wait_mma(mbarR, phR))) break;
+        resplit();
+        fence_before_sync();
+        __syncthreads();
+        if (col_issuer) issue_col();
+        if (!(ok = wait_mma(mbarC, phC))) break;
+        demod(n);
+        fence_before_sync();
+        __syncthreads();
+      }
+    } else {
+      // Pipelined schedule: the column MMAs of harmonic n run while harmonic n+1
+      // is modulated, and the row MMAs of n+1 run while n is demodulated and the
+      // tables of n+2 are built.
       modulate();
       fence_before_sync();
       __syncthreads();
       if (row_issuer) issue_row();
-      if (n + 1 < a.K) build_lut<BF>(lut16, lutf + ((n + 1) & 1) * kLutStride, n + 1, a.twoT, a.T, tid);
-      if (!(ok = wait_mma(mbarR, phR))) break;
-      resplit();
-      fence_before_sync();
-      __syncthreads();
-      if (col_issuer) issue_col();
-      if (!(ok = wait_mma(mbarC, phC))) break;
-      demod(n);
-      fence_before_sync();
-      __syncthreads();
-    }
-  } else {
-    // Pipelined schedule: the column MMAs of harmonic n run while harmonic n+1
-    // is modulated, and the row MMAs of n+1 run while n is demodulated and the
-    // tables of n+2 are built.
-    modulate();
-    fence_before_sync();
-    __syncthreads();
-    if (row_issuer) issue_row();
-    if (a.K > 1) build_lut<BF>(lut16, lutf + kLutStride, 1, a.twoT, a.T, tid);
-    ok = wait_mma(mbarR, phR);
-    if (ok) {
-      resplit();
-      fence_before_sync();
-      __syncthreads();
-    }
-    for (int n = 0; n < a.K && ok; ++n) {
-      if (col_issuer) issue_col();  // C(n): A2 -> D2
-      if (n + 1 < a.K) modulate();  // A1 <- harmonic n+1 (R(n) has finished)
-      fence_before_sync();
-      __syncthreads();
-      if (n + 1 < a.K && row_issuer) issue_row();  // R(n+1): A1 -> D1
-      if (!(ok = wait_mma(mbarC, phC))) break;
-      demod(n);  // D2, table n
-      fence_before_sync();
-      __syncthreads();
-      if (n + 2 < a.K) build_lut<BF>(lut16, lutf + (n & 1) * kLutStride, n + 2, a.twoT, a.T, tid);
-      if (n + 1 < a.K) {
-        if (!(ok = wait_mma(mbarR, phR))) break;
-        resplit();  // D1 -> A2 (C(n) has finished)
+      if (a.K > 1) build_lut<BF>(lut16, lutf + 1 * kLutStride, 1, a.twoT, a.T, tid);
+      ok = wait_mma(mbarR, phR);
+      if (ok) {
+        resplit();
         fence_before_sync();
         __syncthreads();
       }
-    }
-  }
-
-  // ---- combine the four channel partials and write fhat = P / Q.
-  if (ok) {
-    float *comb = reinterpret_cast<float *>(A2);  // [c][y][x], 4 * BY * 32 floats
-    const int x = 8 * q + (lane >> 2), c = lane & 3;
-#pragma unroll
-    for (int j = 0; j < BYH; ++j) comb[(c * BY + h * BYH + j) * kBX + x] = part[j];
-    __syncthreads();
-    for (int e = tid; e < BY * kBX; e += kNT) {
-      const int y = e / kBX, xx = e - y * kBX;
-      const int iy = ty0 + y, ix = tx0 + xx;
-      if (iy < H && ix < Wd) {
-        const float Q = comb[(0 * BY + y) * kBX + xx] + comb[(1 * BY + y) * kBX + xx];
-        const float P = comb[(2 * BY + y) * kBX + xx] + comb[(3 * BY + y) * kBX + xx];
-        *reinterpret_cast<float *>(reinterpret_cast<char *>(a.out) + (size_t)iy * a.out_pitch +
-                                   (size_t)ix * sizeof(float)) = P / Q;
+      for (int n = 0; n < a.K && ok; ++n) {
+        if (col_issuer) issue_col();  // C(n): A2 -> D2
+        if (n + 1 < a.K) modulate();  // A1 <- harmonic n+1 (R(n) has finished)
+        fence_before_sync();
+        __syncthreads();
+        if (n + 1 < a.K && row_issuer) issue_row();  // R(n+1): A1 -> D1
+        // Tables of n+2 while C(n) and R(n+1) run: lut16 (last read by the
+        // modulation of n+1, done) and lutf buffer (n+2) % 3 (not read by demod(n)).
+        if (n + 2 < a.K) build_lut<BF>(lut16, lutf + ((n + 2) % 3) * kLutStride, n + 2, a.twoT, a.T, tid);
+        if (!(ok = wait_mma(mbarC, phC))) break;
+        demod(n);  // D2, table n
+        fence_before_sync();
+        __syncthreads();
+        if (n + 1 < a.K) {
+          if (!(ok = wait_mma(mbarR, phR))) break;
+          resplit();  // D1 -> A2 (C(n) has finished)
+          fence_before_sync();
+          __syncthreads();
+        }
       }
     }
-  } else if (tid == 0) {
-    atomicOr(&g_fbf_tc_error, 1u);
+    // ---- combine the four channel partials and write fhat = P / Q.
+    if (ok) {
+      float *comb = reinterpret_cast<float *>(A2);  // [c][y][x], 4 * BY * 32 floats
+      const int x = 8 * q + (lane >> 2), c = lane & 3;
+  #pragma unroll
+      for (int j = 0; j < BYH; ++j) comb[(c * BY + h * BYH + j) * kBX + x] = part[j];
+      __syncthreads();
+      for (int e = tid; e < BY * kBX; e += kNT) {
+        const int y = e / kBX, xx = e - y * kBX;
+        const int iy = ty0 + y, ix = tx0 + xx;
+        if (iy < H && ix < Wd) {
+          const float Q = comb[(0 * BY + y) * kBX + xx] + comb[(1 * BY + y) * kBX + xx];
+          const float P = comb[(2 * BY + y) * kBX + xx] + comb[(3 * BY + y) * kBX + xx];
+          *reinterpret_cast<float *>(reinterpret_cast<char *>(a.out) + (size_t)iy * a.out_pitch +
+                                     (size_t)ix * sizeof(float)) = P / Q;
+        }
+      }
+    } else if (tid == 0) {
+      atomicOr(&g_fbf_tc_error, 1u);
+    }
+    fence_before_sync();
+    __syncthreads();
   }
+  // A prefetched box that no tile consumed (the loop was abandoned): let the
+  // copy land (bounded wait) before the CTA exits.
+  if (tma_pending) mbar_wait_bounded(mbarT, phT, kMaxPolls);
   fence_before_sync();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tmem, 512);
@@ -479,6 +567,39 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc_u8_kernel(const __grid_constant
 #define FBF_TC_PIPE 1  // W <= 16: pipelined schedule (A1, D1, D2 disjoint in TMEM)
 #endif
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// dependency on the driver library).
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+// 2-D u8 tensor map of the input image with a kBoxW x 128 box; false when the
+// base address or pitch breaks TMA's 16-byte rules (then every tile loads directly).
+bool make_box_map(const FilterArgs &a, CUtensorMap *map) {
+  std::memset(map, 0, sizeof(*map));
+  if ((reinterpret_cast<uintptr_t>(a.in) & 15) != 0 || (a.in_pitch & 15) != 0) return false;
+  if (a.in_pitch >= (1ull << 40) || a.Wd <= 0 || a.H <= 0) return false;
+  PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)a.Wd, (cuuint64_t)a.H};
+  const cuuint64_t strides[1] = {(cuuint64_t)a.in_pitch};
+  const cuuint32_t box[2] = {(cuuint32_t)kBoxW, (cuuint32_t)kLanes};
+  const cuuint32_t estr[2] = {1, 1};
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 2, const_cast<void *>(a.in), dims, strides, box, estr,
+             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int BF, int NSPLIT, int BY, int WCAP, int NBR, int NBC, int PIPE>
 fbf_status launch_tc_cfg(const FilterArgs &a0, cudaStream_t s) {
   FilterArgs a = a0;
@@ -486,10 +607,16 @@ fbf_status launch_tc_cfg(const FilterArgs &a0, cudaStream_t s) {
   a.tiles_x = (a.Wd + kBX - 1) / kBX;
   const int tiles_y = (a.H + BY - 1) / BY;
   a.ntiles = a.tiles_x * tiles_y;
+  CUtensorMap map;
+  const int use_tma = make_box_map(a, &map) ? 1 : 0;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return FBF_ERR_CUDA;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = a.ntiles < sms ? a.ntiles : sms;
   auto kern = fbf_tc_u8_kernel<BF, NSPLIT, BY, WCAP, NBR, NBC, PIPE>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Ly.bytes) != cudaSuccess)
     return FBF_ERR_CUDA;
-  kern<<<a.ntiles, kNT, Ly.bytes, s>>>(a);
+  kern<<<grid, kNT, Ly.bytes, s>>>(a, map, use_tma);
   return cuda_status(cudaGetLastError());
 }
 

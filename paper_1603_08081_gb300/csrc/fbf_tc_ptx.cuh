@@ -149,5 +149,21 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *m, uint32_t parity, 
   return false;
 }
 
+// ---- TMA ------------------------------------------------------------------
+
+// Expect `bytes` of asynchronous transactions on `m` (and arrive once).
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *m, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(m)), "r"(bytes) : "memory");
+}
+// 2-D tiled TMA load of the box at (x, y) (x is the innermost coordinate and
+// must be a multiple of 16 bytes) into shared memory; completes on `m`.
+__device__ __forceinline__ void tma_load_2d(void *dst, const void *tmap, int x, int y, uint64_t *m) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(tmap)), "r"(x), "r"(y), "r"(smem_u32(m))
+      : "memory");
+}
+
 }  // namespace tc
 }  // namespace fbf
