@@ -62,7 +62,10 @@ typedef enum { FBF_BORDER_REFLECT = 0, FBF_BORDER_TRUNCATE = 1 } fbf_border;
 typedef enum { FBF_U8 = 0, FBF_F32 = 1 } fbf_dtype;
 
 /* Arithmetic form of the device filter.  FP32: every step in FP32 on the FMA
- * pipe.  AUTO: the fastest form this build provides for the request. */
+ * pipe.  TC_FP16 / TC_BF16: both 1-D passes as banded-Toeplitz products on the
+ * tensor cores (tcgen05) with FP32 accumulation; data split into hi + lo
+ * 16-bit parts (BF16 splits the weights too); uint8 input only.  AUTO: the
+ * faster of FP32 and TC_FP16 for the window (TC_FP16 from W = 10 up). */
 typedef enum {
   FBF_FORM_AUTO = 0,
   FBF_FORM_FP32 = 1,
