@@ -3,12 +3,13 @@
 // products on the 5th-generation tensor cores (tcgen05.mma, kind::f16, FP32
 // accumulation in tensor memory).
 //
-// One CTA (256 threads) owns a 32-column x BY-row output tile; its BY + 2W halo
+// One CTA (512 threads: four groups of four warps, warp w reaching TMEM lanes
+// 32 (w % 4) ... + 31) owns a 32-column x BY-row output tile; its BY + 2W halo
 // rows fit the 128 TMEM lanes (BY = 96 for W <= 16, 64 for W <= 32).  For each
 // harmonic n:
 //
-//   modulate  thread (lane r, half h) gathers, for ext row r and half of the
-//             ext columns, the per-harmonic table entry of each pixel value:
+//   modulate  thread (lane r, group h) gathers, for ext row r and a quarter
+//             of the ext columns, the per-harmonic table entry of each pixel value:
 //             (cos, sin, f cos, f sin)(n w f) already split into hi + lo 16-bit
 //             parts, pairs neighbouring columns with byte permutes and writes
 //             them with tcgen05.st into TMEM: A1[c][part] (lane = ext row,
@@ -74,7 +75,6 @@ constexpr int kPT = kLanes + 2;                     // tile pitch (u16), PT/2 od
 constexpr int kA2Group = 2048;                      // bytes per 8-row K group of A2 (16 M groups x 128 B)
 constexpr int kA2Part = 16 * kA2Group;              // one part of A2: 128 (M) x 128 (K) x 16 bit
 constexpr uint32_t kMaxPolls = 1u << 22;
-constexpr int kNT = 256;
 
 struct TcLayout {
   int kcr;  // 16-wide K chunks meeting the band of one NBR-output block (row pass)
@@ -143,9 +143,9 @@ __device__ __forceinline__ float from16(unsigned short x) {
 
 // Per-harmonic tables (see above); copies written rotated so the 8 stores of one
 // value land in 8 different bank groups.
-template <int BF>
+template <int BF, int NT>
 __device__ __forceinline__ void build_lut(uint4 *L16, float2 *Lf, int n, int twoT, float T, int tid) {
-  for (int v = tid; v < 256; v += kNT) {
+  for (int v = tid; v < 256; v += NT) {
     const int m = (n * v) % twoT;  // exact phase index: n*omega*v = pi * m / T (mod 2 pi)
     float sn, cs;
     sincospif((float)m / T, &sn, &cs);
@@ -172,9 +172,9 @@ __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
 // element (n, k) = w[16 i + k - n] inside the band and 0 outside, K-major
 // without swizzle ((n % 8) * 16 + (n / 8) * 256 + (k % 8) * 2 + (k / 8) * 128);
 // part 0 is the 16-bit weight, part 1 its residual.
-template <int BF, int NB>
+template <int BF, int NB, int NT>
 __device__ __forceinline__ void build_toeplitz(unsigned char *B, int nblocks, int W, const float *w, int tid) {
-  for (int e = tid; e < nblocks * NB * 16; e += kNT) {
+  for (int e = tid; e < nblocks * NB * 16; e += NT) {
     const int i = e / (NB * 16), rem = e - i * NB * 16, n = rem >> 4, k = rem & 15;
     const int t = 16 * i + k - n;
     const float wv = (t >= 0 && t <= 2 * W) ? w[t] : 0.f;
@@ -189,17 +189,23 @@ __device__ __forceinline__ void build_toeplitz(unsigned char *B, int nblocks, in
 // BF: 0 = FP16, 1 = BF16.  NSPLIT: 2 = data hi/lo x weights hi; 3 = plus data hi x weights lo.
 // BY: output rows per tile (BY + 2 * WCAP <= 128).  NBR / NBC: MMA N (output
 // block) of the row / column pass; bigger blocks issue fewer, larger MMAs at the
-// price of more zero taps inside each block.
-template <int BF, int NSPLIT, int BY, int WCAP, int NBR, int NBC, int PIPE>
-__global__ void __launch_bounds__(kNT, 1) fbf_tc_u8_kernel(const __grid_constant__ FilterArgs a,
-                                                            const __grid_constant__ CUtensorMap tmap, int use_tma) {
+// price of more zero taps inside each block.  NT: threads (256 or 512); the
+// NT / 32 warps form NT / 128 groups of four, each group covering the 128 TMEM
+// lanes once (warp w reaches lanes 32 (w % 4) ... + 31).
+template <int BF, int NSPLIT, int BY, int WCAP, int NBR, int NBC, int PIPE, int NT>
+__global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant__ FilterArgs a,
+                                                           const __grid_constant__ CUtensorMap tmap, int use_tma) {
   static_assert(BY + 2 * WCAP <= kLanes && BY % 32 == 0, "halo rows must fit the TMEM lanes");
   static_assert(kBX % NBR == 0 && BY % NBC == 0 && NBR % 16 == 0 && NBC % 16 == 0, "output blocks");
   static_assert(BY - NBC + 16 * ((NBC + 2 * WCAP + 15) / 16) <= kLanes, "column-pass K fits A2");
   // A1 (8 regions of KX/2 columns) must fit below D1: 256 columns when
   // pipelined (D1 at 256, D2 at 384), 384 otherwise (D1 at 384, D2 over A1).
   static_assert(4 * (kBX - NBR + 16 * ((NBR + 2 * WCAP + 15) / 16)) <= (PIPE ? 256 : 384), "A1 fits below D1");
-  constexpr int BYH = BY / 2;  // output rows per thread in the demodulation
+  static_assert(NT == 256 || NT == 512, "two or four warp groups");
+  constexpr int kGroups = NT / 128;   // warp groups; h = warp / 4 in [0, kGroups)
+  constexpr int BYH = BY / kGroups;   // output rows per thread in the demodulation
+  constexpr int XPT = kBX / kGroups;  // outputs x per thread in the re-split
+  static_assert(BYH % 8 == 0 && XPT % 8 == 0, "TMEM loads in groups of 8 columns");
   constexpr int NP = NSPLIT;   // products per (chunk, output block)
   // MMAs are issued by lane 0 of several warps (a single issuing thread would
   // spend ~50 cycles per small MMA); every issuer owns whole accumulator blocks.
@@ -221,7 +227,7 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc_u8_kernel(const __grid_constant
   unsigned char *raw = smem + Ly.raw_off;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, cp = lane & (kCopies - 1);
-  const int q = warp & 3, h = warp >> 2;  // TMEM lane quadrant, half
+  const int q = warp & 3, h = warp >> 2;  // TMEM lane quadrant, warp group
   const int H = a.H, Wd = a.Wd, HY = BY + 2 * W, HX = kBX + 2 * W;
   const int kcr = Ly.kcr, kcc = Ly.kcc, A1C = Ly.A1C, KX = Ly.KX;
   const bool reflect = a.border == FBF_BORDER_REFLECT;
@@ -261,8 +267,8 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc_u8_kernel(const __grid_constant
   if (tid < kCopies) lut16[kSentinel * kCopies + tid] = make_uint4(0u, 0u, 0u, 0u);
   if (tid < 3 * kCopies)  // sentinel rows: zero channels
     lutf[(tid / kCopies) * kLutStride + kSentinel * kCopies + (tid % kCopies)] = make_float2(0.f, 0.f);
-  build_toeplitz<BF, NBR>(smem + Ly.br_off, kcr, W, a.w, tid);
-  build_toeplitz<BF, NBC>(smem + Ly.bc_off, kcc, W, a.w, tid);
+  build_toeplitz<BF, NBR, NT>(smem + Ly.br_off, kcr, W, a.w, tid);
+  build_toeplitz<BF, NBC, NT>(smem + Ly.bc_off, kcc, W, a.w, tid);
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
@@ -281,18 +287,19 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc_u8_kernel(const __grid_constant
   const char *L16 = reinterpret_cast<const char *>(lut16 + cp);
 
   float part[BYH];
-  uint32_t cen_pk[BYH / 2];  // lutf byte offsets of this thread's demodulation pixels, two per register
+  uint32_t cen_pk[BYH / 2] = {};  // lutf byte offsets of this thread's demodulation pixels, two per register
   auto cen_off = [&](int j) -> uint32_t { return (j & 1) ? (cen_pk[j >> 1] >> 16) : (cen_pk[j >> 1] & 0xFFFFu); };
   uint32_t phR = 0, phC = 0, phT = 0;
   bool ok = true;
   bool tma_pending = blockIdx.x < a.ntiles && tma_tile(blockIdx.x);  // a box copy is in flight
 
-  // ---- modulate harmonic n: ext row r = 32 q + lane, TMEM columns [h * A1C/2, (h+1) * A1C/2).
+  // ---- modulate harmonic n: ext row r = 32 q + lane; units of 4 TMEM columns
+  // (8 ext columns) u = h, h + kGroups, ... of the A1C / 4 units.
   auto modulate = [&]() {
     const unsigned short *tcol = tileT + 32 * q + lane;
-    const int c0 = h * (A1C / 2), c1 = (h + 1) * (A1C / 2);
-#pragma unroll 2
-    for (int col = c0; col < c1; col += 4) {
+#pragma unroll 1
+    for (int u = h; u < A1C / 4; u += kGroups) {
+      const int col = 4 * u;
       uint4 e[8];
 #pragma unroll
       for (int j = 0; j < 8; ++j) e[j] = *reinterpret_cast<const uint4 *>(L16 + tcol[(2 * col + j) * kPT]);
@@ -340,25 +347,25 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc_u8_kernel(const __grid_constant
   };
 
   // ---- re-split the row-pass result into the column pass's A operand.
-  // Thread: ext row r, outputs x in [16 h, 16 h + 16), all four channels;
+  // Thread: ext row r, outputs x in [XPT h, XPT h + XPT), all four channels;
   // A2[m = 4 x + c][r] is MN-major:
   // (m % 8) * 2 + (r % 8) * 16 + (m / 8) * 128 + (r / 8) * kA2Group.
   auto resplit = [&]() {
     const int r = 32 * q + lane;
     unsigned char *rowp = A2 + (r & 7) * 16 + (r >> 3) * kA2Group;
-    uint32_t v[4][16];
+    uint32_t v[4][XPT];
 #pragma unroll
-    for (int c = 0; c < 4; ++c) tmem_ld_x16(tmem + lane_base + kD1 + (uint32_t)(32 * c + 16 * h), v[c]);
+    for (int c = 0; c < 4; ++c) tmem_ld(tmem + lane_base + kD1 + (uint32_t)(32 * c + XPT * h), v[c]);
 #pragma unroll
     for (int c = 0; c < 4; ++c) tmem_ld_wait_dep(v[c]);
 #pragma unroll
-    for (int k = 0; k < 8; ++k) {  // m = 64 h + 8 k + (0..7): x = 16 h + 2 k + {0, 1}, c = 0..3
+    for (int k = 0; k < XPT / 2; ++k) {  // m = 4 XPT h + 8 k + (0..7): x = XPT h + 2 k + {0, 1}, c = 0..3
       uint4 vh, vl;
       split2<BF>(__uint_as_float(v[0][2 * k]), __uint_as_float(v[1][2 * k]), vh.x, vl.x);
       split2<BF>(__uint_as_float(v[2][2 * k]), __uint_as_float(v[3][2 * k]), vh.y, vl.y);
       split2<BF>(__uint_as_float(v[0][2 * k + 1]), __uint_as_float(v[1][2 * k + 1]), vh.z, vl.z);
       split2<BF>(__uint_as_float(v[2][2 * k + 1]), __uint_as_float(v[3][2 * k + 1]), vh.w, vl.w);
-      const int mg = 8 * h + k;
+      const int mg = (XPT / 2) * h + k;
       *reinterpret_cast<uint4 *>(rowp + mg * 128) = vh;
       *reinterpret_cast<uint4 *>(rowp + kA2Part + mg * 128) = vl;
     }
@@ -390,9 +397,10 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc_u8_kernel(const __grid_constant
     const int c = lane & 3;
     const float dn = a.d[n];
     const char *Lf = reinterpret_cast<const char *>(lutf + (n % 3) * kLutStride + ((lane >> 2) & (kCopies - 1)));
-    uint32_t v[BYH / 16][16];
+    constexpr int DG = BYH % 16 == 0 ? 16 : 8;  // columns per TMEM load
+    uint32_t v[BYH / DG][DG];
 #pragma unroll
-    for (int g = 0; g < BYH / 16; ++g) tmem_ld_x16(tmem + lane_base + kD2 + (uint32_t)(h * BYH + 16 * g), v[g]);
+    for (int g = 0; g < BYH / DG; ++g) tmem_ld(tmem + lane_base + kD2 + (uint32_t)(h * BYH + DG * g), v[g]);
     float t[BYH];
 #pragma unroll
     for (int j = 0; j < BYH; ++j) {
@@ -400,11 +408,11 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc_u8_kernel(const __grid_constant
       t[j] = dn * ((c & 1) ? cs.y : cs.x);  // cos for G_r, F_r; sin for G_i, F_i
     }
 #pragma unroll
-    for (int g = 0; g < BYH / 16; ++g) tmem_ld_wait_dep(v[g]);
+    for (int g = 0; g < BYH / DG; ++g) tmem_ld_wait_dep(v[g]);
 #pragma unroll
-    for (int g = 0; g < BYH / 16; ++g)
+    for (int g = 0; g < BYH / DG; ++g)
 #pragma unroll
-      for (int j = 0; j < 16; ++j) part[16 * g + j] = fmaf(t[16 * g + j], __uint_as_float(v[g][j]), part[16 * g + j]);
+      for (int j = 0; j < DG; ++j) part[DG * g + j] = fmaf(t[DG * g + j], __uint_as_float(v[g][j]), part[DG * g + j]);
   };
 
   // Bounded wait on an MMA barrier, then a CTA-wide agreement on failure.
@@ -429,7 +437,7 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc_u8_kernel(const __grid_constant
         break;
       }
       const int xoff = (tx0 - W) - box_x(tile);
-      for (int ey = warp; ey < kLanes; ey += kNT / 32) {
+      for (int ey = warp; ey < kLanes; ey += NT / 32) {
         const int iy = ty0 - W + ey;
         const bool row_ok = ey < HY && iy >= 0 && iy < H;
 #pragma unroll
@@ -444,10 +452,10 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc_u8_kernel(const __grid_constant
       }
       fence_proxy_async_smem();  // the box is rewritten by the next TMA copy
     } else {
-      stage_tile<kNT>(static_cast<const unsigned char *>(a.in), a.in_pitch, H, Wd, a.border, ty0 - W, tx0 - W, HY,
+      stage_tile<NT>(static_cast<const unsigned char *>(a.in), a.in_pitch, H, Wd, a.border, ty0 - W, tx0 - W, HY,
                       HX, kLanes, KX, tileT, kPT, kScale, kSent);
     }
-    build_lut<BF>(lut16, lutf, 0, a.twoT, a.T, tid);
+    build_lut<BF, NT>(lut16, lutf, 0, a.twoT, a.T, tid);
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
@@ -476,7 +484,7 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc_u8_kernel(const __grid_constant
         fence_before_sync();
         __syncthreads();
         if (row_issuer) issue_row();
-        if (n + 1 < a.K) build_lut<BF>(lut16, lutf + ((n + 1) % 3) * kLutStride, n + 1, a.twoT, a.T, tid);
+        if (n + 1 < a.K) build_lut<BF, NT>(lut16, lutf + ((n + 1) % 3) * kLutStride, n + 1, a.twoT, a.T, tid);
         if (!(ok = wait_mma(mbarR, phR))) break;
         resplit();
         fence_before_sync();
@@ -495,7 +503,7 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc_u8_kernel(const __grid_constant
       fence_before_sync();
       __syncthreads();
       if (row_issuer) issue_row();
-      if (a.K > 1) build_lut<BF>(lut16, lutf + 1 * kLutStride, 1, a.twoT, a.T, tid);
+      if (a.K > 1) build_lut<BF, NT>(lut16, lutf + 1 * kLutStride, 1, a.twoT, a.T, tid);
       ok = wait_mma(mbarR, phR);
       if (ok) {
         resplit();
@@ -510,7 +518,7 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc_u8_kernel(const __grid_constant
         if (n + 1 < a.K && row_issuer) issue_row();  // R(n+1): A1 -> D1
         // Tables of n+2 while C(n) and R(n+1) run: lut16 (last read by the
         // modulation of n+1, done) and lutf buffer (n+2) % 3 (not read by demod(n)).
-        if (n + 2 < a.K) build_lut<BF>(lut16, lutf + ((n + 2) % 3) * kLutStride, n + 2, a.twoT, a.T, tid);
+        if (n + 2 < a.K) build_lut<BF, NT>(lut16, lutf + ((n + 2) % 3) * kLutStride, n + 2, a.twoT, a.T, tid);
         if (!(ok = wait_mma(mbarC, phC))) break;
         demod(n);  // D2, table n
         fence_before_sync();
@@ -530,7 +538,7 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc_u8_kernel(const __grid_constant
   #pragma unroll
       for (int j = 0; j < BYH; ++j) comb[(c * BY + h * BYH + j) * kBX + x] = part[j];
       __syncthreads();
-      for (int e = tid; e < BY * kBX; e += kNT) {
+      for (int e = tid; e < BY * kBX; e += NT) {
         const int y = e / kBX, xx = e - y * kBX;
         const int iy = ty0 + y, ix = tx0 + xx;
         if (iy < H && ix < Wd) {
@@ -562,6 +570,12 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc_u8_kernel(const __grid_constant
 #endif
 #ifndef FBF_TC_NBC_64
 #define FBF_TC_NBC_64 16
+#endif
+#ifndef FBF_TC_NT_96
+#define FBF_TC_NT_96 512  // threads per CTA, 96-row tiles
+#endif
+#ifndef FBF_TC_NT_64
+#define FBF_TC_NT_64 512  // threads per CTA, 64-row tiles
 #endif
 #ifndef FBF_TC_PIPE
 #define FBF_TC_PIPE 1  // W <= 16: pipelined schedule (A1, D1, D2 disjoint in TMEM)
@@ -600,7 +614,7 @@ bool make_box_map(const FilterArgs &a, CUtensorMap *map) {
              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-template <int BF, int NSPLIT, int BY, int WCAP, int NBR, int NBC, int PIPE>
+template <int BF, int NSPLIT, int BY, int WCAP, int NBR, int NBC, int PIPE, int NT>
 fbf_status launch_tc_cfg(const FilterArgs &a0, cudaStream_t s) {
   FilterArgs a = a0;
   const TcLayout Ly = tc_layout(a.W, WCAP, NBR, NBC);
@@ -613,10 +627,10 @@ fbf_status launch_tc_cfg(const FilterArgs &a0, cudaStream_t s) {
   if (cudaGetDevice(&dev) != cudaSuccess) return FBF_ERR_CUDA;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid = a.ntiles < sms ? a.ntiles : sms;
-  auto kern = fbf_tc_u8_kernel<BF, NSPLIT, BY, WCAP, NBR, NBC, PIPE>;
+  auto kern = fbf_tc_u8_kernel<BF, NSPLIT, BY, WCAP, NBR, NBC, PIPE, NT>;
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Ly.bytes) != cudaSuccess)
     return FBF_ERR_CUDA;
-  kern<<<grid, kNT, Ly.bytes, s>>>(a, map, use_tma);
+  kern<<<grid, NT, Ly.bytes, s>>>(a, map, use_tma);
   return cuda_status(cudaGetLastError());
 }
 
@@ -626,11 +640,11 @@ fbf_status launch_tc_cfg(const FilterArgs &a0, cudaStream_t s) {
 // otherwise FP16 operands, split data, single weights (2 products).
 fbf_status launch_tc_u8(const FilterArgs &a, int bf16, cudaStream_t s) {
   if (a.W <= 16)
-    return bf16 ? launch_tc_cfg<1, 3, 96, 16, FBF_TC_NBR, FBF_TC_NBC_96, FBF_TC_PIPE>(a, s)
-                : launch_tc_cfg<0, 2, 96, 16, FBF_TC_NBR, FBF_TC_NBC_96, FBF_TC_PIPE>(a, s);
+    return bf16 ? launch_tc_cfg<1, 3, 96, 16, FBF_TC_NBR, FBF_TC_NBC_96, FBF_TC_PIPE, FBF_TC_NT_96>(a, s)
+                : launch_tc_cfg<0, 2, 96, 16, FBF_TC_NBR, FBF_TC_NBC_96, FBF_TC_PIPE, FBF_TC_NT_96>(a, s);
   if (a.W <= 32)
-    return bf16 ? launch_tc_cfg<1, 3, 64, 32, FBF_TC_NBR, FBF_TC_NBC_64, 0>(a, s)
-                : launch_tc_cfg<0, 2, 64, 32, FBF_TC_NBR, FBF_TC_NBC_64, 0>(a, s);
+    return bf16 ? launch_tc_cfg<1, 3, 64, 32, FBF_TC_NBR, FBF_TC_NBC_64, 0, FBF_TC_NT_64>(a, s)
+                : launch_tc_cfg<0, 2, 64, 32, FBF_TC_NBR, FBF_TC_NBC_64, 0, FBF_TC_NT_64>(a, s);
   return FBF_ERR_RANGE;
 }
 
