@@ -6,8 +6,9 @@ sigma_s in {3, 5, 10} x sigma_r in {20, 40}, Gaussian spatial and range kernels,
 coefficients fitted to eps = 1e-3 (K = 17 for sigma_r = 20, K = 9 for 40),
 REFLECT border.  The coefficient fit is host work done once and reported apart.
 
-Forms: fp32 (fused FP32 FMA kernel), tc_fp16 and tc_bf16 (tensor-core
-kernels); all three are timed (interleaved step by step) and the headline
+Forms: fp32 (fused FP32 FMA kernel), tc_fp16, tc_bf16 and tc_fp16_single
+(tensor-core kernels: split FP16 data, split BF16 data and weights, FP16
+rounded once); all are timed (interleaved step by step) and the headline
 `form` is the fastest whose output stays within 0.5 gray of the FP64 oracle on
 the CPU-baseline slab.
 
@@ -185,23 +186,28 @@ def cpu_baseline(img, slab_rows: int):
 
 # ------------------------------------------------------------------ main ---
 
-FORMS_ALL = ["fp32", "tc_fp16", "tc_bf16"]
-FORM_DTYPE = {"fp32": "f32", "tc_fp16": "f16", "tc_bf16": "bf16"}
+FORMS_ALL = ["fp32", "tc_fp16", "tc_bf16", "tc_fp16_single"]
+FORM_DTYPE = {"fp32": "f32", "tc_fp16": "f16", "tc_bf16": "bf16", "tc_fp16_single": "f16"}
 FORM_KERNEL = {"fp32": "fbf_fp32_u8_kernel", "tc_fp16": "fbf_tc_u8_kernel<0,2,..>",
-               "tc_bf16": "fbf_tc_u8_kernel<1,3,..>"}
+               "tc_bf16": "fbf_tc_u8_kernel<1,3,..>", "tc_fp16_single": "fbf_tc_u8_kernel<0,1,..>"}
+TC_NSPLIT = {"tc_fp16": 2, "tc_bf16": 3, "tc_fp16_single": 1}
 
 
 def tc_issued_flops(K: int, W: int, form: str) -> float:
-    """Dense MMA flops the tensor-core kernel issues for one 2048x2048 launch
-    (mirrors its tiling: 32-column tiles, 96 rows for W <= 16 else 64; per
-    harmonic 4 channels x 2 output blocks x kc chunks for the row pass and
-    BY/16 x kc for the column pass; 2 or 3 split products per step)."""
-    nsplit = 3 if form == "tc_bf16" else 2
-    BY = 96 if W <= 16 else 64
-    kc = (16 + 2 * W + 15) // 16
+    """Dense MMA flops the tensor-core kernel issues for one 2048x2048 launch,
+    band padding and split products included (mirrors its tiling: 32 x BY tiles,
+    BY = 96 for W <= 16 else 64; per harmonic and tile, the row pass issues 4
+    channels x ceil((32 + 2W) / 16) K-chunks of M = 128, N = 32, K = 16, the
+    column pass BY / NBC output blocks x ceil((NBC + 2W) / 16) chunks of
+    N = NBC, NBC = 32 for BY = 96 else 16; each chunk once per split product)."""
+    nsplit = TC_NSPLIT[form]
+    BY, NBC = (96, 32) if W <= 16 else (64, 16)
+    kcr = (32 + 2 * W + 15) // 16
+    kcc = (NBC + 2 * W + 15) // 16
     tiles = math.ceil(W_IMG / 32) * math.ceil(H / BY)
-    mmas = (4 * 2 * kc + (BY // 16) * kc) * nsplit
-    return tiles * K * mmas * 2.0 * 128 * 16 * 16
+    row = 4 * kcr * (2.0 * 128 * 32 * 16)
+    col = (BY // NBC) * kcc * (2.0 * 128 * NBC * 16)
+    return tiles * K * (row + col) * nsplit
 
 
 def tensor_peak():

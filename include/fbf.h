@@ -64,13 +64,19 @@ typedef enum { FBF_U8 = 0, FBF_F32 = 1 } fbf_dtype;
 /* Arithmetic form of the device filter.  FP32: every step in FP32 on the FMA
  * pipe.  TC_FP16 / TC_BF16: both 1-D passes as banded-Toeplitz products on the
  * tensor cores (tcgen05) with FP32 accumulation; data split into hi + lo
- * 16-bit parts (BF16 splits the weights too); uint8 input only.  AUTO: the
- * faster of FP32 and TC_FP16 for the window (TC_FP16 from W = 10 up). */
+ * 16-bit parts (BF16 splits the weights too); uint8 input only.
+ * TC_FP16_SINGLE: the same with data and weights rounded to FP16 once (half the
+ * tensor-core products); on 8-bit images its error against the exact
+ * Algorithm 1 stays near 0.02-0.05 gray level for sigma_r >= 20 and grows as
+ * sigma_r shrinks (about 0.1 at sigma_r = 5), where the split forms stay below
+ * 2e-3.  AUTO: the faster of FP32 and TC_FP16 for the window (TC_FP16 from
+ * W = 10 up); AUTO never picks TC_FP16_SINGLE. */
 typedef enum {
   FBF_FORM_AUTO = 0,
   FBF_FORM_FP32 = 1,
   FBF_FORM_TC_FP16 = 2,
-  FBF_FORM_TC_BF16 = 3
+  FBF_FORM_TC_BF16 = 3,
+  FBF_FORM_TC_FP16_SINGLE = 4
 } fbf_form;
 
 #define FBF_KMAX 256 /* maximum number of coefficients K                 */

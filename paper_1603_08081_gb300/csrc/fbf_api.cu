@@ -75,15 +75,16 @@ extern "C" fbf_status fbf_filter(const fbf_params *p, const void *d_in, fbf_dtyp
   if (st != FBF_OK) return st;
   if (H == 0 || Wd == 0) return FBF_OK;
   const fbf_form form = p->form;
-  if (form != FBF_FORM_AUTO && form != FBF_FORM_FP32 && form != FBF_FORM_TC_FP16 && form != FBF_FORM_TC_BF16)
-    return FBF_ERR_INVALID_ARGUMENT;
+  const bool tc = form == FBF_FORM_TC_FP16 || form == FBF_FORM_TC_BF16 || form == FBF_FORM_TC_FP16_SINGLE;
+  if (form != FBF_FORM_AUTO && form != FBF_FORM_FP32 && !tc) return FBF_ERR_INVALID_ARGUMENT;
   if (dtype == FBF_F32) {
-    if (form == FBF_FORM_TC_FP16 || form == FBF_FORM_TC_BF16) return FBF_ERR_UNSUPPORTED;
+    if (tc) return FBF_ERR_UNSUPPORTED;
     if (a.W > f32_wmax()) return FBF_ERR_RANGE;
     return launch_fp32_f32(a, stream);
   }
   if (form == FBF_FORM_TC_FP16) return launch_tc_u8(a, 0, stream);
   if (form == FBF_FORM_TC_BF16) return launch_tc_u8(a, 1, stream);
+  if (form == FBF_FORM_TC_FP16_SINGLE) return launch_tc_u8(a, 2, stream);
   // AUTO: the tensor-core FP16 form from W = 10 up (faster there on GB300:
   // W = 15: 0.62 vs 0.82 ms, W = 30: 1.06 vs 1.51 ms on a 2048^2 image with
   // K = 17); the FP32 form below (W = 9: 0.60 vs 0.62 ms).

@@ -105,7 +105,8 @@ extern "C" fbf_status fbf_plan_create(const fbf_image_desc *descs, int n, fbf_fo
   if (n < 0 || (n > 0 && !descs)) return FBF_ERR_INVALID_ARGUMENT;
   if (border != FBF_BORDER_REFLECT && border != FBF_BORDER_TRUNCATE) return FBF_ERR_INVALID_ARGUMENT;
   if (form != FBF_FORM_AUTO && form != FBF_FORM_FP32) {
-    if (form == FBF_FORM_TC_FP16 || form == FBF_FORM_TC_BF16) return FBF_ERR_UNSUPPORTED;
+    if (form == FBF_FORM_TC_FP16 || form == FBF_FORM_TC_BF16 || form == FBF_FORM_TC_FP16_SINGLE)
+      return FBF_ERR_UNSUPPORTED;
     return FBF_ERR_INVALID_ARGUMENT;
   }
   std::vector<ImageParams> imgs(n);

@@ -46,7 +46,8 @@ fbf_status pack_filter_args(const fbf_params *p, const void *d_in, fbf_dtype dty
                             FilterArgs *a);
 
 fbf_status launch_fp32_u8(const FilterArgs &a, cudaStream_t s);
-fbf_status launch_tc_u8(const FilterArgs &a, int bf16, cudaStream_t s);
+// mode: 0 = FP16 split data, 1 = BF16 split data and weights, 2 = FP16 single.
+fbf_status launch_tc_u8(const FilterArgs &a, int mode, cudaStream_t s);
 fbf_status tc_read_clear_error(unsigned int *code);
 
 // FP32-input forward and the adjoint (fbf_f32.cu); W <= f32_wmax().

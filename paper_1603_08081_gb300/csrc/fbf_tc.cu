@@ -28,7 +28,9 @@
 //             own partial: cos for the G_r / F_r channels, sin for G_i / F_i.
 //
 // P = partial(F_r) + partial(F_i), Q = partial(G_r) + partial(G_i) are combined
-// once per tile, and fhat = P / Q is written.
+// once per tile, and fhat = P / Q + c0 is written.  The f channels carry
+// (f - c0) with c0 = T / 2 instead of f: the sums become P - c0 Q, the ratio is
+// unchanged in exact arithmetic, and the magnitudes rounded to 16 bits halve.
 //
 // The kernel is persistent (one CTA per SM walks the tiles blockIdx.x,
 // blockIdx.x + gridDim.x, ...; TMEM, barriers and Toeplitz blocks are set up
@@ -39,7 +41,8 @@
 // reflected indices; under TRUNCATE every tile does (out-of-image box entries
 // become the zero-channel sentinel by their coordinates).  Precision: the data are split
 // hi + lo; FP16 uses one weight part (2 products per step), BF16 splits the
-// weights too (3 products).  Table entries, the phase (exact integer
+// weights too (3 products); the single FP16 form rounds data and weights once
+// (1 product per step: half the MMAs, table entries and re-split stores).  Table entries, the phase (exact integer
 // reduction), the K-term accumulation and the ratio stay in FP32.
 #include <cuda.h>
 #include <cuda_bf16.h>
@@ -144,12 +147,12 @@ __device__ __forceinline__ float from16(unsigned short x) {
 // Per-harmonic tables (see above); copies written rotated so the 8 stores of one
 // value land in 8 different bank groups.
 template <int BF, int NT>
-__device__ __forceinline__ void build_lut(uint4 *L16, float2 *Lf, int n, int twoT, float T, int tid) {
+__device__ __forceinline__ void build_lut(uint4 *L16, float2 *Lf, int n, int twoT, float T, float c0, int tid) {
   for (int v = tid; v < 256; v += NT) {
     const int m = (n * v) % twoT;  // exact phase index: n*omega*v = pi * m / T (mod 2 pi)
     float sn, cs;
     sincospif((float)m / T, &sn, &cs);
-    const float fv = (float)v;
+    const float fv = (float)v - c0;  // centred intensity
     uint4 e;
     split2<BF>(cs, sn, e.x, e.z);
     split2<BF>(fv * cs, fv * sn, e.y, e.w);
@@ -186,7 +189,8 @@ __device__ __forceinline__ void build_toeplitz(unsigned char *B, int nblocks, in
   }
 }
 
-// BF: 0 = FP16, 1 = BF16.  NSPLIT: 2 = data hi/lo x weights hi; 3 = plus data hi x weights lo.
+// BF: 0 = FP16, 1 = BF16.  NSPLIT: 1 = data hi x weights hi; 2 = data hi/lo x
+// weights hi; 3 = plus data hi x weights lo.
 // BY: output rows per tile (BY + 2 * WCAP <= 128).  NBR / NBC: MMA N (output
 // block) of the row / column pass; bigger blocks issue fewer, larger MMAs at the
 // price of more zero taps inside each block.  NT: threads (256 or 512); the
@@ -198,9 +202,12 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
   static_assert(BY + 2 * WCAP <= kLanes && BY % 32 == 0, "halo rows must fit the TMEM lanes");
   static_assert(kBX % NBR == 0 && BY % NBC == 0 && NBR % 16 == 0 && NBC % 16 == 0, "output blocks");
   static_assert(BY - NBC + 16 * ((NBC + 2 * WCAP + 15) / 16) <= kLanes, "column-pass K fits A2");
-  // A1 (8 regions of KX/2 columns) must fit below D1: 256 columns when
+  static_assert(NSPLIT >= 1 && NSPLIT <= 3, "products per step");
+  constexpr int kParts = NSPLIT > 1 ? 2 : 1;  // data parts held in A1 / A2 (hi, lo)
+  // A1 (4 kParts regions of KX/2 columns) must fit below D1: 256 columns when
   // pipelined (D1 at 256, D2 at 384), 384 otherwise (D1 at 384, D2 over A1).
-  static_assert(4 * (kBX - NBR + 16 * ((NBR + 2 * WCAP + 15) / 16)) <= (PIPE ? 256 : 384), "A1 fits below D1");
+  static_assert(2 * kParts * (kBX - NBR + 16 * ((NBR + 2 * WCAP + 15) / 16)) <= (PIPE ? 256 : 384),
+                "A1 fits below D1");
   static_assert(NT == 256 || NT == 512, "two or four warp groups");
   constexpr int kGroups = NT / 128;   // warp groups; h = warp / 4 in [0, kGroups)
   constexpr int BYH = BY / kGroups;   // output rows per thread in the demodulation
@@ -231,6 +238,7 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
   const int H = a.H, Wd = a.Wd, HY = BY + 2 * W, HX = kBX + 2 * W;
   const int kcr = Ly.kcr, kcc = Ly.kcc, A1C = Ly.A1C, KX = Ly.KX;
   const bool reflect = a.border == FBF_BORDER_REFLECT;
+  const float c0 = 0.5f * a.T;  // intensity centre
   constexpr unsigned short kScale = kCopies * sizeof(uint4), kSent = kSentinel * kCopies * sizeof(uint4);
 
   // Whether a tile's halo comes through the TMA box: always under TRUNCATE,
@@ -300,24 +308,33 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
 #pragma unroll 1
     for (int u = h; u < A1C / 4; u += kGroups) {
       const int col = 4 * u;
-      uint4 e[8];
+      uint4 e[8];  // table entries of 8 ext columns (the single form reads the hi half only)
 #pragma unroll
-      for (int j = 0; j < 8; ++j) e[j] = *reinterpret_cast<const uint4 *>(L16 + tcol[(2 * col + j) * kPT]);
-      uint32_t v[8][4];  // [channel * 2 + part][column]
+      for (int j = 0; j < 8; ++j) {
+        if (kParts == 2) {
+          e[j] = *reinterpret_cast<const uint4 *>(L16 + tcol[(2 * col + j) * kPT]);
+        } else {
+          const uint2 hi = *reinterpret_cast<const uint2 *>(L16 + tcol[(2 * col + j) * kPT]);
+          e[j] = make_uint4(hi.x, hi.y, 0u, 0u);
+        }
+      }
+      uint32_t v[8][4];  // [channel * kParts + part][column]
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const uint4 a0 = e[2 * j], a1 = e[2 * j + 1];
-        v[0][j] = prmt(a0.x, a1.x, 0x5410);  // cos hi
-        v[2][j] = prmt(a0.x, a1.x, 0x7632);  // sin hi
-        v[4][j] = prmt(a0.y, a1.y, 0x5410);  // f cos hi
-        v[6][j] = prmt(a0.y, a1.y, 0x7632);  // f sin hi
-        v[1][j] = prmt(a0.z, a1.z, 0x5410);  // cos lo
-        v[3][j] = prmt(a0.z, a1.z, 0x7632);  // sin lo
-        v[5][j] = prmt(a0.w, a1.w, 0x5410);  // f cos lo
-        v[7][j] = prmt(a0.w, a1.w, 0x7632);  // f sin lo
+        v[0 * kParts][j] = prmt(a0.x, a1.x, 0x5410);  // cos hi
+        v[1 * kParts][j] = prmt(a0.x, a1.x, 0x7632);  // sin hi
+        v[2 * kParts][j] = prmt(a0.y, a1.y, 0x5410);  // f cos hi
+        v[3 * kParts][j] = prmt(a0.y, a1.y, 0x7632);  // f sin hi
+        if (kParts == 2) {
+          v[1][j] = prmt(a0.z, a1.z, 0x5410);  // cos lo
+          v[3][j] = prmt(a0.z, a1.z, 0x7632);  // sin lo
+          v[5][j] = prmt(a0.w, a1.w, 0x5410);  // f cos lo
+          v[7][j] = prmt(a0.w, a1.w, 0x7632);  // f sin lo
+        }
       }
 #pragma unroll
-      for (int cp2 = 0; cp2 < 8; ++cp2)
+      for (int cp2 = 0; cp2 < 4 * kParts; ++cp2)
         tmem_st_x4(tmem + lane_base + kA1 + (uint32_t)(cp2 * A1C + col), v[cp2][0], v[cp2][1], v[cp2][2],
                    v[cp2][3]);
     }
@@ -340,7 +357,7 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
 #pragma unroll
         for (int j = 0; j < kBX / NBR; ++j)
           mma_ts(tmem + kD1 + (uint32_t)(c * 32 + j * NBR),
-                 tmem + kA1 + (uint32_t)((2 * c + ap) * A1C + (j * NBR / 16 + i) * 8), bd, idesc_row,
+                 tmem + kA1 + (uint32_t)((kParts * c + ap) * A1C + (j * NBR / 16 + i) * 8), bd, idesc_row,
                  (i > 0 || pp > 0) ? 1u : 0u);
       }
     mma_commit(mbarR);
@@ -367,7 +384,7 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
       split2<BF>(__uint_as_float(v[2][2 * k + 1]), __uint_as_float(v[3][2 * k + 1]), vh.w, vl.w);
       const int mg = (XPT / 2) * h + k;
       *reinterpret_cast<uint4 *>(rowp + mg * 128) = vh;
-      *reinterpret_cast<uint4 *>(rowp + kA2Part + mg * 128) = vl;
+      if (kParts == 2) *reinterpret_cast<uint4 *>(rowp + kA2Part + mg * 128) = vl;
     }
     fence_proxy_async_smem();
   };
@@ -455,7 +472,7 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
       stage_tile<NT>(static_cast<const unsigned char *>(a.in), a.in_pitch, H, Wd, a.border, ty0 - W, tx0 - W, HY,
                       HX, kLanes, KX, tileT, kPT, kScale, kSent);
     }
-    build_lut<BF, NT>(lut16, lutf, 0, a.twoT, a.T, tid);
+    build_lut<BF, NT>(lut16, lutf, 0, a.twoT, a.T, c0, tid);
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
@@ -484,7 +501,7 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
         fence_before_sync();
         __syncthreads();
         if (row_issuer) issue_row();
-        if (n + 1 < a.K) build_lut<BF, NT>(lut16, lutf + ((n + 1) % 3) * kLutStride, n + 1, a.twoT, a.T, tid);
+        if (n + 1 < a.K) build_lut<BF, NT>(lut16, lutf + ((n + 1) % 3) * kLutStride, n + 1, a.twoT, a.T, c0, tid);
         if (!(ok = wait_mma(mbarR, phR))) break;
         resplit();
         fence_before_sync();
@@ -503,7 +520,7 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
       fence_before_sync();
       __syncthreads();
       if (row_issuer) issue_row();
-      if (a.K > 1) build_lut<BF, NT>(lut16, lutf + 1 * kLutStride, 1, a.twoT, a.T, tid);
+      if (a.K > 1) build_lut<BF, NT>(lut16, lutf + 1 * kLutStride, 1, a.twoT, a.T, c0, tid);
       ok = wait_mma(mbarR, phR);
       if (ok) {
         resplit();
@@ -518,7 +535,7 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
         if (n + 1 < a.K && row_issuer) issue_row();  // R(n+1): A1 -> D1
         // Tables of n+2 while C(n) and R(n+1) run: lut16 (last read by the
         // modulation of n+1, done) and lutf buffer (n+2) % 3 (not read by demod(n)).
-        if (n + 2 < a.K) build_lut<BF, NT>(lut16, lutf + ((n + 2) % 3) * kLutStride, n + 2, a.twoT, a.T, tid);
+        if (n + 2 < a.K) build_lut<BF, NT>(lut16, lutf + ((n + 2) % 3) * kLutStride, n + 2, a.twoT, a.T, c0, tid);
         if (!(ok = wait_mma(mbarC, phC))) break;
         demod(n);  // D2, table n
         fence_before_sync();
@@ -545,7 +562,7 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
           const float Q = comb[(0 * BY + y) * kBX + xx] + comb[(1 * BY + y) * kBX + xx];
           const float P = comb[(2 * BY + y) * kBX + xx] + comb[(3 * BY + y) * kBX + xx];
           *reinterpret_cast<float *>(reinterpret_cast<char *>(a.out) + (size_t)iy * a.out_pitch +
-                                     (size_t)ix * sizeof(float)) = P / Q;
+                                     (size_t)ix * sizeof(float)) = P / Q + c0;
         }
       }
     } else if (tid == 0) {
@@ -636,15 +653,22 @@ fbf_status launch_tc_cfg(const FilterArgs &a0, cudaStream_t s) {
 
 }  // namespace
 
-// bf16 != 0: BF16 operands with split weights (3 products per step);
-// otherwise FP16 operands, split data, single weights (2 products).
-fbf_status launch_tc_u8(const FilterArgs &a, int bf16, cudaStream_t s) {
-  if (a.W <= 16)
-    return bf16 ? launch_tc_cfg<1, 3, 96, 16, FBF_TC_NBR, FBF_TC_NBC_96, FBF_TC_PIPE, FBF_TC_NT_96>(a, s)
-                : launch_tc_cfg<0, 2, 96, 16, FBF_TC_NBR, FBF_TC_NBC_96, FBF_TC_PIPE, FBF_TC_NT_96>(a, s);
-  if (a.W <= 32)
-    return bf16 ? launch_tc_cfg<1, 3, 64, 32, FBF_TC_NBR, FBF_TC_NBC_64, 0, FBF_TC_NT_64>(a, s)
-                : launch_tc_cfg<0, 2, 64, 32, FBF_TC_NBR, FBF_TC_NBC_64, 0, FBF_TC_NT_64>(a, s);
+// mode 0: FP16 operands, split data, single weights (2 products per step);
+// 1: BF16 operands, split data and weights (3 products); 2: FP16 operands, data
+// and weights rounded once (1 product; A1 then takes half the TMEM columns, so
+// the 64-row tiles run the pipelined schedule too).
+fbf_status launch_tc_u8(const FilterArgs &a, int mode, cudaStream_t s) {
+  if (mode < 0 || mode > 2) return FBF_ERR_INVALID_ARGUMENT;
+  if (a.W <= 16) {
+    if (mode == 1) return launch_tc_cfg<1, 3, 96, 16, FBF_TC_NBR, FBF_TC_NBC_96, FBF_TC_PIPE, FBF_TC_NT_96>(a, s);
+    if (mode == 2) return launch_tc_cfg<0, 1, 96, 16, FBF_TC_NBR, FBF_TC_NBC_96, FBF_TC_PIPE, FBF_TC_NT_96>(a, s);
+    return launch_tc_cfg<0, 2, 96, 16, FBF_TC_NBR, FBF_TC_NBC_96, FBF_TC_PIPE, FBF_TC_NT_96>(a, s);
+  }
+  if (a.W <= 32) {
+    if (mode == 1) return launch_tc_cfg<1, 3, 64, 32, FBF_TC_NBR, FBF_TC_NBC_64, 0, FBF_TC_NT_64>(a, s);
+    if (mode == 2) return launch_tc_cfg<0, 1, 64, 32, FBF_TC_NBR, FBF_TC_NBC_64, 1, FBF_TC_NT_64>(a, s);
+    return launch_tc_cfg<0, 2, 64, 32, FBF_TC_NBR, FBF_TC_NBC_64, 0, FBF_TC_NT_64>(a, s);
+  }
   return FBF_ERR_RANGE;
 }
 

@@ -22,10 +22,10 @@ FBF_RANGE_GAUSSIAN, FBF_RANGE_EXPONENTIAL = 0, 1
 FBF_SPATIAL_GAUSSIAN, FBF_SPATIAL_BOX = 0, 1
 FBF_BORDER_REFLECT, FBF_BORDER_TRUNCATE = 0, 1
 FBF_U8, FBF_F32 = 0, 1
-FBF_FORM_AUTO, FBF_FORM_FP32, FBF_FORM_TC_FP16, FBF_FORM_TC_BF16 = 0, 1, 2, 3
+FBF_FORM_AUTO, FBF_FORM_FP32, FBF_FORM_TC_FP16, FBF_FORM_TC_BF16, FBF_FORM_TC_FP16_SINGLE = 0, 1, 2, 3, 4
 
 _NAMES = {"gaussian": 0, "exponential": 1, "box": 1, "reflect": 0, "truncate": 1,
-          "auto": 0, "fp32": 1, "tc_fp16": 2, "tc_bf16": 3}
+          "auto": 0, "fp32": 1, "tc_fp16": 2, "tc_bf16": 3, "tc_fp16_single": 4}
 
 
 class fbf_coeffs(C.Structure):
