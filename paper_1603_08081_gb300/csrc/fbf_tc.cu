@@ -144,9 +144,11 @@ __device__ __forceinline__ float from16(unsigned short x) {
   return __half2float(*reinterpret_cast<const __half *>(&x));
 }
 
-// Per-harmonic tables (see above); copies written rotated so the 8 stores of one
-// value land in 8 different bank groups.
-template <int BF, int NT>
+// Per-harmonic tables (see above); copies written rotated so that the stores of
+// neighbouring values land in different bank groups.  SINGLE: the 16-bit table
+// keeps only the hi words (uint2), in 16 copies of 8 bytes (the same 128 bytes
+// per value), so that the modulation's 8-byte gathers are conflict-free too.
+template <int BF, int NT, int SINGLE>
 __device__ __forceinline__ void build_lut(uint4 *L16, float2 *Lf, int n, int twoT, float T, float c0, int tid) {
   for (int v = tid; v < 256; v += NT) {
     const int m = (n * v) % twoT;  // exact phase index: n*omega*v = pi * m / T (mod 2 pi)
@@ -157,11 +159,16 @@ __device__ __forceinline__ void build_lut(uint4 *L16, float2 *Lf, int n, int two
     split2<BF>(cs, sn, e.x, e.z);
     split2<BF>(fv * cs, fv * sn, e.y, e.w);
     const float2 f = make_float2(cs, sn);
+    if (SINGLE) {
+      uint2 *L8 = reinterpret_cast<uint2 *>(L16);
 #pragma unroll
-    for (int j = 0; j < kCopies; ++j) {
-      L16[v * kCopies + ((j + v) & (kCopies - 1))] = e;
-      Lf[v * kCopies + ((j + v) & (kCopies - 1))] = f;
+      for (int j = 0; j < 2 * kCopies; ++j) L8[v * 2 * kCopies + ((j + v) & (2 * kCopies - 1))] = make_uint2(e.x, e.y);
+    } else {
+#pragma unroll
+      for (int j = 0; j < kCopies; ++j) L16[v * kCopies + ((j + v) & (kCopies - 1))] = e;
     }
+#pragma unroll
+    for (int j = 0; j < kCopies; ++j) Lf[v * kCopies + ((j + (v >> 1)) & (kCopies - 1))] = f;
   }
 }
 
@@ -292,7 +299,10 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
   const uint64_t br_desc = smem_desc(smem_u32(smem + Ly.br_off), 128, 256);
   const uint64_t bc_desc = smem_desc(smem_u32(smem + Ly.bc_off), 128, 256);
   const uint64_t a2_desc = smem_desc(smem_u32(A2), kA2Group, 128);
-  const char *L16 = reinterpret_cast<const char *>(lut16 + cp);
+  // Gather base: copy cp of the 8 16-byte entries, or copy lane % 16 of the 16
+  // 8-byte entries of the single form.
+  const char *L16 = kParts == 2 ? reinterpret_cast<const char *>(lut16 + cp)
+                                : reinterpret_cast<const char *>(lut16) + 8 * (lane & (2 * kCopies - 1));
 
   float part[BYH];
   uint32_t cen_pk[BYH / 2] = {};  // lutf byte offsets of this thread's demodulation pixels, two per register
@@ -472,7 +482,7 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
       stage_tile<NT>(static_cast<const unsigned char *>(a.in), a.in_pitch, H, Wd, a.border, ty0 - W, tx0 - W, HY,
                       HX, kLanes, KX, tileT, kPT, kScale, kSent);
     }
-    build_lut<BF, NT>(lut16, lutf, 0, a.twoT, a.T, c0, tid);
+    build_lut<BF, NT, kParts == 1>(lut16, lutf, 0, a.twoT, a.T, c0, tid);
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
@@ -501,7 +511,8 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
         fence_before_sync();
         __syncthreads();
         if (row_issuer) issue_row();
-        if (n + 1 < a.K) build_lut<BF, NT>(lut16, lutf + ((n + 1) % 3) * kLutStride, n + 1, a.twoT, a.T, c0, tid);
+        if (n + 1 < a.K)
+          build_lut<BF, NT, kParts == 1>(lut16, lutf + ((n + 1) % 3) * kLutStride, n + 1, a.twoT, a.T, c0, tid);
         if (!(ok = wait_mma(mbarR, phR))) break;
         resplit();
         fence_before_sync();
@@ -520,7 +531,7 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
       fence_before_sync();
       __syncthreads();
       if (row_issuer) issue_row();
-      if (a.K > 1) build_lut<BF, NT>(lut16, lutf + 1 * kLutStride, 1, a.twoT, a.T, c0, tid);
+      if (a.K > 1) build_lut<BF, NT, kParts == 1>(lut16, lutf + 1 * kLutStride, 1, a.twoT, a.T, c0, tid);
       ok = wait_mma(mbarR, phR);
       if (ok) {
         resplit();
@@ -535,7 +546,8 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
         if (n + 1 < a.K && row_issuer) issue_row();  // R(n+1): A1 -> D1
         // Tables of n+2 while C(n) and R(n+1) run: lut16 (last read by the
         // modulation of n+1, done) and lutf buffer (n+2) % 3 (not read by demod(n)).
-        if (n + 2 < a.K) build_lut<BF, NT>(lut16, lutf + ((n + 2) % 3) * kLutStride, n + 2, a.twoT, a.T, c0, tid);
+        if (n + 2 < a.K)
+          build_lut<BF, NT, kParts == 1>(lut16, lutf + ((n + 2) % 3) * kLutStride, n + 2, a.twoT, a.T, c0, tid);
         if (!(ok = wait_mma(mbarC, phC))) break;
         demod(n);  // D2, table n
         fence_before_sync();
@@ -583,7 +595,7 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
 #define FBF_TC_NBR 32
 #endif
 #ifndef FBF_TC_NBC_96
-#define FBF_TC_NBC_96 32
+#define FBF_TC_NBC_96 48
 #endif
 #ifndef FBF_TC_NBC_64
 #define FBF_TC_NBC_64 16
