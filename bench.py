@@ -210,6 +210,28 @@ def tc_issued_flops(K: int, W: int, form: str) -> float:
     return tiles * K * (row + col) * nsplit
 
 
+def recorded_traffic(kernel: str, launch: str):
+    """DRAM bytes per launch (read + write) of `kernel` on `launch`, from the ncu
+    capture recorded in profiles/traffic.json, or None when there is no record
+    or the kernel's sources have changed since the capture (hash mismatch)."""
+    import hashlib
+
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as fh:
+            rec = json.load(fh)[kernel]
+        if rec["launch"] != launch:
+            return None
+        h = hashlib.sha256()
+        for path in rec["sources"]:
+            with open(os.path.join(ROOT, path), "rb") as fh:
+                h.update(fh.read())
+        if h.hexdigest() != rec["sources_sha256"]:
+            return None
+        return int(rec["dram_bytes_read"]) + int(rec["dram_bytes_write"])
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def tensor_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -380,7 +402,7 @@ def run_ours(args):
             alg = algorithmic_flops_per_pixel(K_dom, W_dom) * H * W_IMG / t_dom / 1e12
             roof = {"bound": "tensor", "kernel": FORM_KERNEL[f], "launch": launch, "achieved": round(ach, 3),
                     "peak": round(tpeak, 1), "unit": "TFLOP/s", "frac": round(ach / tpeak, 4),
-                    "traffic": None, "peak_source": tpeak_src,
+                    "traffic": recorded_traffic(FORM_KERNEL[f], launch), "peak_source": tpeak_src,
                     "fir_equivalent_tflops": round(alg, 3),
                     "fir_equivalent_frac_of_fp32_peak": round(alg / fp32_peak, 4)}
         per_form[f] = {"value": world * px_step * args.steps / (total_ms * 1e-3) / 1e6,
