@@ -67,6 +67,8 @@ def _load():
             lib.orc_grad_direct.restype = None
             lib.orc_grad_at.argtypes = [dp, dp, i, i, dp, i, i, dp, i, d, ip, ip, lp, dp]
             lib.orc_grad_at.restype = None
+            lib.orc_local_range.argtypes = [dp, i, i, i, i]
+            lib.orc_local_range.restype = d
             _lib = lib
     return _lib
 
@@ -235,6 +237,14 @@ def grad_at(f, g, w1, border: int, d, T: float, points):
     _load().orc_grad_at(_dp(f), _dp(g), H, Wd, _dp(w1), W, int(border), _dp(d), len(d), float(T),
                         _ip(ys), _ip(xs), n, _dp(out))
     return out
+
+
+def local_range(f, W: int, border: int = 0) -> float:
+    """Dynamic range T of f over the window [-W, W]^2 (the definition opening
+    Sec. III); see ``orc_local_range`` in the C source."""
+    f = _img(f)
+    H, Wd = f.shape
+    return float(_load().orc_local_range(_dp(f), H, Wd, int(W), int(border)))
 
 
 def bound12(T: float, eps: float, w0: float) -> float:

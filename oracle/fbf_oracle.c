@@ -19,6 +19,8 @@
  *   orc_alg1           Algorithm 1 in the paper's complex notation, eqs. (4)-(5)
  *   orc_grad_direct    d/df(m) of sum_i g(i) fhat(i), fhat from eq. (9)
  *   orc_grad_at        the same derivative at sampled pixels only
+ *   orc_local_range    the dynamic range T of the image over the window Omega,
+ *                      the definition that opens Sec. III
  *
  * The fit uses Householder QR, deliberately not the modified Gram-Schmidt
  * recursion of Algorithm 2, so the two are independent: the least-squares
@@ -508,4 +510,40 @@ void orc_grad_at(const double *f, const double *g, int H, int Wd, const double *
     }
     out[p] = acc;
   }
+}
+
+/*
+ * Dynamic range of f over the window (the definition of T at the start of
+ * Sec. III): the largest |f(i - j) - f(i)| over every pixel i and every offset
+ * j in Omega = [-W, W]^2, read with f(i) as the centre (the paper's f(j) there
+ * is taken as a misprint).  Neighbours outside the image are skipped
+ * (TRUNCATE) or mirrored (REFLECT).  Written out directly: O(W^2) per pixel.
+ */
+double orc_local_range(const double *f, int H, int Wd, int W, int border) {
+  double T = 0.0;
+#pragma omp parallel for reduction(max : T) schedule(static)
+  for (long y = 0; y < H; ++y) {
+    for (long x = 0; x < Wd; ++x) {
+      const double c = f[y * Wd + x];
+      for (long dy = -W; dy <= W; ++dy) {
+        long sy = y - dy;
+        if (border == ORC_BORDER_REFLECT) {
+          sy = orc_reflect(sy, H);
+        } else if (sy < 0 || sy >= H) {
+          continue;
+        }
+        for (long dx = -W; dx <= W; ++dx) {
+          long sx = x - dx;
+          if (border == ORC_BORDER_REFLECT) {
+            sx = orc_reflect(sx, Wd);
+          } else if (sx < 0 || sx >= Wd) {
+            continue;
+          }
+          const double t = fabs(f[sy * Wd + sx] - c);
+          if (t > T) T = t;
+        }
+      }
+    }
+  }
+  return T;
 }

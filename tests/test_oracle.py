@@ -306,3 +306,53 @@ def test_gradient_at_points_equals_full_gradient(border, shape, W):
     ys, xs = np.mgrid[0:shape[0], 0:shape[1]]
     pts = O.grad_at(f, g, w1, border, fit.d, 1.0, (ys.ravel(), xs.ravel()))
     assert np.max(np.abs(pts - full.ravel())) <= 1e-11 * max(1.0, np.max(np.abs(full)))
+
+
+# ---- local dynamic range T (the definition opening Sec. III) ----------------
+
+@pytest.mark.parametrize("W", [0, 1, 2, 5, 9])
+@pytest.mark.parametrize("shape", [(1, 1), (1, 17), (13, 1), (20, 31), (7, 40)])
+def test_local_range_equals_max_min_filters(shape, W):
+    """Max/min filters with edge replication (scipy) see the same values as the
+    clipped window (a replicated pixel lies inside it), so
+    T = max(maxfilt(f) - f, f - minfilt(f)) must hold for both borders."""
+    ndi = pytest.importorskip("scipy.ndimage")
+    from paper_1603_08081_gb300.synth import make_image
+
+    f = make_image(*shape, seed=50 + W).astype(np.float64)
+    size = 2 * W + 1
+    want = max(np.max(ndi.maximum_filter(f, size=size, mode="nearest") - f),
+               np.max(f - ndi.minimum_filter(f, size=size, mode="nearest")))
+    for border in (O.BORDER_REFLECT, O.BORDER_TRUNCATE):
+        assert O.local_range(f, W, border) == want
+
+
+def test_local_range_closed_forms():
+    rng = np.random.default_rng(3)
+    f = rng.integers(0, 256, size=(12, 15)).astype(np.float64)
+    # W = 0: every window is the pixel itself
+    assert O.local_range(f, 0) == 0.0
+    # a window covering the whole image: the full dynamic range
+    assert O.local_range(f, 20) == f.max() - f.min()
+    # constant image
+    assert O.local_range(np.full((9, 9), 77.0), 4) == 0.0
+    # a vertical step a | b: any window crossing it sees |a - b|, none sees more
+    step = np.full((10, 12), 40.0)
+    step[:, 6:] = 217.0
+    for W in (1, 3, 11):
+        assert O.local_range(step, W) == 177.0
+    # an isolated spike of height s on a flat background is seen at distance <= W
+    spike = np.zeros((15, 15))
+    spike[7, 7] = 90.0
+    assert O.local_range(spike, 2) == 90.0
+    # monotone in W
+    g = rng.integers(0, 256, size=(30, 30)).astype(np.float64)
+    vals = [O.local_range(g, W) for W in range(0, 8)]
+    assert all(a <= b for a, b in zip(vals, vals[1:]))
+
+
+def test_local_range_gives_fewer_terms():
+    """Sec. III: a smaller T needs fewer terms for the same sigma_r and eps (here
+    K = 10 at T = 217 against K = 11 at T = 255 for sigma_r = 30, eps = 1e-3)."""
+    assert O.fit(O.RANGE_GAUSSIAN, 30.0, 217.0, 1e-3).K == 10
+    assert O.fit(O.RANGE_GAUSSIAN, 30.0, 255.0, 1e-3).K == 11
