@@ -241,6 +241,23 @@ fbf_status fbf_filter_backward_noalloc(const fbf_params *p, const float *d_in, c
                                        const float *d_out_fwd, float *d_gin, int H, int Wd, size_t pitch,
                                        cudaStream_t stream);
 
+/* Dynamic range T of an 8-bit image over the window Omega = [-W, W]^2: the
+ * quantity defined at the start of Sec. III, T = max over pixels i and offsets
+ * j in Omega of |f(i - j) - f(i)|, neighbours outside the image excluded (the
+ * mirrored neighbours of REFLECT are image pixels inside the same clipped
+ * window, so both borders give the same T).  Passing this T (instead of the
+ * full 255) to fbf_fit_coeffs gives omega = pi / T and, for the same sigma_r
+ * and eps, no more -- often fewer -- terms (Sec. III).
+ *
+ * d_in: H x Wd bytes (dtype FBF_U8), row pitch `pitch` bytes >= Wd.  d_T: one
+ * device uint32 that receives T in 0..255; it is zeroed on `stream` first,
+ * then written by the kernel (asynchronous: read it after the stream).  W in
+ * 0..FBF_WMAX.  Empty images give T = 0.  Errors: FBF_ERR_INVALID_ARGUMENT
+ * (null pointers, negative sizes, pitch < Wd), FBF_ERR_UNSUPPORTED (float
+ * input), FBF_ERR_RANGE (W > FBF_WMAX).  Allocates nothing. */
+fbf_status fbf_local_range(const void *d_in, fbf_dtype dtype, int H, int Wd, size_t pitch, int W,
+                           unsigned int *d_T, cudaStream_t stream);
+
 /* Half window actually used for the parameters (W, or ceil(3 sigma_s) when
  * W <= 0), or -1 when invalid.  Host only. */
 int fbf_resolve_window(const fbf_params *p);

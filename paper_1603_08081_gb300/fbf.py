@@ -82,6 +82,8 @@ def _load():
     lib.fbf_plan_destroy.restype = i
     lib.fbf_plan_size.argtypes = [p, C.POINTER(i), C.POINTER(i)]
     lib.fbf_plan_size.restype = i
+    lib.fbf_local_range.argtypes = [p, i, i, i, sz, i, p, p]
+    lib.fbf_local_range.restype = i
     lib.fbf_resolve_window.argtypes = [C.POINTER(fbf_params)]
     lib.fbf_resolve_window.restype = i
     lib.fbf_device_error.argtypes = [C.POINTER(C.c_uint)]
@@ -174,6 +176,28 @@ def fbf_filter(params: fbf_params, x, out=None, stream=None):
     if st != FBF_OK:
         raise FbfError(st, "fbf_filter")
     return out
+
+
+def fbf_local_range(x, W: int, out=None, stream=None) -> int:
+    """Dynamic range T of a uint8 CUDA image over the window [-W, W]^2 (see
+    include/fbf.h).  Writes it to `out` (a 1-element int32 CUDA tensor, allocated
+    when None) and returns it as an int (synchronises the stream)."""
+    import torch
+
+    if x.dim() != 2 or not x.is_cuda or x.dtype != torch.uint8:
+        raise TypeError("fbf_local_range expects a 2-D uint8 CUDA tensor")
+    if x.stride(1) != 1:
+        x = x.contiguous()
+    if out is None:
+        out = torch.empty(1, dtype=torch.int32, device=x.device)
+    H, Wd = x.shape
+    sh = _stream_handle(stream)
+    st = lib.fbf_local_range(C.c_void_p(x.data_ptr()), FBF_U8, H, Wd, x.stride(0), int(W),
+                             C.c_void_p(out.data_ptr()), sh)
+    if st != FBF_OK:
+        raise FbfError(st, "fbf_local_range")
+    (stream or torch.cuda.current_stream()).synchronize()
+    return int(out.item())
 
 
 def fbf_filter_backward(params: fbf_params, x, g, grad=None, stream=None):
