@@ -310,6 +310,127 @@ def run_batched(fbf, torch, dev, stream, imgs, specs_raw, steps):
     return res
 
 
+def _timed_steps(torch, dev, stream, fn, steps, flush=None):
+    """Mean ms of `fn` over `steps` runs (2 untimed first), CUDA events on
+    `stream` around each run, the L2 flushed before each one outside the events."""
+    for _ in range(2):
+        fn()
+    torch.cuda.synchronize(dev)
+    tot = 0.0
+    for _ in range(steps):
+        if flush is not None:
+            flush()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        e1.synchronize()
+        tot += e0.elapsed_time(e1)
+    return tot / steps
+
+
+def run_exponential(fbf, torch, dev, stream, steps, flush, with_oracle, slab_rows=32):
+    """4096x4096 u8 image (seed 1200), exponential range kernel sigma_r = 20 with
+    a fixed K = 40 (the eps = 1e-3 fit needs K = 255, timed once as a stress
+    case), box W = 8 and Gaussian sigma_s = 5 (W = 15), every form; error of
+    each output against the FP64 oracle on rows 0..slab_rows-1."""
+    from paper_1603_08081_gb300.synth import make_image
+
+    img = make_image(4096, 4096, 1200)
+    x = torch.from_numpy(img).to(dev)
+    y = torch.empty((4096, 4096), dtype=torch.float32, device=dev)
+    npx = img.size
+    c40 = fbf.fbf_fit_coeffs("exponential", 20.0, T, 0.0, 40)
+    c255 = fbf.fbf_fit_coeffs("exponential", 20.0, T, EPS, 0, 0, allow_not_converged=True)
+    spatials = [("box", 1.0, 8), ("gaussian", 5.0, 15)]
+    res = {"workload": "4096x4096 u8 synthetic (seed 1200), exponential range kernel sigma_r=20, "
+                       "K=40 fixed (eps=1e-3 would need K=%d), reflect" % c255.K,
+           "pixels": int(npx), "runs": []}
+    refs = {}
+    if with_oracle:
+        import oracle as O
+
+        fit = O.fit(O.RANGE_EXPONENTIAL, 20.0, T, 0.0, 40)
+        for sp, ss, W in spatials:
+            w1 = O.weights_1d(O.SPATIAL_BOX if sp == "box" else O.SPATIAL_GAUSSIAN, ss, W)
+            refs[sp] = O.alg1(img.astype(np.float64), w1, O.BORDER_REFLECT, fit.d, T, rows=(0, slab_rows))[0]
+    for sp, ss, W in spatials:
+        for f in FORMS_ALL:
+            p = fbf.make_params(c40, ss, W, sp, "reflect", f)
+            ms = _timed_steps(torch, dev, stream, lambda: fbf.fbf_filter(p, x, out=y, stream=stream), steps, flush)
+            row = {"spatial": sp, "W": W, "K": c40.K, "form": f, "ms": round(ms, 4),
+                   "mpix_s": round(npx / ms / 1e3, 1)}
+            if sp in refs:
+                torch.cuda.synchronize(dev)
+                got = y[:slab_rows].cpu().numpy().astype(np.float64)
+                row["max_err_vs_oracle"] = round(float(np.max(np.abs(got - refs[sp]))), 6)
+            res["runs"].append(row)
+    p = fbf.make_params(c255, 5.0, 15, "gaussian", "reflect", "fp32")
+    ms = _timed_steps(torch, dev, stream, lambda: fbf.fbf_filter(p, x, out=y, stream=stream), 2, flush)
+    res["stress_K%d_fp32_gaussian" % c255.K] = {"ms": round(ms, 3), "mpix_s": round(npx / ms / 1e3, 1)}
+    return res
+
+
+def run_differentiation(fbf, torch, dev, stream, steps, with_oracle):
+    """16 float32 512x512 images (seeds 1400+i, u8/255, T = 1), sigma_s = 4
+    (W = 12), sigma_r = 0.1, 256 levels, eps = 1e-3: forward + hand-written
+    adjoint through the autograd Function for d(sum(g * f_BF))/df, g ~ N(0, 1)
+    (seed 1499)."""
+    from paper_1603_08081_gb300.synth import make_grad, make_image_f32
+
+    n, S = 16, 512
+    xs = torch.stack([torch.from_numpy(make_image_f32(S, S, 1400 + i)) for i in range(n)]).to(dev)
+    gs = torch.stack([torch.from_numpy(make_grad(S, S, 1499 + i)) for i in range(n)]).to(dev)
+    c = fbf.fbf_fit_coeffs("gaussian", 0.1, 1.0, EPS, 0, 256)
+    p = fbf.make_params(c, 4.0)
+    Fn = fbf.FBFFunction
+    grads = [None] * n
+
+    def step():
+        with torch.cuda.stream(stream):
+            for i in range(n):
+                xi = xs[i].detach().requires_grad_(True)
+                yi = Fn.apply(xi, p)
+                (yi * gs[i]).sum().backward()
+                grads[i] = xi.grad
+
+    ms = _timed_steps(torch, dev, stream, step, steps)
+    res = {"workload": "16 x 512x512 f32 synthetic (seeds 1400+i, u8/255, T=1), sigma_s=4 (W=12), "
+                       "sigma_r=0.1, levels=256, eps=1e-3, K=%d; forward + adjoint via torch.autograd" % c.K,
+           "ms": round(ms, 3), "mpix_s": round(n * S * S / ms / 1e3, 1)}
+    if with_oracle:
+        import oracle as O
+
+        torch.cuda.synchronize(dev)
+        rng = np.random.default_rng(7)
+        ys_, xs_ = rng.integers(0, S, 64), rng.integers(0, S, 64)
+        w1 = O.weights_1d(O.SPATIAL_GAUSSIAN, 4.0, 12)
+        f0 = xs[0].cpu().numpy().astype(np.float64)
+        g0 = gs[0].cpu().numpy().astype(np.float64)
+        ref = O.grad_at(f0, g0, w1, O.BORDER_REFLECT, np.array(c.coefficients), 1.0, (ys_, xs_))
+        got = grads[0].cpu().numpy()[ys_, xs_]
+        res["grad_max_err_vs_oracle_rel"] = round(float(np.max(np.abs(got - ref)) / np.max(np.abs(ref))), 8)
+    return res
+
+
+def run_local_range(fbf, torch, dev, stream, img_dev, steps):
+    """Dynamic range T of the 2048^2 image over each window (Sec. III) and the
+    order K it gives against T = 255."""
+    out = torch.empty(1, dtype=torch.int32, device=dev)
+    res = []
+    for W in sorted({fbf.fbf_resolve_window(fbf.make_params(fbf.fbf_fit_coeffs("gaussian", 20.0, T, EPS), ss))
+                     for ss, _ in SETTINGS}):
+        Tl = fbf.fbf_local_range(img_dev, W, out=out, stream=stream)
+        ms = _timed_steps(torch, dev, stream, lambda: fbf.fbf_local_range(img_dev, W, out=out, stream=stream), steps)
+        row = {"W": W, "T": Tl, "ms": round(ms, 4)}
+        for sr in sorted({sr for _, sr in SETTINGS}):
+            row["K_sigma_r_%g" % sr] = [fbf.fbf_fit_coeffs("gaussian", sr, float(Tl), EPS).K,
+                                        fbf.fbf_fit_coeffs("gaussian", sr, T, EPS).K]
+        res.append(row)
+    return {"note": "T of the 2048x2048 image over [-W, W]^2; K pairs are [local T, T = 255]; ms includes the "
+                    "host sync of the result", "windows": res}
+
+
 def run_ours(args):
     batch_imgs = batch_specs = None
     if args.batched:
@@ -451,6 +572,19 @@ def run_ours(args):
     batched = None
     if batch_imgs is not None:
         batched = run_batched(fbf, torch, dev, stream, batch_imgs, batch_specs, max(2, min(args.steps, 10)))
+    extras = {}
+    if args.extras and rank == 0:
+        ex_steps = max(2, min(args.steps, 10))
+
+        def flush_l2():
+            with torch.cuda.stream(stream):
+                flush.zero_()
+
+        extras["exponential_4096"] = run_exponential(fbf, torch, dev, stream, ex_steps, flush_l2,
+                                                     not args.no_cpu_baseline)
+        extras["differentiation"] = run_differentiation(fbf, torch, dev, stream, ex_steps,
+                                                        not args.no_cpu_baseline)
+        extras["local_range"] = run_local_range(fbf, torch, dev, stream, x, ex_steps)
 
     hf = per_form[head]
     result = {
@@ -477,6 +611,7 @@ def run_ours(args):
     }
     if batched is not None:
         result["batched"] = batched
+    result.update(extras)
     if cb is not None:
         result["cpu_baseline"] = cb
         result["max_err_vs_oracle"] = round(errs[head], 6)
@@ -539,6 +674,10 @@ def main():
     ap.add_argument("--batched", dest="batched", action="store_true", default=True,
                     help="also time the uneven 64-image batch (default on)")
     ap.add_argument("--no-batched", dest="batched", action="store_false")
+    ap.add_argument("--extras", dest="extras", action="store_true", default=True,
+                    help="also time the 4096^2 exponential-kernel, differentiation and local-range"
+                         " workloads (default on; rank 0 only)")
+    ap.add_argument("--no-extras", dest="extras", action="store_false")
     ap.add_argument("--only", type=int, default=None,
                     help="run a single setting (index into the six) -- for profiling")
     args = ap.parse_args()
