@@ -54,6 +54,7 @@ fbf_status pack_filter_args(const fbf_params *p, const void *d_in, fbf_dtype dty
   a->T = (float)c->T;
   a->twoT = dtype == FBF_U8 ? 2 * (int)c->T : 0;
   a->border = (int)p->border;
+  a->box = p->spatial == FBF_SPATIAL_BOX ? 1 : 0;
   spatial_weights(p->spatial, p->sigma_s, W, a->w);
   for (int j = 0; j < 2 * W + 1; ++j) {
     unsigned int b;

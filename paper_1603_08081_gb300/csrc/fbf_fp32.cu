@@ -8,8 +8,10 @@ fbf_status launch_fp32_u8_w11_16(const FilterArgs &a, cudaStream_t s);
 fbf_status launch_fp32_u8_w17_22(const FilterArgs &a, cudaStream_t s);
 fbf_status launch_fp32_u8_w23_27(const FilterArgs &a, cudaStream_t s);
 fbf_status launch_fp32_u8_w28_32(const FilterArgs &a, cudaStream_t s);
+fbf_status launch_fp32_u8_box(const FilterArgs &a, cudaStream_t s);
 
 fbf_status launch_fp32_u8(const FilterArgs &a, cudaStream_t s) {
+  if (a.box) return launch_fp32_u8_box(a, s);  // running window sums
   if (a.W <= 10) return launch_fp32_u8_w00_10(a, s);
   if (a.W <= 16) return launch_fp32_u8_w11_16(a, s);
   if (a.W <= 22) return launch_fp32_u8_w17_22(a, s);

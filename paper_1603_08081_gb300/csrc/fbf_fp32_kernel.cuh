@@ -157,6 +157,44 @@ __device__ __forceinline__ void fir_run(const u64 *w2, int taps_rt, Load load, Q
   }
 }
 
+// Box kernel: kRun outputs of the unweighted window sum acc[o] = sum_{k < taps}
+// src(o + k), the first summed directly, each next one from the previous by
+// adding the entering position and subtracting the leaving one (2 f32x2 ops
+// per channel pair and output instead of `taps`; the restart every kRun outputs
+// bounds the rounding drift to kRun - 1 steps).  The common factor 1/taps^2 of
+// the box weights cancels in fhat = P / Q and is never applied.  Reads the
+// same positions as fir_run (at most taps - 1 + kRun).
+template <class Load>
+__device__ __forceinline__ void box_run(int taps, Load load, Quad (&acc)[kRun]) {
+  const u64 one = pack_f(1.f, 1.f), minus_one = pack_f(-1.f, -1.f);
+  Quad head[kRun - 1];  // src(0 .. kRun - 2): the positions that leave the window
+  Quad s{0ull, 0ull};
+#pragma unroll
+  for (int j = 0; j < kRun - 1; ++j) {
+    head[j] = load(j);
+    if (j < taps) {
+      fma2(s.a, one, head[j].a);
+      fma2(s.b, one, head[j].b);
+    }
+  }
+#pragma unroll 4
+  for (int k = kRun - 1; k < taps; ++k) {
+    const Quad v = load(k);
+    fma2(s.a, one, v.a);
+    fma2(s.b, one, v.b);
+  }
+  acc[0] = s;
+#pragma unroll
+  for (int o = 1; o < kRun; ++o) {
+    const Quad v = load(o - 1 + taps);
+    fma2(s.a, one, v.a);
+    fma2(s.b, one, v.b);
+    fma2(s.a, minus_one, head[o - 1].a);
+    fma2(s.b, minus_one, head[o - 1].b);
+    acc[o] = s;
+  }
+}
+
 // Per-tile parameters of the fused FP32 filter.  w2 / d point into the kernel
 // parameter block (single image) or into shared memory (batched plan).
 struct K1View {
@@ -173,8 +211,9 @@ struct K1View {
 // One output tile (origin ty0, tx0) of the fused FP32 filter: stage, then for
 // every harmonic modulate / row pass / column pass / demodulate, then write
 // fhat.  `smem` is the dynamic shared memory laid out by make_layout (the
-// caller owns anything placed after Layout::bytes).
-template <int BX, int BY, int NT, int NBUF, int WCAP, int TAPSC>
+// caller owns anything placed after Layout::bytes).  BOXSUM: both passes are
+// unweighted running window sums (box kernel, box_run) instead of the FIR.
+template <int BX, int BY, int NT, int NBUF, int WCAP, int TAPSC, int BOXSUM = 0>
 __device__ __forceinline__ void k1_tile(const K1View &a, int ty0, int tx0, unsigned char *smem) {
   static_assert(BX % 32 == 0 && BY % kRun == 0 && NT % 32 == 0, "tile shape");
   static_assert(NBUF == 1 || NBUF == 2, "one or two table buffers");
@@ -226,12 +265,14 @@ __device__ __forceinline__ void k1_tile(const K1View &a, int ty0, int tx0, unsig
       const unsigned short *tp = tileT + ox0 * Ly.PT + ey;
       const int PT = Ly.PT;
       Quad acc[kRun];
-      fir_run<TAPSC>(a.w2, taps,
-              [&](int p) {
-                const ulonglong2 e = *reinterpret_cast<const ulonglong2 *>(Lc + tp[p * PT]);
-                return Quad{e.x, e.y};
-              },
-              acc);
+      auto ld = [&](int p) {
+        const ulonglong2 e = *reinterpret_cast<const ulonglong2 *>(Lc + tp[p * PT]);
+        return Quad{e.x, e.y};
+      };
+      if (BOXSUM)
+        box_run(taps, ld, acc);
+      else
+        fir_run<TAPSC>(a.w2, taps, ld, acc);
       ulonglong2 *rb = rowbuf + ey * Ly.PR + ox0;
 #pragma unroll
       for (int o = 0; o < kRun; ++o) rb[o] = make_ulonglong2(acc[o].a, acc[o].b);
@@ -251,12 +292,14 @@ __device__ __forceinline__ void k1_tile(const K1View &a, int ty0, int tx0, unsig
       const ulonglong2 *cpnt = rowbuf + oy0 * Ly.PR + ox;
       const int PR = Ly.PR;
       Quad acc[kRun];
-      fir_run<TAPSC>(a.w2, taps,
-              [&](int p) {
-                const ulonglong2 e = cpnt[p * PR];
-                return Quad{e.x, e.y};
-              },
-              acc);
+      auto ld = [&](int p) {
+        const ulonglong2 e = cpnt[p * PR];
+        return Quad{e.x, e.y};
+      };
+      if (BOXSUM)
+        box_run(taps, ld, acc);
+      else
+        fir_run<TAPSC>(a.w2, taps, ld, acc);
       const unsigned short *cen = tileT + (ox + W) * Ly.PT + oy0 + W;
 #pragma unroll
       for (int o = 0; o < kRun; ++o) {
@@ -290,23 +333,23 @@ __device__ __forceinline__ void k1_tile(const K1View &a, int ty0, int tx0, unsig
   }
 }
 
-template <int BX, int BY, int NT, int NBUF, int WCAP, int TAPSC>
+template <int BX, int BY, int NT, int NBUF, int WCAP, int TAPSC, int BOXSUM = 0>
 __global__ void __launch_bounds__(NT, 1) fbf_fp32_u8_kernel(const __grid_constant__ FilterArgs a) {
   extern __shared__ __align__(128) unsigned char smem[];
   const int tile_y = blockIdx.x / a.tiles_x, tile_x = blockIdx.x - tile_y * a.tiles_x;
   const K1View v{static_cast<const unsigned char *>(a.in), a.in_pitch, a.out, a.out_pitch, a.H, a.Wd, a.W, a.K,
                  a.twoT, a.border, a.T, a.w2, a.d};
-  k1_tile<BX, BY, NT, NBUF, WCAP, TAPSC>(v, tile_y * BY, tile_x * BX, smem);
+  k1_tile<BX, BY, NT, NBUF, WCAP, TAPSC, BOXSUM>(v, tile_y * BY, tile_x * BX, smem);
 }
 
-template <int BX, int BY, int NT, int NBUF, int WCAP, int TAPSC = 0>
+template <int BX, int BY, int NT, int NBUF, int WCAP, int TAPSC = 0, int BOXSUM = 0>
 fbf_status launch_cfg(const FilterArgs &a0, cudaStream_t s) {
   FilterArgs a = a0;
   const Layout Ly = make_layout(BX, BY, a.W, NBUF, WCAP);
   a.tiles_x = (a.Wd + BX - 1) / BX;
   const int tiles_y = (a.H + BY - 1) / BY;
   a.ntiles = a.tiles_x * tiles_y;
-  auto kern = fbf_fp32_u8_kernel<BX, BY, NT, NBUF, WCAP, TAPSC>;
+  auto kern = fbf_fp32_u8_kernel<BX, BY, NT, NBUF, WCAP, TAPSC, BOXSUM>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Ly.bytes);
   if (e != cudaSuccess) return FBF_ERR_CUDA;
   kern<<<a.ntiles, NT, Ly.bytes, s>>>(a);

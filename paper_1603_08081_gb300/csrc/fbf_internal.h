@@ -35,6 +35,7 @@ struct FilterArgs {
   int border;        // fbf_border
   int tiles_x;       // tiles per image row
   int ntiles;        // tiles in the image
+  int box;           // 1: box spatial kernel (all taps equal)
   float w[TAPS_MAX];  // normalised 1-D spatial taps w1[j + W]
   float d[FBF_KMAX];  // cosine coefficients, eq. (6)
   unsigned long long w2[TAPS_MAX];  // each tap duplicated into both halves of an f32x2 pair

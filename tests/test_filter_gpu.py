@@ -204,3 +204,19 @@ def test_single_form_small_range_scale(fbf, sigma_r):
     ref = _oracle_full(img, c, 3.0, 9, "gaussian", "reflect")
     _check(_gpu(fbf, img, c, 3.0, form="tc_fp16_single"), ref, 0.2)
     _check(_gpu(fbf, img, c, 3.0, form="tc_fp16"), ref, TOL_TC)
+
+
+@pytest.mark.parametrize("border", ["reflect", "truncate"])
+def test_box_4096_exponential_sampled(fbf, border):
+    """The 4096x4096 exponential-kernel workload with the box kernel W = 8 (the
+    FP32 form runs it as running window sums), K = 40 fixed: sampled pixels
+    against eq. (9) summed directly, every form."""
+    img = make_image(4096, 4096, 1200)
+    c = fbf.fbf_fit_coeffs("exponential", 20.0, 255.0, 0.0, 40)
+    ys, xs = _sample_points(4096, 4096, 400, seed=88)
+    w1 = O.weights_1d(O.SPATIAL_BOX, 1.0, 8)
+    bd = O.BORDER_REFLECT if border == "reflect" else O.BORDER_TRUNCATE
+    ref = O.direct_sbf(img, w1, bd, np.array(c.coefficients), 255.0, points=(ys, xs))[0]
+    for form in FORMS:
+        got = _gpu(fbf, img, c, 1.0, W=8, spatial="box", border=border, form=form)
+        _check(got[ys, xs], ref, TOL[form])
