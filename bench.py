@@ -259,16 +259,19 @@ def make_batch_images(specs):
 
 
 def run_batched(fbf, torch, dev, stream, imgs, specs_raw, steps):
-    """One graph launch over the whole uneven batch vs one fbf_filter per image."""
+    """The uneven batch as one graph launch of an autotuned plan (forms FP32,
+    AUTO and the single FP16 tensor-core form) vs one fbf_filter per image."""
     xs = [torch.from_numpy(im).to(dev) for im in imgs]
     ys = [torch.empty(im.shape, dtype=torch.float32, device=dev) for im in imgs]
     specs = [dict(sigma_s=ss, sigma_r=sr, eps=EPS) for (_, _, ss, sr, _) in specs_raw]
     total_px = sum(im.size for im in imgs)
+    plans = {}
     with torch.cuda.stream(stream):
-        plan = fbf.fbf_plan_create(xs, ys, specs, "fp32", "reflect")
-    n_items = plan.size()[1]
+        for f in ("fp32", "auto", "tc_fp16_single"):
+            plans[f] = fbf.fbf_plan_create(xs, ys, specs, f, "reflect")
+    n_items = plans["fp32"].size()[1]
     params = {}
-    for f in FORMS_ALL:
+    for f in FORMS_ALL + ["auto"]:
         params[f] = [fbf.make_params(fbf.fbf_fit_coeffs("gaussian", sp["sigma_r"], T, EPS), sp["sigma_s"], 0,
                                      "gaussian", "reflect", f) for sp in specs]
 
@@ -290,23 +293,19 @@ def run_batched(fbf, torch, dev, stream, imgs, specs_raw, steps):
                 fbf.fbf_filter(p, x, out=y, stream=stream)
         return go
 
-    def separate_best():  # per image, the faster single-image form at that window
-        for k, (x, y) in enumerate(zip(xs, ys)):
-            f = "fp32" if fbf.fbf_resolve_window(params["fp32"][k]) <= 12 else "tc_fp16"
-            fbf.fbf_filter(params[f][k], x, out=y, stream=stream)
-
     res = {"workload": "64 u8 synthetic images (seeds 1300+i), H, W ~ U[256, 2048], sigma_s ~ U[2, 10], "
                        "sigma_r ~ U[10, 60] (seed 1399), eps=1e-3, reflect",
            "pixels": int(total_px), "work_items": n_items}
-    ms = timed(lambda: fbf.fbf_filter_batched(plan, stream))
-    res["graph_persistent_fp32"] = {"ms": round(ms, 3), "mpix_s": round(total_px / ms / 1e3, 1), "launches": 1}
-    for f in FORMS_ALL:
+    for f, plan in plans.items():
+        kind, tuned_ms = plan.schedule()
+        ms = timed(lambda: fbf.fbf_filter_batched(plan, stream))
+        res["plan_" + f] = {"ms": round(ms, 3), "mpix_s": round(total_px / ms / 1e3, 1), "graph_launches": 1,
+                            "schedule": kind, "autotune_ms": round(tuned_ms, 3)}
+    for f in FORMS_ALL + ["auto"]:
         ms = timed(separate(f))
         res["separate_" + f] = {"ms": round(ms, 3), "mpix_s": round(total_px / ms / 1e3, 1), "launches": len(imgs)}
-    ms = timed(separate_best)
-    res["separate_best_form"] = {"ms": round(ms, 3), "mpix_s": round(total_px / ms / 1e3, 1),
-                                 "launches": len(imgs), "rule": "fp32 if W <= 12 else tc_fp16"}
-    plan.destroy()
+    for plan in plans.values():
+        plan.destroy()
     return res
 
 

@@ -69,8 +69,9 @@ typedef enum { FBF_U8 = 0, FBF_F32 = 1 } fbf_dtype;
  * tensor-core products); on 8-bit images its error against the exact
  * Algorithm 1 stays near 0.02-0.05 gray level for sigma_r >= 20 and grows as
  * sigma_r shrinks (about 0.1 at sigma_r = 5), where the split forms stay below
- * 2e-3.  AUTO: the faster of FP32 and TC_FP16 for the window (TC_FP16 from
- * W = 10 up); AUTO never picks TC_FP16_SINGLE. */
+ * 2e-3.  AUTO: the faster of FP32 and TC_FP16 for the window (TC_FP16 for
+ * Gaussian windows from W = 10 up; FP32 for the box kernel, which the FP32
+ * form runs as running window sums); AUTO never picks TC_FP16_SINGLE. */
 typedef enum {
   FBF_FORM_AUTO = 0,
   FBF_FORM_FP32 = 1,
@@ -157,7 +158,8 @@ fbf_status fbf_filter(const fbf_params *p, const void *d_in, fbf_dtype dtype, in
 /* ---- Batched filtering ---------------------------------------------------
  * Many uint8 images of uneven sizes, each with its own spatial window, range
  * kernel, sigma_r, T and tolerance (hence its own K), filtered by one
- * persistent launch captured in a CUDA graph. */
+ * CUDA graph whose schedule (one persistent launch, or one launch per image)
+ * the plan picks by timing the candidates on the batch itself. */
 
 typedef struct fbf_plan fbf_plan; /* owns its device tables and the graph */
 
@@ -174,16 +176,30 @@ typedef struct {
   int K_fixed, levels;        /* as fbf_fit_coeffs                                       */
 } fbf_image_desc;
 
+/* Schedules a plan can replay (see fbf_plan_create). */
+typedef enum {
+  FBF_SCHEDULE_PERSISTENT = 0,      /* one persistent FP32 launch, 32 x 192 tiles     */
+  FBF_SCHEDULE_PERSISTENT_WIDE = 1, /* one persistent FP32 launch, 64 x 96 tiles      */
+  FBF_SCHEDULE_PER_IMAGE_FP32 = 2,  /* one single-image FP32 launch per image         */
+  FBF_SCHEDULE_PER_IMAGE_FORM = 3   /* one launch per image in the plan's form        */
+} fbf_schedule;
+
 /*
- * fbf_plan_create -- fit every image's coefficients (Algorithm 2, host FP64),
- * upload a table of per-image parameters and a work list of (image, tile)
- * items sorted by estimated cost, and capture one persistent launch (one CTA
- * per SM pulling items from a counter) into a CUDA graph on the current
- * device.  The pointers in `descs` are baked into the plan: the images must
- * stay allocated while the plan is used.  Allocates device memory
- * (synchronously) for the tables.  form: AUTO or FP32 (tensor-core forms
- * return FBF_ERR_UNSUPPORTED).  A fit that misses its tolerance returns
- * FBF_ERR_NOT_CONVERGED.
+ * fbf_plan_create -- fit every image's coefficients (Algorithm 2, host FP64)
+ * and capture the plan's schedule in a CUDA graph on the current device.
+ * Candidate schedules: PERSISTENT (one CTA per SM pulling cost-sorted (image,
+ * tile) items from a counter; FP32 tile body with run-time taps), its 64 x 96
+ * tile variant PERSISTENT_WIDE (when every W <= 16), PER_IMAGE_FP32 (the
+ * single-image FP32 kernels, one launch each) and PER_IMAGE_FORM (one
+ * launch per image in `form`).  form FP32: the first three; AUTO: all four
+ * (per image as fbf_filter's AUTO); a tensor-core form: PER_IMAGE_FORM only.
+ * With more than one candidate the plan autotunes: it replays every
+ * candidate on the given images -- writing their outputs -- times each with
+ * CUDA events and keeps the fastest (fbf_plan_schedule reports which); this
+ * synchronises the device.  The pointers in `descs` are baked into the plan:
+ * the images must stay allocated while the plan is used.  Allocates device
+ * memory (synchronously) for the persistent tables.  A fit that misses its
+ * tolerance returns FBF_ERR_NOT_CONVERGED.
  */
 fbf_status fbf_plan_create(const fbf_image_desc *descs, int n, fbf_form form, fbf_border border,
                            fbf_plan **out);
@@ -193,6 +209,9 @@ fbf_status fbf_filter_batched(fbf_plan *plan, cudaStream_t stream);
 fbf_status fbf_plan_destroy(fbf_plan *plan);
 /* Number of images and (image, tile) work items of a plan. */
 fbf_status fbf_plan_size(const fbf_plan *plan, int *n_images, int *n_items);
+/* The schedule the plan replays and the time autotuning measured for it (ms
+ * per replay; 0 when the plan had a single candidate). */
+fbf_status fbf_plan_schedule(const fbf_plan *plan, fbf_schedule *schedule, double *ms);
 
 /*
  * fbf_filter_backward -- gradient of L = sum_i g(i) fhat(i) with respect to the

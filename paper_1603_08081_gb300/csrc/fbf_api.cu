@@ -69,13 +69,11 @@ fbf_status pack_filter_args(const fbf_params *p, const void *d_in, fbf_dtype dty
 
 using namespace fbf;
 
-extern "C" fbf_status fbf_filter(const fbf_params *p, const void *d_in, fbf_dtype dtype, int H, int Wd,
-                                 size_t in_pitch, float *d_out, size_t out_pitch, cudaStream_t stream) {
-  FilterArgs a;
-  fbf_status st = pack_filter_args(p, d_in, dtype, H, Wd, in_pitch, d_out, out_pitch, &a);
-  if (st != FBF_OK) return st;
-  if (H == 0 || Wd == 0) return FBF_OK;
-  const fbf_form form = p->form;
+namespace fbf {
+
+// Launch of one packed image in the requested form (validated by the caller's
+// pack_filter_args; sizes non-zero).
+fbf_status launch_filter(const FilterArgs &a, fbf_form form, fbf_dtype dtype, cudaStream_t stream) {
   const bool tc = form == FBF_FORM_TC_FP16 || form == FBF_FORM_TC_BF16 || form == FBF_FORM_TC_FP16_SINGLE;
   if (form != FBF_FORM_AUTO && form != FBF_FORM_FP32 && !tc) return FBF_ERR_INVALID_ARGUMENT;
   if (dtype == FBF_F32) {
@@ -86,11 +84,25 @@ extern "C" fbf_status fbf_filter(const fbf_params *p, const void *d_in, fbf_dtyp
   if (form == FBF_FORM_TC_FP16) return launch_tc_u8(a, 0, stream);
   if (form == FBF_FORM_TC_BF16) return launch_tc_u8(a, 1, stream);
   if (form == FBF_FORM_TC_FP16_SINGLE) return launch_tc_u8(a, 2, stream);
-  // AUTO: the tensor-core FP16 form from W = 10 up (faster there on GB300:
-  // W = 15: 0.62 vs 0.82 ms, W = 30: 1.06 vs 1.51 ms on a 2048^2 image with
-  // K = 17); the FP32 form below (W = 9: 0.60 vs 0.62 ms).
-  if (form == FBF_FORM_AUTO && a.W >= 10) return launch_tc_u8(a, 0, stream);
+  if (form == FBF_FORM_AUTO && auto_picks_tc(a)) return launch_tc_u8(a, 0, stream);
   return launch_fp32_u8(a, stream);
+}
+
+// AUTO: the tensor-core FP16 form for Gaussian windows from W = 10 up (2048^2,
+// K = 17 on GB300: W = 15 0.59 vs 0.82 ms, W = 30 1.04 vs 1.51 ms; at W = 9 the
+// two are equal, 0.59 vs 0.60 ms); the FP32 form otherwise, and always for the
+// box kernel, whose running window sums make the FP32 form the faster one.
+bool auto_picks_tc(const FilterArgs &a) { return a.W >= 10 && !a.box; }
+
+}  // namespace fbf
+
+extern "C" fbf_status fbf_filter(const fbf_params *p, const void *d_in, fbf_dtype dtype, int H, int Wd,
+                                 size_t in_pitch, float *d_out, size_t out_pitch, cudaStream_t stream) {
+  FilterArgs a;
+  fbf_status st = pack_filter_args(p, d_in, dtype, H, Wd, in_pitch, d_out, out_pitch, &a);
+  if (st != FBF_OK) return st;
+  if (H == 0 || Wd == 0) return FBF_OK;
+  return launch_filter(a, p->form, dtype, stream);
 }
 
 extern "C" fbf_status fbf_filter_backward(const fbf_params *p, const float *d_in, const float *d_gout,

@@ -1,16 +1,27 @@
 // Batched filtering of many uneven images, each with its own spatial and range
-// parameters (its own W, K and coefficients), in one persistent launch that is
-// captured in a CUDA graph.
+// parameters (its own W, K and coefficients), replayed as one CUDA graph.
 //
-// fbf_plan_create fits every image's coefficients (Algorithm 2, host FP64),
-// uploads a table of per-image parameters, and lists every (image, tile) work
-// item sorted by estimated cost (K x taps per tile, largest first).  The
-// persistent kernel runs one CTA per SM; each CTA repeatedly takes the next
-// item from a global counter (one atomicAdd per tile, no waiting), copies that
-// image's taps and coefficients to shared memory, and runs the fused FP32 tile
-// body (32 x 192 outputs, W <= 32, tap count at run time).  The graph holds a
-// memset of the counter followed by the kernel, so fbf_filter_batched is one
-// cudaGraphLaunch.
+// fbf_plan_create fits every image's coefficients (Algorithm 2, host FP64) and
+// prepares the candidate schedules that apply to the plan's form, each
+// captured in its own graph:
+//
+//   PERSISTENT       one launch, one CTA per SM; each CTA repeatedly takes
+//                    the next (image, tile) item from a global counter (one
+//                    atomicAdd per tile, no waiting), copies that image's taps
+//                    and coefficients to shared memory and runs the fused
+//                    FP32 tile body with run-time taps.  Items are sorted by
+//                    estimated cost (K x taps per tile, largest first).  32 x
+//                    192 tiles, any W <= 32;
+//   PERSISTENT_WIDE  the same with 64 x 96 tiles (when every W <= 16);
+//   PER_IMAGE_FP32   one launch per image of the single-image FP32 kernel
+//                    (compile-time tap counts, running sums for box windows);
+//   PER_IMAGE_FORM   one launch per image in the plan's form (AUTO: the
+//                    per-image choice of fbf_filter; the tensor-core forms).
+//
+// Autotuning: when more than one candidate applies (forms AUTO and FP32), the
+// plan replays every candidate's graph on its own images (writing the
+// outputs), times it with CUDA events and keeps the fastest; the others are
+// released.  fbf_plan_schedule reports the choice and its time.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -23,7 +34,7 @@
 namespace fbf {
 namespace {
 
-constexpr int kBBX = 32, kBBY = 192, kBNT = 256, kBNBUF = 1, kBWCAP = 32;
+constexpr int kBNT = 256;
 
 struct ImageParams {
   const unsigned char *in;
@@ -44,9 +55,10 @@ struct BatchArgs {
   int *counter;
 };
 
+template <int BX, int BY, int NBUF, int WCAP>
 __global__ void __launch_bounds__(kBNT, 1) fbf_batched_kernel(const __grid_constant__ BatchArgs b) {
   extern __shared__ __align__(128) unsigned char smem[];
-  const Layout Lmax = make_layout(kBBX, kBBY, kBWCAP, kBNBUF, kBWCAP);
+  const Layout Lmax = make_layout(BX, BY, WCAP, NBUF, WCAP);
   u64 *w2s = reinterpret_cast<u64 *>(smem + Lmax.bytes);
   float *ds = reinterpret_cast<float *>(w2s + TAPS_MAX);
   int *item_s = reinterpret_cast<int *>(ds + FBF_KMAX);
@@ -63,15 +75,47 @@ __global__ void __launch_bounds__(kBNT, 1) fbf_batched_kernel(const __grid_const
     __syncthreads();
     const K1View v{P.in, P.in_pitch, P.out, P.out_pitch, P.H, P.Wd, W, K, P.twoT, b.border, P.T, w2s, ds};
     const int ty = w.y / P.tiles_x, tx = w.y - ty * P.tiles_x;
-    k1_tile<kBBX, kBBY, kBNT, kBNBUF, kBWCAP, 0>(v, ty * kBBY, tx * kBBX, smem);
+    k1_tile<BX, BY, kBNT, NBUF, WCAP, 0>(v, ty * BY, tx * BX, smem);
     __syncthreads();  // the next item overwrites the taps, coefficients and item slot
   }
 }
 
+template <int BX, int BY, int NBUF, int WCAP>
 size_t batched_smem_bytes() {
-  const Layout Lmax = make_layout(kBBX, kBBY, kBWCAP, kBNBUF, kBWCAP);
+  const Layout Lmax = make_layout(BX, BY, WCAP, NBUF, WCAP);
   return Lmax.bytes + TAPS_MAX * sizeof(u64) + FBF_KMAX * sizeof(float) + 16;
 }
+
+// Device tables of one persistent schedule.
+struct Persistent {
+  ImageParams *d_imgs = nullptr;
+  int2 *d_items = nullptr;
+  int *d_counter = nullptr;
+  int n_items = 0;
+  void release() {
+    if (d_imgs) cudaFree(d_imgs);
+    if (d_items) cudaFree(d_items);
+    if (d_counter) cudaFree(d_counter);
+    d_imgs = nullptr;
+    d_items = nullptr;
+    d_counter = nullptr;
+  }
+};
+
+struct Candidate {
+  fbf_schedule kind = FBF_SCHEDULE_PERSISTENT;
+  Persistent tables;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  double ms = 0.0;
+  void release() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+    exec = nullptr;
+    graph = nullptr;
+    tables.release();
+  }
+};
 
 }  // namespace
 }  // namespace fbf
@@ -81,20 +125,126 @@ using namespace fbf;
 struct fbf_plan {
   int device = 0;
   int n_images = 0, n_items = 0;
-  ImageParams *d_imgs = nullptr;
-  int2 *d_items = nullptr;
-  int *d_counter = nullptr;
-  cudaGraph_t graph = nullptr;
-  cudaGraphExec_t exec = nullptr;
+  Candidate chosen;
 };
+
+namespace fbf {
+namespace {
+
+// Per-image tables and cost-sorted work list for BX x BY tiles.
+template <int BX, int BY>
+fbf_status build_persistent(const std::vector<FilterArgs> &args, Persistent *t) {
+  const int n = (int)args.size();
+  std::vector<ImageParams> imgs(n);
+  struct Item {
+    int img, tile;
+    double cost;
+  };
+  std::vector<Item> items;
+  for (int i = 0; i < n; ++i) {
+    const FilterArgs &a = args[i];
+    ImageParams &P = imgs[i];
+    std::memset(&P, 0, sizeof(P));
+    P.in = static_cast<const unsigned char *>(a.in);
+    P.out = a.out;
+    P.in_pitch = a.in_pitch;
+    P.out_pitch = a.out_pitch;
+    P.H = a.H;
+    P.Wd = a.Wd;
+    P.W = a.W;
+    P.K = a.K;
+    P.twoT = a.twoT;
+    P.T = a.T;
+    P.tiles_x = (a.Wd + BX - 1) / BX;
+    std::memcpy(P.w2, a.w2, sizeof(P.w2));
+    std::memcpy(P.d, a.d, sizeof(P.d));
+    const int ntiles = a.H > 0 && a.Wd > 0 ? P.tiles_x * ((a.H + BY - 1) / BY) : 0;
+    const double cost = (double)a.K * (2 * a.W + 1) + 8.0;  // per tile: harmonics x taps (+ staging)
+    for (int t = 0; t < ntiles; ++t) items.push_back({i, t, cost});
+  }
+  std::stable_sort(items.begin(), items.end(), [](const Item &x, const Item &y) { return x.cost > y.cost; });
+  std::vector<int2> h_items(items.size());
+  for (size_t k = 0; k < items.size(); ++k) h_items[k] = make_int2(items[k].img, items[k].tile);
+  t->n_items = (int)items.size();
+  bool ok = cudaMalloc(&t->d_imgs, sizeof(ImageParams) * std::max(n, 1)) == cudaSuccess &&
+            cudaMalloc(&t->d_items, sizeof(int2) * std::max<size_t>(items.size(), 1)) == cudaSuccess &&
+            cudaMalloc(&t->d_counter, sizeof(int)) == cudaSuccess;
+  if (ok && n > 0)
+    ok = cudaMemcpy(t->d_imgs, imgs.data(), sizeof(ImageParams) * n, cudaMemcpyHostToDevice) == cudaSuccess;
+  if (ok && !items.empty())
+    ok = cudaMemcpy(t->d_items, h_items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice) ==
+         cudaSuccess;
+  return ok ? FBF_OK : FBF_ERR_CUDA;
+}
+
+// Capture of a persistent schedule: counter reset + one launch (one CTA per SM).
+template <int BX, int BY, int NBUF, int WCAP>
+fbf_status capture_persistent(int device, int border, Candidate *c, cudaStream_t cs) {
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  const int grid = std::max(1, std::min(c->tables.n_items, sms));
+  const size_t smem = batched_smem_bytes<BX, BY, NBUF, WCAP>();
+  auto kern = fbf_batched_kernel<BX, BY, NBUF, WCAP>;
+  if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+    return FBF_ERR_CUDA;
+  BatchArgs args{c->tables.d_imgs, c->tables.d_items, c->tables.n_items, border, c->tables.d_counter};
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return FBF_ERR_CUDA;
+  cudaMemsetAsync(c->tables.d_counter, 0, sizeof(int), cs);
+  if (c->tables.n_items > 0) kern<<<grid, kBNT, smem, cs>>>(args);
+  if (cudaStreamEndCapture(cs, &c->graph) != cudaSuccess || !c->graph) return FBF_ERR_CUDA;
+  return cudaGraphInstantiate(&c->exec, c->graph, 0) == cudaSuccess ? FBF_OK : FBF_ERR_CUDA;
+}
+
+// Capture of one single-image launch per image in `form`.  Every launch runs
+// once before the capture, so that the kernels' one-time host set-up
+// (function attributes, driver entry points) happens outside it.
+fbf_status capture_per_image(const std::vector<FilterArgs> &args, fbf_form form, Candidate *c, cudaStream_t cs) {
+  for (const FilterArgs &a : args) {
+    if (a.H == 0 || a.Wd == 0) continue;
+    const fbf_status st = launch_filter(a, form, FBF_U8, cs);
+    if (st != FBF_OK) return st;
+  }
+  if (cudaStreamSynchronize(cs) != cudaSuccess) return FBF_ERR_CUDA;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return FBF_ERR_CUDA;
+  fbf_status st = FBF_OK;
+  for (const FilterArgs &a : args) {
+    if (a.H == 0 || a.Wd == 0) continue;
+    st = launch_filter(a, form, FBF_U8, cs);
+    if (st != FBF_OK) break;
+  }
+  cudaGraph_t g = nullptr;
+  const bool ended = cudaStreamEndCapture(cs, &g) == cudaSuccess;
+  c->graph = g;
+  if (st != FBF_OK) return st;
+  if (!ended || !g) return FBF_ERR_CUDA;
+  return cudaGraphInstantiate(&c->exec, c->graph, 0) == cudaSuccess ? FBF_OK : FBF_ERR_CUDA;
+}
+
+// Mean time of three replays of a candidate's graph (after one untimed replay).
+fbf_status time_candidate(Candidate *c, cudaStream_t cs) {
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    if (e0) cudaEventDestroy(e0);
+    return FBF_ERR_CUDA;
+  }
+  constexpr int kReps = 3;
+  bool ok = cudaGraphLaunch(c->exec, cs) == cudaSuccess && cudaEventRecord(e0, cs) == cudaSuccess;
+  for (int r = 0; ok && r < kReps; ++r) ok = cudaGraphLaunch(c->exec, cs) == cudaSuccess;
+  ok = ok && cudaEventRecord(e1, cs) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess;
+  float ms = 0.f;
+  if (ok) ok = cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess;
+  c->ms = ms / kReps;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return ok ? FBF_OK : FBF_ERR_CUDA;
+}
+
+}  // namespace
+}  // namespace fbf
 
 static void plan_free(fbf_plan *p) {
   if (!p) return;
-  if (p->exec) cudaGraphExecDestroy(p->exec);
-  if (p->graph) cudaGraphDestroy(p->graph);
-  if (p->d_imgs) cudaFree(p->d_imgs);
-  if (p->d_items) cudaFree(p->d_items);
-  if (p->d_counter) cudaFree(p->d_counter);
+  p->chosen.release();
   delete p;
 }
 
@@ -104,17 +254,11 @@ extern "C" fbf_status fbf_plan_create(const fbf_image_desc *descs, int n, fbf_fo
   *out = nullptr;
   if (n < 0 || (n > 0 && !descs)) return FBF_ERR_INVALID_ARGUMENT;
   if (border != FBF_BORDER_REFLECT && border != FBF_BORDER_TRUNCATE) return FBF_ERR_INVALID_ARGUMENT;
-  if (form != FBF_FORM_AUTO && form != FBF_FORM_FP32) {
-    if (form == FBF_FORM_TC_FP16 || form == FBF_FORM_TC_BF16 || form == FBF_FORM_TC_FP16_SINGLE)
-      return FBF_ERR_UNSUPPORTED;
-    return FBF_ERR_INVALID_ARGUMENT;
-  }
-  std::vector<ImageParams> imgs(n);
-  struct Item {
-    int img, tile;
-    double cost;
-  };
-  std::vector<Item> items;
+  const bool tc = form == FBF_FORM_TC_FP16 || form == FBF_FORM_TC_BF16 || form == FBF_FORM_TC_FP16_SINGLE;
+  if (form != FBF_FORM_AUTO && form != FBF_FORM_FP32 && !tc) return FBF_ERR_INVALID_ARGUMENT;
+
+  std::vector<FilterArgs> args(n);
+  int wmax = 0;
   for (int i = 0; i < n; ++i) {
     const fbf_image_desc &d = descs[i];
     fbf_coeffs c;
@@ -125,31 +269,12 @@ extern "C" fbf_status fbf_plan_create(const fbf_image_desc *descs, int n, fbf_fo
     prm.sigma_s = d.sigma_s;
     prm.W = d.W;
     prm.border = border;
-    prm.form = FBF_FORM_FP32;
+    prm.form = form;
     prm.coeffs = &c;
-    FilterArgs a;
-    st = pack_filter_args(&prm, d.d_in, FBF_U8, d.H, d.Wd, d.in_pitch, d.d_out, d.out_pitch, &a);
+    st = pack_filter_args(&prm, d.d_in, FBF_U8, d.H, d.Wd, d.in_pitch, d.d_out, d.out_pitch, &args[i]);
     if (st != FBF_OK) return st;
-    ImageParams &P = imgs[i];
-    std::memset(&P, 0, sizeof(P));
-    P.in = static_cast<const unsigned char *>(d.d_in);
-    P.out = d.d_out;
-    P.in_pitch = d.in_pitch;
-    P.out_pitch = d.out_pitch;
-    P.H = d.H;
-    P.Wd = d.Wd;
-    P.W = a.W;
-    P.K = a.K;
-    P.twoT = a.twoT;
-    P.T = a.T;
-    P.tiles_x = (d.Wd + kBBX - 1) / kBBX;
-    std::memcpy(P.w2, a.w2, sizeof(P.w2));
-    std::memcpy(P.d, a.d, sizeof(P.d));
-    const int ntiles = d.H > 0 && d.Wd > 0 ? P.tiles_x * ((d.H + kBBY - 1) / kBBY) : 0;
-    const double cost = (double)a.K * (2 * a.W + 1) + 8.0;  // per tile: harmonics x taps (+ staging)
-    for (int t = 0; t < ntiles; ++t) items.push_back({i, t, cost});
+    wmax = std::max(wmax, args[i].W);
   }
-  std::stable_sort(items.begin(), items.end(), [](const Item &x, const Item &y) { return x.cost > y.cost; });
 
   fbf_plan *p = new fbf_plan();
   if (cudaGetDevice(&p->device) != cudaSuccess) {
@@ -157,57 +282,66 @@ extern "C" fbf_status fbf_plan_create(const fbf_image_desc *descs, int n, fbf_fo
     return FBF_ERR_CUDA;
   }
   p->n_images = n;
-  p->n_items = (int)items.size();
-  std::vector<int2> h_items(items.size());
-  for (size_t k = 0; k < items.size(); ++k) h_items[k] = make_int2(items[k].img, items[k].tile);
-  bool okc = cudaMalloc(&p->d_imgs, sizeof(ImageParams) * std::max(n, 1)) == cudaSuccess &&
-             cudaMalloc(&p->d_items, sizeof(int2) * std::max<size_t>(items.size(), 1)) == cudaSuccess &&
-             cudaMalloc(&p->d_counter, sizeof(int)) == cudaSuccess;
-  if (okc && n > 0)
-    okc = cudaMemcpy(p->d_imgs, imgs.data(), sizeof(ImageParams) * n, cudaMemcpyHostToDevice) == cudaSuccess;
-  if (okc && !items.empty())
-    okc = cudaMemcpy(p->d_items, h_items.data(), sizeof(int2) * items.size(), cudaMemcpyHostToDevice) ==
-          cudaSuccess;
-  if (!okc) {
-    plan_free(p);
-    return FBF_ERR_CUDA;
-  }
-
-  // Capture: counter reset + one persistent launch (one CTA per SM).
-  int sms = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
-  const int grid = std::max(1, std::min(p->n_items, sms));
-  const size_t smem = batched_smem_bytes();
-  if (cudaFuncSetAttribute(fbf_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
-      cudaSuccess) {
-    plan_free(p);
-    return FBF_ERR_CUDA;
-  }
-  BatchArgs args{p->d_imgs, p->d_items, p->n_items, (int)border, p->d_counter};
+  int n_items = 0;  // (image, tile) items of the 32 x 192 tiling, reported by fbf_plan_size
+  for (const FilterArgs &a : args)
+    if (a.H > 0 && a.Wd > 0) n_items += ((a.Wd + 31) / 32) * ((a.H + 191) / 192);
+  p->n_items = n_items;
   cudaStream_t cs = nullptr;
   if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) {
     plan_free(p);
     return FBF_ERR_CUDA;
   }
-  bool okg = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
-  if (okg) {
-    cudaMemsetAsync(p->d_counter, 0, sizeof(int), cs);
-    if (p->n_items > 0) fbf_batched_kernel<<<grid, kBNT, smem, cs>>>(args);
-    okg = cudaStreamEndCapture(cs, &p->graph) == cudaSuccess && p->graph;
+
+  // Candidate schedules of this form.
+  std::vector<fbf_schedule> kinds;
+  if (tc) {
+    kinds.push_back(FBF_SCHEDULE_PER_IMAGE_FORM);
+  } else {
+    kinds.push_back(FBF_SCHEDULE_PERSISTENT);
+    if (wmax <= 16) kinds.push_back(FBF_SCHEDULE_PERSISTENT_WIDE);
+    kinds.push_back(FBF_SCHEDULE_PER_IMAGE_FP32);
+    if (form == FBF_FORM_AUTO) kinds.push_back(FBF_SCHEDULE_PER_IMAGE_FORM);
   }
-  if (okg) okg = cudaGraphInstantiate(&p->exec, p->graph, 0) == cudaSuccess;
+
+  fbf_status st = FBF_OK;
+  std::vector<Candidate> cands;
+  for (fbf_schedule k : kinds) {
+    Candidate c;
+    c.kind = k;
+    if (k == FBF_SCHEDULE_PERSISTENT) {
+      st = build_persistent<32, 192>(args, &c.tables);
+      if (st == FBF_OK) st = capture_persistent<32, 192, 1, 32>(p->device, (int)border, &c, cs);
+    } else if (k == FBF_SCHEDULE_PERSISTENT_WIDE) {
+      st = build_persistent<64, 96>(args, &c.tables);
+      if (st == FBF_OK) st = capture_persistent<64, 96, 1, 16>(p->device, (int)border, &c, cs);
+    } else {
+      st = capture_per_image(args, k == FBF_SCHEDULE_PER_IMAGE_FP32 ? FBF_FORM_FP32 : form, &c, cs);
+    }
+    cands.push_back(c);
+    if (st != FBF_OK) break;
+  }
+  // Autotune: replay and time every candidate, keep the fastest.
+  size_t best = 0;
+  if (st == FBF_OK && cands.size() > 1) {
+    for (size_t i = 0; i < cands.size() && st == FBF_OK; ++i) st = time_candidate(&cands[i], cs);
+    for (size_t i = 1; i < cands.size(); ++i)
+      if (cands[i].ms < cands[best].ms) best = i;
+  }
   cudaStreamDestroy(cs);
-  if (!okg) {
+  for (size_t i = 0; i < cands.size(); ++i)
+    if (st != FBF_OK || i != best) cands[i].release();
+  if (st != FBF_OK) {
     plan_free(p);
-    return FBF_ERR_CUDA;
+    return st;
   }
+  p->chosen = cands[best];
   *out = p;
   return FBF_OK;
 }
 
 extern "C" fbf_status fbf_filter_batched(fbf_plan *plan, cudaStream_t stream) {
-  if (!plan || !plan->exec) return FBF_ERR_INVALID_ARGUMENT;
-  return cuda_status(cudaGraphLaunch(plan->exec, stream));
+  if (!plan || !plan->chosen.exec) return FBF_ERR_INVALID_ARGUMENT;
+  return cuda_status(cudaGraphLaunch(plan->chosen.exec, stream));
 }
 
 extern "C" fbf_status fbf_plan_destroy(fbf_plan *plan) {
@@ -220,5 +354,12 @@ extern "C" fbf_status fbf_plan_size(const fbf_plan *plan, int *n_images, int *n_
   if (!plan) return FBF_ERR_INVALID_ARGUMENT;
   if (n_images) *n_images = plan->n_images;
   if (n_items) *n_items = plan->n_items;
+  return FBF_OK;
+}
+
+extern "C" fbf_status fbf_plan_schedule(const fbf_plan *plan, fbf_schedule *schedule, double *ms) {
+  if (!plan) return FBF_ERR_INVALID_ARGUMENT;
+  if (schedule) *schedule = plan->chosen.kind;
+  if (ms) *ms = plan->chosen.ms;
   return FBF_OK;
 }

@@ -47,6 +47,9 @@ fbf_status pack_filter_args(const fbf_params *p, const void *d_in, fbf_dtype dty
                             FilterArgs *a);
 
 fbf_status launch_fp32_u8(const FilterArgs &a, cudaStream_t s);
+// One packed image in `form` (AUTO resolved by auto_picks_tc); sizes non-zero.
+fbf_status launch_filter(const FilterArgs &a, fbf_form form, fbf_dtype dtype, cudaStream_t stream);
+bool auto_picks_tc(const FilterArgs &a);
 // mode: 0 = FP16 split data, 1 = BF16 split data and weights, 2 = FP16 single.
 fbf_status launch_tc_u8(const FilterArgs &a, int mode, cudaStream_t s);
 fbf_status tc_read_clear_error(unsigned int *code);

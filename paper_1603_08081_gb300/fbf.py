@@ -24,6 +24,8 @@ FBF_BORDER_REFLECT, FBF_BORDER_TRUNCATE = 0, 1
 FBF_U8, FBF_F32 = 0, 1
 FBF_FORM_AUTO, FBF_FORM_FP32, FBF_FORM_TC_FP16, FBF_FORM_TC_BF16, FBF_FORM_TC_FP16_SINGLE = 0, 1, 2, 3, 4
 
+SCHEDULES = ["persistent", "persistent_wide", "per_image_fp32", "per_image_form"]
+
 _NAMES = {"gaussian": 0, "exponential": 1, "box": 1, "reflect": 0, "truncate": 1,
           "auto": 0, "fp32": 1, "tc_fp16": 2, "tc_bf16": 3, "tc_fp16_single": 4}
 
@@ -82,6 +84,8 @@ def _load():
     lib.fbf_plan_destroy.restype = i
     lib.fbf_plan_size.argtypes = [p, C.POINTER(i), C.POINTER(i)]
     lib.fbf_plan_size.restype = i
+    lib.fbf_plan_schedule.argtypes = [p, C.POINTER(i), C.POINTER(d)]
+    lib.fbf_plan_schedule.restype = i
     lib.fbf_local_range.argtypes = [p, i, i, i, sz, i, p, p]
     lib.fbf_local_range.restype = i
     lib.fbf_resolve_window.argtypes = [C.POINTER(fbf_params)]
@@ -262,6 +266,14 @@ class Plan:
         if st != FBF_OK:
             raise FbfError(st, "fbf_plan_size")
         return ni.value, nt.value
+
+    def schedule(self):
+        """(name of the replayed schedule, ms measured by autotuning)."""
+        k, ms = C.c_int(0), C.c_double(0.0)
+        st = lib.fbf_plan_schedule(self.handle, C.byref(k), C.byref(ms))
+        if st != FBF_OK:
+            raise FbfError(st, "fbf_plan_schedule")
+        return SCHEDULES[k.value], ms.value
 
     def destroy(self):
         if self.handle:

@@ -1,6 +1,7 @@
 """GPU parity of the batched plan (fbf_plan_create / fbf_filter_batched): every
 image of an uneven batch, each with its own window, range scale and order K,
-against the FP64 oracle and against the single-image FP32 filter."""
+against the FP64 oracle and against the single-image filter, for the
+autotuned FP32 / AUTO plans and the per-image tensor-core plans."""
 import numpy as np
 import pytest
 
@@ -24,12 +25,14 @@ def fbf():
     return mod
 
 
-def _run_plan(fbf, imgs, specs, border="reflect"):
+def _run_plan(fbf, imgs, specs, border="reflect", form="fp32"):
     import torch
 
     xs = [torch.from_numpy(im).cuda() for im in imgs]
     ys = [torch.full(im.shape, float("nan"), dtype=torch.float32, device="cuda") for im in imgs]
-    plan = fbf.fbf_plan_create(xs, ys, specs, "fp32", border)
+    plan = fbf.fbf_plan_create(xs, ys, specs, form, border)
+    for y in ys:  # autotuning wrote the outputs: clear them before the timed-free replay
+        y.fill_(float("nan"))
     fbf.fbf_filter_batched(plan)
     torch.cuda.synchronize()
     return plan, xs, ys
@@ -83,7 +86,7 @@ def test_batch_equals_single_image_filter_and_relaunches(fbf):
     plan.destroy()
 
 
-def test_empty_plan_and_unsupported_form(fbf):
+def test_empty_plan_and_invalid_arguments(fbf):
     import ctypes as C
 
     import torch
@@ -94,5 +97,61 @@ def test_empty_plan_and_unsupported_form(fbf):
     torch.cuda.synchronize()
     plan.destroy()
     h = C.c_void_p()
-    arr = (fbf.fbf_image_desc * 1)()
-    assert fbf.lib.fbf_plan_create(arr, 1, fbf.FBF_FORM_TC_FP16, 0, C.byref(h)) == fbf.FBF_ERR_UNSUPPORTED
+    arr = (fbf.fbf_image_desc * 1)()  # sigma_r = 0: the fit rejects it
+    assert fbf.lib.fbf_plan_create(arr, 1, fbf.FBF_FORM_TC_FP16, 0, C.byref(h)) == fbf.FBF_ERR_INVALID_ARGUMENT
+    assert fbf.lib.fbf_plan_create(arr, 1, 9, 0, C.byref(h)) == fbf.FBF_ERR_INVALID_ARGUMENT
+
+
+@pytest.mark.parametrize("form", ["fp32", "auto"])
+def test_autotuned_plan_equals_its_schedule(fbf, form):
+    """The autotuner keeps one of its candidates; whichever it keeps, every
+    output equals the single-image filter of the matching form (per-image
+    schedules replay exactly those kernels: bit-identical; the persistent
+    kernels are the FP32 tile body with run-time taps: within 1e-4)."""
+    import torch
+
+    specs_raw = make_batch_specs(24, seed=1399, lo=64, hi=700)
+    imgs = [make_image(h, w, seed=s) for (h, w, _, _, s) in specs_raw]
+    specs = [dict(sigma_s=ss, sigma_r=sr) for (_, _, ss, sr, _) in specs_raw]
+    specs[3] = dict(sigma_s=1.0, sigma_r=30.0, W=6, spatial="box")
+    plan, xs, ys = _run_plan(fbf, imgs, specs, form=form)
+    kind, ms = plan.schedule()
+    assert kind in fbf.SCHEDULES and ms > 0
+    per_form = {"per_image_fp32": "fp32", "per_image_form": form}.get(kind, "fp32")
+    for x, y, sp in zip(xs, ys, specs):
+        c = fbf.fbf_fit_coeffs("gaussian", sp["sigma_r"], 255.0, 1e-3)
+        p = fbf.make_params(c, sp["sigma_s"], sp.get("W", 0), sp.get("spatial", "gaussian"), "reflect", per_form)
+        single = fbf.fbf_filter(p, x)
+        torch.cuda.synchronize()
+        if kind.startswith("per_image"):
+            assert torch.equal(single, y)
+        else:  # box windows: FIR in the persistent kernels, running sums in the single-image one
+            tol = 2e-3 if sp.get("spatial") == "box" else 1e-4
+            assert torch.max(torch.abs(single - y)).item() <= tol
+    plan.destroy()
+
+
+@pytest.mark.parametrize("form", ["tc_fp16", "tc_fp16_single", "tc_bf16"])
+def test_tensor_core_plan(fbf, form):
+    """Tensor-core plans replay one launch per image: identical to fbf_filter in
+    that form, and within the form's tolerance of the oracle."""
+    import torch
+
+    shapes = [(70, 90), (33, 200), (256, 40), (130, 131), (300, 260)]
+    specs = [dict(sigma_s=3.0, sigma_r=30.0), dict(sigma_s=0.7, sigma_r=15.0), dict(sigma_s=6.0, sigma_r=50.0),
+             dict(sigma_s=2.0, sigma_r=60.0, eps=1e-2), dict(sigma_s=10.0, sigma_r=25.0)]
+    imgs = [make_image(h, w, seed=1500 + k) for k, (h, w) in enumerate(shapes)]
+    plan, xs, ys = _run_plan(fbf, imgs, specs, form=form)
+    assert plan.schedule()[0] == "per_image_form"
+    tol = 0.15 if form == "tc_fp16_single" else 0.02
+    for im, x, y, sp in zip(imgs, xs, ys, specs):
+        c = fbf.fbf_fit_coeffs("gaussian", sp["sigma_r"], 255.0, sp.get("eps", 1e-3))
+        p = fbf.make_params(c, sp["sigma_s"], 0, "gaussian", "reflect", form)
+        single = fbf.fbf_filter(p, x)
+        torch.cuda.synchronize()
+        assert torch.equal(single, y)
+        W = int(np.ceil(3 * sp["sigma_s"] - 1e-12))
+        ref = O.alg1(im, O.weights_1d(O.SPATIAL_GAUSSIAN, sp["sigma_s"], W), O.BORDER_REFLECT,
+                     np.array(c.coefficients), 255.0)[0]
+        assert np.abs(y.cpu().numpy() - ref).max() <= tol
+    plan.destroy()
