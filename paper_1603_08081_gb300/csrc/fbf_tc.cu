@@ -442,12 +442,19 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
       for (int j = 0; j < DG; ++j) part[DG * g + j] = fmaf(t[DG * g + j], __uint_as_float(v[g][j]), part[DG * g + j]);
   };
 
-  // Bounded wait on an MMA barrier, then a CTA-wide agreement on failure.
-  auto wait_mma = [&](uint64_t *m, uint32_t &ph) -> bool {
-    if (!mbar_wait_bounded(m, ph, kMaxPolls)) *abort_s = 1;
+  // Bounded wait of this thread on an MMA barrier (each thread then reads only
+  // its own TMEM lanes, so no CTA barrier is needed here); a wait that gives
+  // up is recorded and agreed on at the next phase barrier.
+  bool fail = false;
+  auto wait_mma = [&](uint64_t *m, uint32_t &ph) {
+    if (!mbar_wait_bounded(m, ph, kMaxPolls)) fail = true;
     ph ^= 1;
     fence_after_sync();
-    return __syncthreads_or(*abort_s) == 0;
+  };
+  // End of a phase: CTA barrier that also agrees on failure.
+  auto phase_sync = [&]() -> bool {
+    fence_before_sync();
+    return __syncthreads_or(fail) == 0;
   };
 
   for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
@@ -508,55 +515,47 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
       // re-split -> column MMAs -> demodulate.
       for (int n = 0; n < a.K && ok; ++n) {
         modulate();
-        fence_before_sync();
-        __syncthreads();
+        if (!(ok = phase_sync())) break;
         if (row_issuer) issue_row();
         if (n + 1 < a.K)
           build_lut<BF, NT, kParts == 1>(lut16, lutf + ((n + 1) % 3) * kLutStride, n + 1, a.twoT, a.T, c0, tid);
-        if (!(ok = wait_mma(mbarR, phR))) break;
+        wait_mma(mbarR, phR);
         resplit();
-        fence_before_sync();
-        __syncthreads();
+        if (!(ok = phase_sync())) break;
         if (col_issuer) issue_col();
-        if (!(ok = wait_mma(mbarC, phC))) break;
+        wait_mma(mbarC, phC);
         demod(n);
-        fence_before_sync();
-        __syncthreads();
+        if (!(ok = phase_sync())) break;
       }
     } else {
       // Pipelined schedule: the column MMAs of harmonic n run while harmonic n+1
       // is modulated, and the row MMAs of n+1 run while n is demodulated and the
       // tables of n+2 are built.
       modulate();
-      fence_before_sync();
-      __syncthreads();
-      if (row_issuer) issue_row();
-      if (a.K > 1) build_lut<BF, NT, kParts == 1>(lut16, lutf + 1 * kLutStride, 1, a.twoT, a.T, c0, tid);
-      ok = wait_mma(mbarR, phR);
+      ok = phase_sync();
       if (ok) {
+        if (row_issuer) issue_row();
+        if (a.K > 1) build_lut<BF, NT, kParts == 1>(lut16, lutf + 1 * kLutStride, 1, a.twoT, a.T, c0, tid);
+        wait_mma(mbarR, phR);
         resplit();
-        fence_before_sync();
-        __syncthreads();
+        ok = phase_sync();
       }
       for (int n = 0; n < a.K && ok; ++n) {
         if (col_issuer) issue_col();  // C(n): A2 -> D2
         if (n + 1 < a.K) modulate();  // A1 <- harmonic n+1 (R(n) has finished)
-        fence_before_sync();
-        __syncthreads();
+        if (!(ok = phase_sync())) break;
         if (n + 1 < a.K && row_issuer) issue_row();  // R(n+1): A1 -> D1
         // Tables of n+2 while C(n) and R(n+1) run: lut16 (last read by the
         // modulation of n+1, done) and lutf buffer (n+2) % 3 (not read by demod(n)).
         if (n + 2 < a.K)
           build_lut<BF, NT, kParts == 1>(lut16, lutf + ((n + 2) % 3) * kLutStride, n + 2, a.twoT, a.T, c0, tid);
-        if (!(ok = wait_mma(mbarC, phC))) break;
+        wait_mma(mbarC, phC);
         demod(n);  // D2, table n
-        fence_before_sync();
-        __syncthreads();
+        if (!(ok = phase_sync())) break;
         if (n + 1 < a.K) {
-          if (!(ok = wait_mma(mbarR, phR))) break;
+          wait_mma(mbarR, phR);
           resplit();  // D1 -> A2 (C(n) has finished)
-          fence_before_sync();
-          __syncthreads();
+          if (!(ok = phase_sync())) break;
         }
       }
     }
