@@ -550,13 +550,21 @@ def run_ours(args):
     host_outs = [torch.empty((H, W_IMG), dtype=torch.float32).pin_memory() for _ in SETTINGS]
     e2e_steps = max(2, min(args.steps, 5))
 
+    copy_stream = torch.cuda.Stream(device=dev)
+    done = [torch.cuda.Event() for _ in SETTINGS]
+
     def e2e_step():
+        # Each output goes back on a copy stream while the next setting computes.
         with torch.cuda.stream(stream):
             xd = host_in.to(dev, non_blocking=True)
             for i, p in enumerate(params[head]):
-                y = fbf.fbf_filter(p, xd, out=outs[head][i], stream=stream)
-                host_outs[i].copy_(y, non_blocking=True)
+                fbf.fbf_filter(p, xd, out=outs[head][i], stream=stream)
+                done[i].record(stream)
+                copy_stream.wait_event(done[i])
+                with torch.cuda.stream(copy_stream):
+                    host_outs[i].copy_(outs[head][i], non_blocking=True)
         stream.synchronize()
+        copy_stream.synchronize()
 
     e2e_step()
     dist_barrier(world)

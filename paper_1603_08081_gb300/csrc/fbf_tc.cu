@@ -529,8 +529,8 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
       }
     } else {
       // Pipelined schedule: the column MMAs of harmonic n run while harmonic n+1
-      // is modulated, and the row MMAs of n+1 run while n is demodulated and the
-      // tables of n+2 are built.
+      // is modulated, and the row MMAs of n+1 run while the tables of n+2 are
+      // built and n is demodulated; two CTA barriers per harmonic.
       modulate();
       ok = phase_sync();
       if (ok) {
@@ -551,12 +551,12 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
           build_lut<BF, NT, kParts == 1>(lut16, lutf + ((n + 2) % 3) * kLutStride, n + 2, a.twoT, a.T, c0, tid);
         wait_mma(mbarC, phC);
         demod(n);  // D2, table n
-        if (!(ok = phase_sync())) break;
         if (n + 1 < a.K) {
+          // C(n) has finished (observed above), so A2 may be overwritten.
           wait_mma(mbarR, phR);
-          resplit();  // D1 -> A2 (C(n) has finished)
-          if (!(ok = phase_sync())) break;
+          resplit();  // D1 -> A2
         }
+        if (!(ok = phase_sync())) break;
       }
     }
     // ---- combine the four channel partials and write fhat = P / Q.
