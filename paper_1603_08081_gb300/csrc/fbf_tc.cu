@@ -313,10 +313,16 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
 
   // ---- modulate harmonic n: ext row r = 32 q + lane; units of 4 TMEM columns
   // (8 ext columns) u = h, h + kGroups, ... of the A1C / 4 units.
+  // With four warp groups, group 0 (whose lane-0 threads issue the MMAs)
+  // takes no modulation units and no table building: the issue cost overlaps
+  // the other groups' work instead of delaying group 0's share of it.
+  constexpr int kModGroups = kGroups > 2 ? kGroups - 1 : kGroups;
+  const int hm = kGroups > 2 ? h - 1 : h;                     // -1: no modulation units
+  const int btid = kGroups > 2 ? (tid >= 256 ? tid - 256 : 256) : tid;  // table-building index
   auto modulate = [&]() {
     const unsigned short *tcol = tileT + 32 * q + lane;
 #pragma unroll 1
-    for (int u = h; u < A1C / 4; u += kGroups) {
+    for (int u = hm; u >= 0 && u < A1C / 4; u += kModGroups) {
       const int col = 4 * u;
       uint4 e[8];  // table entries of 8 ext columns (the single form reads the hi half only)
 #pragma unroll
@@ -518,7 +524,8 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
         if (!(ok = phase_sync())) break;
         if (row_issuer) issue_row();
         if (n + 1 < a.K)
-          build_lut<BF, NT, kParts == 1>(lut16, lutf + ((n + 1) % 3) * kLutStride, n + 1, a.twoT, a.T, c0, tid);
+          build_lut<BF, NT, kParts == 1>(lut16, lutf + ((n + 1) % 3) * kLutStride, n + 1, a.twoT, a.T, c0,
+                                         btid);
         wait_mma(mbarR, phR);
         resplit();
         if (!(ok = phase_sync())) break;
@@ -535,7 +542,7 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
       ok = phase_sync();
       if (ok) {
         if (row_issuer) issue_row();
-        if (a.K > 1) build_lut<BF, NT, kParts == 1>(lut16, lutf + 1 * kLutStride, 1, a.twoT, a.T, c0, tid);
+        if (a.K > 1) build_lut<BF, NT, kParts == 1>(lut16, lutf + 1 * kLutStride, 1, a.twoT, a.T, c0, btid);
         wait_mma(mbarR, phR);
         resplit();
         ok = phase_sync();
@@ -548,7 +555,8 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
         // Tables of n+2 while C(n) and R(n+1) run: lut16 (last read by the
         // modulation of n+1, done) and lutf buffer (n+2) % 3 (not read by demod(n)).
         if (n + 2 < a.K)
-          build_lut<BF, NT, kParts == 1>(lut16, lutf + ((n + 2) % 3) * kLutStride, n + 2, a.twoT, a.T, c0, tid);
+          build_lut<BF, NT, kParts == 1>(lut16, lutf + ((n + 2) % 3) * kLutStride, n + 2, a.twoT, a.T, c0,
+                                         btid);
         wait_mma(mbarC, phC);
         demod(n);  // D2, table n
         if (n + 1 < a.K) {
