@@ -88,11 +88,17 @@ fbf_status launch_filter(const FilterArgs &a, fbf_form form, fbf_dtype dtype, cu
   return launch_fp32_u8(a, stream);
 }
 
-// AUTO: the tensor-core FP16 form for Gaussian windows from W = 10 up (2048^2,
-// K = 17 on GB300: W = 15 0.59 vs 0.82 ms, W = 30 1.04 vs 1.51 ms; at W = 9 the
-// two are equal, 0.59 vs 0.60 ms); the FP32 form otherwise, and always for the
-// box kernel, whose running window sums make the FP32 form the faster one.
-bool auto_picks_tc(const FilterArgs &a) { return a.W >= 10 && !a.box; }
+// AUTO: the faster of the FP32 and split tensor-core FP16 forms for the window,
+// from a sweep on GB300 (2048^2 u8, K = 17, ms FP32 / TC): Gaussian W = 5
+// 0.449 / 0.464, W = 6 0.483 / 0.464, W = 9 0.595 / 0.501, W = 30 1.50 / 0.94;
+// box (FP32 as running sums) W = 7 0.452 / 0.464, W = 8 0.488 / 0.464, W = 16
+// 0.662 / 0.499, W = 17 0.726 / 0.853, W = 22 ~0.85 / 0.854, W = 24 0.893 /
+// 0.854.  The tensor-core cost steps at W = 17 (64-row tiles), the FP32 cost
+// grows with the taps (slowly for the box sums).
+bool auto_picks_tc(const FilterArgs &a) {
+  if (!a.box) return a.W >= 6;
+  return (a.W >= 8 && a.W <= 16) || a.W >= 23;
+}
 
 }  // namespace fbf
 
