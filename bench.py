@@ -199,9 +199,9 @@ def tc_issued_flops(K: int, W: int, form: str) -> float:
     BY = 96 for W <= 16 else 64; per harmonic and tile, the row pass issues 4
     channels x ceil((32 + 2W) / 16) K-chunks of M = 128, N = 32, K = 16, the
     column pass BY / NBC output blocks x ceil((NBC + 2W) / 16) chunks of
-    N = NBC, NBC = 48 for BY = 96 else 16; each chunk once per split product)."""
+    N = NBC, NBC = 48 for BY = 96 else 32; each chunk once per split product)."""
     nsplit = TC_NSPLIT[form]
-    BY, NBC = (96, 48) if W <= 16 else (64, 16)
+    BY, NBC = (96, 48) if W <= 16 else (64, 32)
     kcr = (32 + 2 * W + 15) // 16
     kcc = (NBC + 2 * W + 15) // 16
     tiles = math.ceil(W_IMG / 32) * math.ceil(H / BY)

@@ -605,7 +605,7 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
 #define FBF_TC_NBC_96 48
 #endif
 #ifndef FBF_TC_NBC_64
-#define FBF_TC_NBC_64 16
+#define FBF_TC_NBC_64 32
 #endif
 #ifndef FBF_TC_NT_96
 #define FBF_TC_NT_96 512  // threads per CTA, 96-row tiles

@@ -220,3 +220,17 @@ def test_box_4096_exponential_sampled(fbf, border):
     for form in FORMS:
         got = _gpu(fbf, img, c, 1.0, W=8, spatial="box", border=border, form=form)
         _check(got[ys, xs], ref, TOL[form])
+
+
+@pytest.mark.parametrize("spatial,W,expect", [("gaussian", 3, "fp32"), ("gaussian", 5, "fp32"),
+                                              ("gaussian", 6, "tc_fp16"), ("gaussian", 30, "tc_fp16"),
+                                              ("box", 4, "fp32"), ("box", 10, "tc_fp16"),
+                                              ("box", 20, "fp32"), ("box", 24, "tc_fp16")])
+def test_auto_form_picks_the_documented_kernel(fbf, spatial, W, expect):
+    """AUTO runs exactly the kernel of the form its rule names (bit-identical output)."""
+    img = make_image(150, 170, seed=W)
+    c = fbf.fbf_fit_coeffs("gaussian", 25.0, 255.0, 1e-3)
+    auto = _gpu(fbf, img, c, max(W, 1) / 3.0, W=W, spatial=spatial, form="auto")
+    want = _gpu(fbf, img, c, max(W, 1) / 3.0, W=W, spatial=spatial, form=expect)
+    assert np.array_equal(auto, want)
+    _check(auto, _oracle_full(img, c, max(W, 1) / 3.0, W, spatial, "reflect"), TOL[expect])
