@@ -8,22 +8,24 @@
 // rows fit the 128 TMEM lanes (BY = 96 for W <= 16, 64 for W <= 32).  For each
 // harmonic n:
 //
-//   modulate  thread (lane r, group h) gathers, for ext row r and a quarter
-//             of the ext columns, the per-harmonic table entry of each pixel value:
-//             (cos, sin, f cos, f sin)(n w f) already split into hi + lo 16-bit
-//             parts, pairs neighbouring columns with byte permutes and writes
-//             them with tcgen05.st into TMEM: A1[c][part] (lane = ext row,
-//             K = ext column, two 16-bit elements per 32-bit column);
+//   modulate  thread (lane r, group h) gathers, for ext row r and its share
+//             of the ext columns, the per-harmonic table entry of each pixel
+//             value: (cos, sin, f cos, f sin)(n w f) already rounded to 16
+//             bits (hi, and lo = the rounding residual for the split forms),
+//             pairs neighbouring columns with byte permutes and writes them
+//             with tcgen05.st into TMEM: A1[c][part] (lane = ext row, K = ext
+//             column, two 16-bit elements per 32-bit column);
 //   row MMA   D1[c] (lane = ext row, 32 columns = outputs x) = sum over
-//             16-wide K chunks of A1[c][part] * T_i[part]; T_i is the 16 x 16
-//             Toeplitz block of chunk offset i (entries w[16 i + k - n]), the
-//             same block for every output block (banded: only the
-//             ceil((16 + 2W) / 16) chunks that meet the band are issued);
-//   re-split  D1 rows are read back (tcgen05.ld), split into hi / lo again
-//             and stored to shared memory as the MN-major A operand of the
-//             column pass, A2[m = c * 32 + x][K = ext row] -- each thread
+//             16-wide K chunks of A1[c][part] * T_i; T_i is the 16 x 32
+//             Toeplitz block of chunk offset i (entries w[16 i + k - n]);
+//             only the ceil((32 + 2W) / 16) chunks that meet the band are
+//             issued;
+//   re-split  D1 rows are read back (tcgen05.ld), rounded to 16 bits again
+//             (hi, lo) and stored to shared memory as the MN-major A operand
+//             of the column pass, A2[m = 4 x + c][K = ext row] -- each thread
 //             writes its own row, so no transpose is needed;
-//   col MMA   D2 (lane m = (c, x), columns = output rows y) = sum A2 * T_i;
+//   col MMA   D2 (lane m = 4 x + c, columns = output rows y) = sum A2 * T_i,
+//             in output blocks of 48 (BY = 96) or 32 (BY = 64) rows;
 //   demod     lane (c, x) accumulates d_n * trig(n w f(y, x)) * D2 into its
 //             own partial: cos for the G_r / F_r channels, sin for G_i / F_i.
 //
@@ -32,17 +34,30 @@
 // (f - c0) with c0 = T / 2 instead of f: the sums become P - c0 Q, the ratio is
 // unchanged in exact arithmetic, and the magnitudes rounded to 16 bits halve.
 //
+// Schedule (pipelined; the serial one for the split forms at W > 16): per
+// harmonic two phases separated by CTA barriers --
+//   (1) group 0 issues the column MMAs of n while groups 1-3 modulate n + 1;
+//   (2) group 0 issues the row MMAs of n + 1 while groups 2-3 build the tables
+//       of n + 2; then every thread waits for the column MMAs of n (its own
+//       mbarrier wait: it reads only its own TMEM lanes), demodulates n, waits
+//       for the row MMAs of n + 1 and re-splits them.
+// MMAs are issued by lane 0 of the four warps of group 0, which own disjoint
+// accumulators; a bounded mbarrier wait that gives up is OR-reduced at the
+// next barrier and the CTA stops with a device error word set.
+//
 // The kernel is persistent (one CTA per SM walks the tiles blockIdx.x,
 // blockIdx.x + gridDim.x, ...; TMEM, barriers and Toeplitz blocks are set up
 // once).  While a tile is processed, the next tile's halo is prefetched by a
 // 2-D TMA copy (cp.async.bulk.tensor) into a raw shared-memory box, which the
-// next tile transposes into the staged tile.  Under REFLECT only interior tiles
-// (no mirrored pixel in the halo) take the TMA path, border tiles load with
-// reflected indices; under TRUNCATE every tile does (out-of-image box entries
-// become the zero-channel sentinel by their coordinates).  Precision: the data are split
-// hi + lo; FP16 uses one weight part (2 products per step), BF16 splits the
-// weights too (3 products); the single FP16 form rounds data and weights once
-// (1 product per step: half the MMAs, table entries and re-split stores).  Table entries, the phase (exact integer
+// next tile transposes into the staged tile.  Under REFLECT only interior
+// tiles (no mirrored pixel in the halo) take the TMA path, border tiles load
+// with reflected indices; under TRUNCATE every tile does (out-of-image box
+// entries become the zero-channel sentinel by their coordinates).
+//
+// Precision: the split forms carry data as hi + lo; FP16 uses one weight part
+// (2 products per step), BF16 splits the weights too (3 products); the single
+// FP16 form rounds data and weights once (1 product per step: half the MMAs,
+// table entries and re-split stores).  Table entries, the phase (exact integer
 // reduction), the K-term accumulation and the ratio stay in FP32.
 #include <cuda.h>
 #include <cuda_bf16.h>
