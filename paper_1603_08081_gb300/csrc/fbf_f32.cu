@@ -186,12 +186,12 @@ __global__ void __launch_bounds__(kNTf, 1) fbf_f32_kernel(const __grid_constant_
     }
     __syncthreads();
     if (MODE == kModeAdjoint) {
-      // ---- adjoint channels: (a cos, -a sin, b cos, -b sin)(n w f), zero outside the image.
+      // ---- adjoint channels: (a cos, -a sin, b cos, -b sin)(n w f), zero outside
+      // the image, from the forward channels in place (their cos, sin).
       for (int e = tid; e < kHXA * kHYP; e += kNTf) {
-        const float fv = S.fT[e];
         const float2 abv = S.abT[e];
-        float sn = 0.f, cs = 0.f;
-        if (fv == fv) sincospif((float)n * fv * invT, &sn, &cs);
+        const u64 c = S.chan[e].x;
+        const float cs = lo_f(c), sn = hi_f(c);
         S.chan[e] = make_ulonglong2(pack_f(abv.x * cs, -abv.x * sn), pack_f(abv.y * cs, -abv.y * sn));
       }
       __syncthreads();
