@@ -263,15 +263,13 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
   const float c0 = 0.5f * a.T;  // intensity centre
   constexpr unsigned short kScale = kCopies * sizeof(uint4), kSent = kSentinel * kCopies * sizeof(uint4);
 
-  // Whether a tile's halo comes through the TMA box: always under TRUNCATE,
-  // under REFLECT only when no halo pixel is mirrored.
-  auto tma_tile = [&](int t) -> bool {
-    if (!use_tma) return false;
-    if (!reflect) return true;
-    const int ty = t / a.tiles_x, tx = t - ty * a.tiles_x;
-    const int y0 = ty * BY - W, x0 = tx * kBX - W;
-    return y0 >= 0 && y0 + HY <= H && x0 >= 0 && x0 + HX <= Wd;
-  };
+  // Whether the tiles' halos come through the TMA box: always under TRUNCATE;
+  // under REFLECT when a single mirror reaches every halo pixel (W < H, W < Wd):
+  // the mirrored source of every halo pixel that can touch an output inside
+  // the image (rows < H + W, columns < Wd + W) then lies inside the box.
+  const bool tma_all = use_tma && (!reflect || (W < H && W < Wd));
+  auto tma_tile = [&](int) -> bool { return tma_all; };
+  auto mirror = [](int i, int n) -> int { return i < 0 ? -i - 1 : (i >= n ? 2 * n - 1 - i : i); };
   auto box_x = [&](int t) -> int {  // 16-byte aligned start column of tile t's box
     const int tx = t - (t / a.tiles_x) * a.tiles_x;
     const int x0 = tx * kBX - W;
@@ -491,17 +489,22 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
         ok = false;
         break;
       }
-      const int xoff = (tx0 - W) - box_x(tile);
+      // Box origin: column box_x(tile), row ty0 - W.  REFLECT reads the mirrored
+      // source of halo pixels outside the image; pixels that touch no output
+      // inside the image become the sentinel.
+      const int bx0 = box_x(tile);
       for (int ey = warp; ey < kLanes; ey += NT / 32) {
         const int iy = ty0 - W + ey;
-        const bool row_ok = ey < HY && iy >= 0 && iy < H;
+        const bool row_ok = ey < HY && (reflect ? iy < H + W : (iy >= 0 && iy < H));
+        const unsigned char *brow = raw + (reflect ? mirror(iy, H) - (ty0 - W) : ey) * kBoxW;
 #pragma unroll
         for (int k4 = 0; k4 < 4; ++k4) {
           const int ex = lane + 32 * k4;
           if (ex < KX) {
             const int ix = tx0 - W + ex;
-            const bool in = row_ok && ex < HX && ix >= 0 && ix < Wd;
-            tileT[ex * kPT + ey] = in ? (unsigned short)(raw[ey * kBoxW + xoff + ex] * kScale) : kSent;
+            const bool in = row_ok && ex < HX && (reflect ? ix < Wd + W : (ix >= 0 && ix < Wd));
+            const int sx = (reflect ? mirror(ix, Wd) : ix) - bx0;
+            tileT[ex * kPT + ey] = in ? (unsigned short)(brow[sx] * kScale) : kSent;
           }
         }
       }
@@ -584,17 +587,20 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
     }
     // ---- combine the four channel partials and write fhat = P / Q.
     if (ok) {
-      float *comb = reinterpret_cast<float *>(A2);  // [c][y][x], 4 * BY * 32 floats
+      // [c][y][x] with the channel planes 8 floats apart in bank position, so that
+      // the four channel lanes of one x store to different banks
+      constexpr int kCS = BY * kBX + 8;
+      float *comb = reinterpret_cast<float *>(A2);
       const int x = 8 * q + (lane >> 2), c = lane & 3;
-  #pragma unroll
-      for (int j = 0; j < BYH; ++j) comb[(c * BY + h * BYH + j) * kBX + x] = part[j];
+#pragma unroll
+      for (int j = 0; j < BYH; ++j) comb[c * kCS + (h * BYH + j) * kBX + x] = part[j];
       __syncthreads();
       for (int e = tid; e < BY * kBX; e += NT) {
         const int y = e / kBX, xx = e - y * kBX;
         const int iy = ty0 + y, ix = tx0 + xx;
         if (iy < H && ix < Wd) {
-          const float Q = comb[(0 * BY + y) * kBX + xx] + comb[(1 * BY + y) * kBX + xx];
-          const float P = comb[(2 * BY + y) * kBX + xx] + comb[(3 * BY + y) * kBX + xx];
+          const float Q = comb[0 * kCS + y * kBX + xx] + comb[1 * kCS + y * kBX + xx];
+          const float P = comb[2 * kCS + y * kBX + xx] + comb[3 * kCS + y * kBX + xx];
           *reinterpret_cast<float *>(reinterpret_cast<char *>(a.out) + (size_t)iy * a.out_pitch +
                                      (size_t)ix * sizeof(float)) = P / Q + c0;
         }
