@@ -181,6 +181,26 @@ def cpu_baseline(img, slab_rows: int):
            "kind": "oracle",
            "sample": "FP64 Algorithm-1 oracle on rows 0..%d of the 2048x2048 image, all %d settings"
                      " (%d pixels, %.1f s)" % (slab_rows - 1, len(SETTINGS), total_px, total_t)}
+    # The same oracle on one core (16 rows per setting), and the direct O(W^2)
+    # filter eq. (1) on a 512x512 crop (sigma_s = 3, sigma_r = 20, all cores).
+    cores = O.num_threads()
+    O.set_threads(1)
+    t1, px1 = 0.0, 0
+    for (ss, sr) in SETTINGS:
+        out, dt, _ = oracle_slab(img, ss, sr, (0, 16))
+        t1 += dt
+        px1 += out.size
+    O.set_threads(cores)
+    res["one_core"] = {"value": round(px1 / t1 / 1e6, 4), "unit": "Mpixel/s",
+                       "sample": "rows 0..15 of every setting (%d pixels, %.1f s)" % (px1, t1)}
+    crop = np.ascontiguousarray(img[:512, :512])
+    w1 = O.weights_1d(O.SPATIAL_GAUSSIAN, 3.0, O.default_W(3.0))
+    t0 = time.perf_counter()
+    O.direct_bf(crop, w1, O.BORDER_REFLECT, O.RANGE_GAUSSIAN, 20.0)
+    td = time.perf_counter() - t0
+    res["direct_eq1_512"] = {"value": round(crop.size / td / 1e6, 4), "unit": "Mpixel/s", "cores": cores,
+                             "sample": "exact filter eq. (1), 512x512 crop, sigma_s=3 (W=9), sigma_r=20 "
+                                       "(%.2f s)" % td}
     return res, slabs
 
 

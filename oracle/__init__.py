@@ -67,6 +67,8 @@ def _load():
             lib.orc_grad_direct.restype = None
             lib.orc_grad_at.argtypes = [dp, dp, i, i, dp, i, i, dp, i, d, ip, ip, lp, dp]
             lib.orc_grad_at.restype = None
+            lib.orc_set_threads.argtypes = [i]
+            lib.orc_set_threads.restype = None
             lib.orc_local_range.argtypes = [dp, i, i, i, i]
             lib.orc_local_range.restype = d
             _lib = lib
@@ -83,6 +85,11 @@ def _ip(a):
 
 def num_threads() -> int:
     return int(_load().orc_num_threads())
+
+
+def set_threads(n: int) -> None:
+    """Threads of the oracle's parallel loops from now on (for timing)."""
+    _load().orc_set_threads(int(n))
 
 
 def phi(kernel: int, sigma_r: float, t: float) -> float:

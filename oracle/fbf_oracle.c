@@ -63,6 +63,15 @@ int orc_num_threads(void) {
 #endif
 }
 
+/* Threads of the following parallel loops (timing on one core or all). */
+void orc_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}
+
 /* Range kernel.  Gaussian: eq. (3).  Exponential: exp(-|t|/sigma_r), the kernel
  * of the works cited in Sec. I (the paper names it without printing it). */
 double orc_phi(int kernel, double sigma_r, double t) {
