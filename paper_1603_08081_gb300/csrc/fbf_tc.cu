@@ -99,13 +99,18 @@ struct TcLayout {
   int kcc;  // the same for one NBC-output block (column pass)
   int KX;   // K extent of the row pass (ext columns, multiple of 16)
   int A1C;  // TMEM columns per (channel, part) of A1 = KX / 2
-  size_t lut16_off, lutf_off, a2_off, br_off, bc_off, tile_off, raw_off, bar_off, bytes;
+  size_t lut16_off, lutf_off, a2_off, br_off, bc_off, tile_off, raw_off, trig_off, bar_off, bytes;
 };
+
+// (cos, sin)(pi m / T) for the phase indices m < 2T, built once per CTA when
+// 2T <= kTrigMax (the per-harmonic tables then look the phase up instead of
+// evaluating sincospi on their critical path).
+constexpr int kTrigMax = 1024;
 
 constexpr int kBoxW = 112;  // TMA box: 112 columns (>= 15 + KX) x 128 rows of bytes
 
 // Shared memory: [lut16 (one buffer)][lutf (three buffers)][A2 hi | lo]
-// [row Toeplitz blocks][column Toeplitz blocks][tile][TMA box][barriers, TMEM address, flags].
+// [row Toeplitz blocks][column Toeplitz blocks][tile][TMA box][trig][barriers, TMEM address, flags].
 __host__ __device__ inline TcLayout tc_layout(int W, int wcap, int nbr, int nbc) {
   TcLayout L;
   L.kcr = (nbr + 2 * W + 15) / 16;
@@ -121,7 +126,8 @@ __host__ __device__ inline TcLayout tc_layout(int W, int wcap, int nbr, int nbc)
   L.bc_off = L.br_off + (size_t)kcr_max * 2 * nbr * 32;
   L.tile_off = L.bc_off + (size_t)kcc_max * 2 * nbc * 32;
   L.raw_off = (L.tile_off + (size_t)KXmax * kPT * 2 + 1023) & ~(size_t)1023;  // TMA destination
-  L.bar_off = L.raw_off + (size_t)kBoxW * kLanes;
+  L.trig_off = L.raw_off + (size_t)kBoxW * kLanes;
+  L.bar_off = L.trig_off + (size_t)kTrigMax * sizeof(float2);
   L.bytes = L.bar_off + 64;
   return L;
 }
@@ -164,11 +170,18 @@ __device__ __forceinline__ float from16(unsigned short x) {
 // keeps only the hi words (uint2), in 16 copies of 8 bytes (the same 128 bytes
 // per value), so that the modulation's 8-byte gathers are conflict-free too.
 template <int BF, int NT, int SINGLE>
-__device__ __forceinline__ void build_lut(uint4 *L16, float2 *Lf, int n, int twoT, float T, float c0, int tid) {
+__device__ __forceinline__ void build_lut(uint4 *L16, float2 *Lf, const float2 *trig, int n, int twoT, float T,
+                                          float c0, int tid) {
   for (int v = tid; v < 256; v += NT) {
     const int m = (n * v) % twoT;  // exact phase index: n*omega*v = pi * m / T (mod 2 pi)
     float sn, cs;
-    sincospif((float)m / T, &sn, &cs);
+    if (twoT <= kTrigMax) {
+      const float2 t = trig[m];
+      cs = t.x;
+      sn = t.y;
+    } else {
+      sincospif((float)m / T, &sn, &cs);
+    }
     const float fv = (float)v - c0;  // centred intensity
     uint4 e;
     split2<BF>(cs, sn, e.x, e.z);
@@ -254,6 +267,7 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
   int *abort_s = reinterpret_cast<int *>(smem + Ly.bar_off + 32);
   uint64_t *mbarT = reinterpret_cast<uint64_t *>(smem + Ly.bar_off + 40);  // TMA box landed
   unsigned char *raw = smem + Ly.raw_off;
+  float2 *trig = reinterpret_cast<float2 *>(smem + Ly.trig_off);
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, cp = lane & (kCopies - 1);
   const int q = warp & 3, h = warp >> 2;  // TMEM lane quadrant, warp group
@@ -295,6 +309,8 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
   if (tid < kCopies) lut16[kSentinel * kCopies + tid] = make_uint4(0u, 0u, 0u, 0u);
   if (tid < 3 * kCopies)  // sentinel rows: zero channels
     lutf[(tid / kCopies) * kLutStride + kSentinel * kCopies + (tid % kCopies)] = make_float2(0.f, 0.f);
+  if (a.twoT <= kTrigMax)
+    for (int m = tid; m < a.twoT; m += NT) sincospif((float)m / a.T, &trig[m].y, &trig[m].x);
   build_toeplitz<BF, NBR, NT>(smem + Ly.br_off, kcr, W, a.w, tid);
   build_toeplitz<BF, NBC, NT>(smem + Ly.bc_off, kcc, W, a.w, tid);
   fence_before_sync();
@@ -513,7 +529,7 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
       stage_tile<NT>(static_cast<const unsigned char *>(a.in), a.in_pitch, H, Wd, a.border, ty0 - W, tx0 - W, HY,
                       HX, kLanes, KX, tileT, kPT, kScale, kSent);
     }
-    build_lut<BF, NT, kParts == 1>(lut16, lutf, 0, a.twoT, a.T, c0, tid);
+    build_lut<BF, NT, kParts == 1>(lut16, lutf, trig, 0, a.twoT, a.T, c0, tid);
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
@@ -542,7 +558,7 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
         if (!(ok = phase_sync())) break;
         if (row_issuer) issue_row();
         if (n + 1 < a.K)
-          build_lut<BF, NT, kParts == 1>(lut16, lutf + ((n + 1) % 3) * kLutStride, n + 1, a.twoT, a.T, c0,
+          build_lut<BF, NT, kParts == 1>(lut16, lutf + ((n + 1) % 3) * kLutStride, trig, n + 1, a.twoT, a.T, c0,
                                          btid);
         wait_mma(mbarR, phR);
         resplit();
@@ -560,7 +576,7 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
       ok = phase_sync();
       if (ok) {
         if (row_issuer) issue_row();
-        if (a.K > 1) build_lut<BF, NT, kParts == 1>(lut16, lutf + 1 * kLutStride, 1, a.twoT, a.T, c0, btid);
+        if (a.K > 1) build_lut<BF, NT, kParts == 1>(lut16, lutf + 1 * kLutStride, trig, 1, a.twoT, a.T, c0, btid);
         wait_mma(mbarR, phR);
         resplit();
         ok = phase_sync();
@@ -573,7 +589,7 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
         // Tables of n+2 while C(n) and R(n+1) run: lut16 (last read by the
         // modulation of n+1, done) and lutf buffer (n+2) % 3 (not read by demod(n)).
         if (n + 2 < a.K)
-          build_lut<BF, NT, kParts == 1>(lut16, lutf + ((n + 2) % 3) * kLutStride, n + 2, a.twoT, a.T, c0,
+          build_lut<BF, NT, kParts == 1>(lut16, lutf + ((n + 2) % 3) * kLutStride, trig, n + 2, a.twoT, a.T, c0,
                                          btid);
         wait_mma(mbarC, phC);
         demod(n);  // D2, table n
