@@ -18,16 +18,16 @@ __device__ __forceinline__ int reflect_index(int i, int n) {
 }
 
 // Stage the halo tile whose ext pixel (0, 0) is image pixel (y0, x0) into
-// tileT[ex * pt + ey] (column-major), for ey < nrows and ex < ncols.  Each
+// tileT[ex * sx + ey * sy], for ey < nrows and ex < ncols.  Each
 // entry is (pixel value) * scale -- the byte offset of that value's row in a
 // channel table -- or `sentinel` for padding (ey >= rows_valid or ex >=
 // cols_valid) and, under TRUNCATE, for pixels outside the image.  Warps take
-// rows, lanes take columns (coalesced global reads; the column-major writes hit
-// distinct banks when pt / 2 is odd); up to 8 loads per thread are in flight.
+// rows, lanes take columns (coalesced global reads; column-major writes, sy = 1,
+// hit distinct banks when sx / 2 is odd); up to 8 loads per thread are in flight.
 template <int NT>
 __device__ __forceinline__ void stage_tile(const unsigned char *__restrict__ in, size_t pitch, int H, int Wd,
                                            int border, int y0, int x0, int rows_valid, int cols_valid,
-                                           int nrows, int ncols, unsigned short *tileT, int pt,
+                                           int nrows, int ncols, unsigned short *tileT, int sx, int sy,
                                            unsigned short scale, unsigned short sentinel) {
   constexpr int NW = NT / 32;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -63,7 +63,7 @@ __device__ __forceinline__ void stage_tile(const unsigned char *__restrict__ in,
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const int ex = lane + 32 * k;
-          if (ex < ncols) tileT[ex * pt + ey] = v[rr][k];
+          if (ex < ncols) tileT[ex * sx + ey * sy] = v[rr][k];
         }
       }
     }

@@ -243,7 +243,7 @@ __device__ __forceinline__ void k1_tile(const K1View &a, int ty0, int tx0, unsig
   // Stage the halo tile, transposed: tileT[ex * PT + ey] (byte offsets into a table buffer).
   static_assert(BX + 2 * WCAP + kRun <= 128, "staging covers at most 128 ext columns");
   stage_tile<NT>(a.in, a.in_pitch, H, Wd, a.border, ty0 - W, tx0 - W,
-                 Ly.HY, Ly.HX, Ly.HYP, Ly.HXA, tileT, Ly.PT, (unsigned short)(kCopies * sizeof(float4)),
+                 Ly.HY, Ly.HX, Ly.HYP, Ly.HXA, tileT, Ly.PT, 1, (unsigned short)(kCopies * sizeof(float4)),
                  (unsigned short)(kSentinel * kCopies * sizeof(float4)));
   build_lut(lut, 0, a.twoT, a.T, tid, NT);
   __syncthreads();

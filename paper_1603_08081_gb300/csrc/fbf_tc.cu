@@ -89,7 +89,19 @@ constexpr int kLutStride = kLutEntries * kCopies;  // entries per table buffer
 // The staged tile holds v * 128, the byte offset of v's row in lut16 (half of it in lutf).
 constexpr int kBX = 32;                             // output columns per tile
 constexpr int kLanes = 128;                         // TMEM lanes = halo rows per tile
-constexpr int kPT = kLanes + 2;                     // tile pitch (u16), PT/2 odd
+// Staged tile, in one of two layouts:
+//  * column-major (windows up to 16): one column of 128 ext rows per ext
+//    column, pitch kPT u16 (kPT / 2 odd); the modulation reads one u16 per
+//    lane and ext column, conflict-free across the lanes (rows).
+//  * row-major (wider windows, 3x the ext columns): one row of KX u16 offsets
+//    per ext row, padded to a pitch of KXmax + 8 u16 (an odd number of 16-byte
+//    units), so that the 16-byte loads of 8 ext columns by neighbouring rows are
+//    conflict-free: half the load wavefronts of the column-major reads, at the
+//    cost of unpacking the offsets (which costs more than it saves when the
+//    tile has few ext columns).
+constexpr int kPT = kLanes + 2;
+__host__ __device__ constexpr int tile_pitch(int kxmax) { return kxmax + 8; }
+__host__ __device__ constexpr bool tile_row_major(int wcap) { return wcap > 16; }
 constexpr int kA2Group = 2048;                      // bytes per 8-row K group of A2 (16 M groups x 128 B)
 constexpr int kA2Part = 16 * kA2Group;              // one part of A2: 128 (M) x 128 (K) x 16 bit
 constexpr uint32_t kMaxPolls = 1u << 22;
@@ -124,8 +136,10 @@ __host__ __device__ inline TcLayout tc_layout(int W, int wcap, int nbr, int nbc)
   L.a2_off = (L.lutf_off + 3ull * kLutStride * sizeof(float2) + 1023) & ~(size_t)1023;
   L.br_off = L.a2_off + 2ull * kA2Part;
   L.bc_off = L.br_off + (size_t)kcr_max * 2 * nbr * 32;
-  L.tile_off = L.bc_off + (size_t)kcc_max * 2 * nbc * 32;
-  L.raw_off = (L.tile_off + (size_t)KXmax * kPT * 2 + 1023) & ~(size_t)1023;  // TMA destination
+  L.tile_off = L.bc_off + (size_t)kcc_max * 2 * nbc * 32;  // 32-byte aligned
+  const size_t tile_bytes =
+      tile_row_major(wcap) ? (size_t)kLanes * tile_pitch(KXmax) * 2 : (size_t)KXmax * kPT * 2;
+  L.raw_off = (L.tile_off + tile_bytes + 1023) & ~(size_t)1023;  // TMA destination
   L.trig_off = L.raw_off + (size_t)kBoxW * kLanes;
   L.bar_off = L.trig_off + (size_t)kTrigMax * sizeof(float2);
   L.bytes = L.bar_off + 64;
@@ -261,6 +275,11 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
   float2 *lutf = reinterpret_cast<float2 *>(smem + Ly.lutf_off);
   unsigned char *A2 = smem + Ly.a2_off;
   unsigned short *tileT = reinterpret_cast<unsigned short *>(smem + Ly.tile_off);
+  // element (ext row ey, ext column ex) of the staged tile at ey * kTY + ex * kTX
+  constexpr bool kRM = tile_row_major(WCAP);
+  constexpr int kTP = tile_pitch(kBX - NBR + 16 * ((NBR + 2 * WCAP + 15) / 16));
+  static_assert(!kRM || (kTP * 2 / 16) % 2 == 1, "odd number of 16-byte units per tile row");
+  constexpr int kTY = kRM ? kTP : 1, kTX = kRM ? 1 : kPT;
   uint64_t *mbarR = reinterpret_cast<uint64_t *>(smem + Ly.bar_off);      // row MMAs done
   uint64_t *mbarC = reinterpret_cast<uint64_t *>(smem + Ly.bar_off + 8);  // column MMAs done
   uint32_t *tmem_base_s = reinterpret_cast<uint32_t *>(smem + Ly.bar_off + 16);
@@ -349,17 +368,27 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
   const int hm = kGroups > 2 ? h - 1 : h;                     // -1: no modulation units
   const int btid = kGroups > 2 ? (tid >= 256 ? tid - 256 : 256) : tid;  // table-building index
   auto modulate = [&]() {
-    const unsigned short *tcol = tileT + 32 * q + lane;
+    const unsigned short *trow = tileT + (32 * q + lane) * kTY;
 #pragma unroll 1
     for (int u = hm; u >= 0 && u < A1C / 4; u += kModGroups) {
       const int col = 4 * u;
+      uint32_t ow[4];  // row-major: offsets of ext columns 8u .. 8u + 7, two per word
+      if constexpr (kRM) {
+        const uint4 o = *reinterpret_cast<const uint4 *>(trow + 8 * u);
+        ow[0] = o.x, ow[1] = o.y, ow[2] = o.z, ow[3] = o.w;
+      }
       uint4 e[8];  // table entries of 8 ext columns (the single form reads the hi half only)
 #pragma unroll
       for (int j = 0; j < 8; ++j) {
+        uint32_t off;
+        if constexpr (kRM)
+          off = (j & 1) ? (ow[j >> 1] >> 16) : (ow[j >> 1] & 0xFFFFu);
+        else
+          off = trow[(8 * u + j) * kTX];
         if (kParts == 2) {
-          e[j] = *reinterpret_cast<const uint4 *>(L16 + tcol[(2 * col + j) * kPT]);
+          e[j] = *reinterpret_cast<const uint4 *>(L16 + off);
         } else {
-          const uint2 hi = *reinterpret_cast<const uint2 *>(L16 + tcol[(2 * col + j) * kPT]);
+          const uint2 hi = *reinterpret_cast<const uint2 *>(L16 + off);
           e[j] = make_uint4(hi.x, hi.y, 0u, 0u);
         }
       }
@@ -496,7 +525,7 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
     const int tile_y = tile / a.tiles_x, tile_x = tile - tile_y * a.tiles_x;
     const int ty0 = tile_y * BY, tx0 = tile_x * kBX;
 
-    // ---- stage this tile: 128 ext rows x KX ext columns, column-major byte offsets v * 128.
+    // ---- stage this tile: 128 ext rows x KX ext columns of byte offsets v * 128.
     if (tma_tile(tile)) {
       if (!mbar_wait_bounded(mbarT, phT, kMaxPolls)) *abort_s = 1;
       phT ^= 1;
@@ -520,14 +549,14 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
             const int ix = tx0 - W + ex;
             const bool in = row_ok && ex < HX && (reflect ? ix < Wd + W : (ix >= 0 && ix < Wd));
             const int sx = (reflect ? mirror(ix, Wd) : ix) - bx0;
-            tileT[ex * kPT + ey] = in ? (unsigned short)(brow[sx] * kScale) : kSent;
+            tileT[ey * kTY + ex * kTX] = in ? (unsigned short)(brow[sx] * kScale) : kSent;
           }
         }
       }
       fence_proxy_async_smem();  // the box is rewritten by the next TMA copy
     } else {
       stage_tile<NT>(static_cast<const unsigned char *>(a.in), a.in_pitch, H, Wd, a.border, ty0 - W, tx0 - W, HY,
-                      HX, kLanes, KX, tileT, kPT, kScale, kSent);
+                     HX, kLanes, KX, tileT, kTX, kTY, kScale, kSent);
     }
     build_lut<BF, NT, kParts == 1>(lut16, lutf, trig, 0, a.twoT, a.T, c0, tid);
     fence_before_sync();
@@ -544,10 +573,10 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
     for (int j = 0; j < BYH; ++j) part[j] = 0.f;
     {
       const int x = 8 * q + (lane >> 2);
-      const unsigned short *cen = tileT + (x + W) * kPT + W + h * BYH;
+      const unsigned short *cen = tileT + (W + h * BYH) * kTY + (x + W) * kTX;
 #pragma unroll
       for (int j = 0; j < BYH / 2; ++j)
-        cen_pk[j] = (uint32_t)(cen[2 * j] >> 1) | ((uint32_t)(cen[2 * j + 1] >> 1) << 16);
+        cen_pk[j] = (uint32_t)(cen[2 * j * kTY] >> 1) | ((uint32_t)(cen[(2 * j + 1) * kTY] >> 1) << 16);
     }
 
     if (!PIPE) {
