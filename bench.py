@@ -215,18 +215,24 @@ TC_NSPLIT = {"tc_fp16": 2, "tc_bf16": 3, "tc_fp16_single": 1}
 
 def tc_issued_flops(K: int, W: int, form: str) -> float:
     """Dense MMA flops the tensor-core kernel issues for one 2048x2048 launch,
-    band padding and split products included (mirrors its tiling: 32 x BY tiles,
-    BY = 96 for W <= 16 else 64; per harmonic and tile, the row pass issues 4
-    channels x ceil((32 + 2W) / 16) K-chunks of M = 128, N = 32, K = 16, the
-    column pass BY / NBC output blocks x ceil((NBC + 2W) / 16) chunks of
-    N = NBC, NBC = 48 for BY = 96 else 32; each chunk once per split product)."""
+    band padding and split products included (mirrors its tiling: tiles of 32
+    columns x min(BY, 128 - 2W) output rows, BY = 112 computed rows for W <= 16
+    else 64; per harmonic and tile, the row pass issues 4 channels x
+    ceil((32 + 2W) / 16) K-chunks of M = 128, N = 32, K = 16; the column pass
+    output blocks of NBC rows (one of 112 for BY = 112; 32 and 32 for BY = 64),
+    each with the K chunks meeting its band inside the 128 ext rows, of N = its
+    rows; each chunk once per split product)."""
     nsplit = TC_NSPLIT[form]
-    BY, NBC = (96, 48) if W <= 16 else (64, 32)
+    BY, NBC = (112, 112) if W <= 16 else (64, 32)
+    rows = min(BY, 128 - 2 * W)
     kcr = (32 + 2 * W + 15) // 16
-    kcc = (NBC + 2 * W + 15) // 16
-    tiles = math.ceil(W_IMG / 32) * math.ceil(H / BY)
+    tiles = math.ceil(W_IMG / 32) * math.ceil(H / rows)
     row = 4 * kcr * (2.0 * 128 * 32 * 16)
-    col = (BY // NBC) * kcc * (2.0 * 128 * NBC * 16)
+    col = 0.0
+    for start in range(0, BY, NBC):
+        n = min(NBC, BY - start)
+        kc = min((n + 2 * W + 15) // 16, (128 - start) // 16)
+        col += kc * (2.0 * 128 * n * 16)
     return tiles * K * (row + col) * nsplit
 
 

@@ -4,9 +4,12 @@
 // accumulation in tensor memory).
 //
 // One CTA (512 threads: four groups of four warps, warp w reaching TMEM lanes
-// 32 (w % 4) ... + 31) owns a 32-column x BY-row output tile; its BY + 2W halo
-// rows fit the 128 TMEM lanes (BY = 96 for W <= 16, 64 for W <= 32).  For each
-// harmonic n:
+// 32 (w % 4) ... + 31) owns a tile of 32 output columns and min(BY, 128 - 2W)
+// output rows, whose halo rows fill at most the 128 TMEM lanes (BY = 112
+// computed rows for W <= 16, 64 for W <= 32; rows computed past 128 - 2W have
+// a clipped band and are discarded).  Taller tiles mean fewer tiles: a 2048^2
+// image at W = 9 is 19 x 64 tiles of 110 rows, 8 waves of 152 CTAs, where
+// 96-row tiles took 10.  For each harmonic n:
 //
 //   modulate  thread (lane r, group h) gathers, for ext row r and its share
 //             of the ext columns, the per-harmonic table entry of each pixel
@@ -25,7 +28,8 @@
 //             of the column pass, A2[m = 4 x + c][K = ext row] -- each thread
 //             writes its own row, so no transpose is needed;
 //   col MMA   D2 (lane m = 4 x + c, columns = output rows y) = sum A2 * T_i,
-//             in output blocks of 48 (BY = 96) or 32 (BY = 64) rows;
+//             in one output block of 112 rows (BY = 112; its Toeplitz blocks
+//             are windows of one shared strip) or two of 32 (BY = 64);
 //   demod     lane (c, x) accumulates d_n * trig(n w f(y, x)) * D2 into its
 //             own partial: cos for the G_r / F_r channels, sin for G_i / F_i.
 //
@@ -49,10 +53,11 @@
 // blockIdx.x + gridDim.x, ...; TMEM, barriers and Toeplitz blocks are set up
 // once).  While a tile is processed, the next tile's halo is prefetched by a
 // 2-D TMA copy (cp.async.bulk.tensor) into a raw shared-memory box, which the
-// next tile transposes into the staged tile.  Under REFLECT only interior
-// tiles (no mirrored pixel in the halo) take the TMA path, border tiles load
-// with reflected indices; under TRUNCATE every tile does (out-of-image box
-// entries become the zero-channel sentinel by their coordinates).
+// next tile converts into the staged tile.  Under TRUNCATE out-of-image box
+// entries become the zero-channel sentinel by their coordinates; under REFLECT
+// the halo pixels outside the image read their mirrored source inside the box
+// (a single mirror reaches it when W < H and W < Wd; otherwise, and for
+// unaligned images, the tiles load directly with reflected indices).
 //
 // Precision: the split forms carry data as hi + lo; FP16 uses one weight part
 // (2 products per step), BF16 splits the weights too (3 products); the single
@@ -106,9 +111,30 @@ constexpr int kA2Group = 2048;                      // bytes per 8-row K group o
 constexpr int kA2Part = 16 * kA2Group;              // one part of A2: 128 (M) x 128 (K) x 16 bit
 constexpr uint32_t kMaxPolls = 1u << 22;
 
+// Output rows of one tile: the BY computed rows, at most the kLanes - 2W rows
+// whose 2W + 1 taps all lie in the 128 ext rows (the rows past that are
+// computed with a truncated band and discarded).
+__host__ __device__ constexpr int tile_rows(int by, int W) { return by < kLanes - 2 * W ? by : kLanes - 2 * W; }
+// Column pass: output blocks of nbc rows (the last one by - (blocks - 1) nbc
+// rows).  K chunks of the block of n outputs starting at row `start`: those
+// meeting its band, clipped to the 128 ext rows (outputs whose band is clipped
+// lie past tile_rows and are discarded).
+__host__ __device__ constexpr int col_chunks(int W, int start, int n) {
+  return (n + 2 * W + 15) / 16 < (kLanes - start) / 16 ? (n + 2 * W + 15) / 16 : (kLanes - start) / 16;
+}
+// The column pass's Toeplitz weights: a strip shared by all K chunks and
+// blocks when the blocks are uneven or wide (per-chunk blocks would hold kcc
+// blocks of nbc rows), one block per chunk otherwise.  Bytes of one part (sized
+// for the widest window):
+__host__ __device__ constexpr bool col_strip(int by, int nbc) { return by % nbc != 0 || nbc > 64; }
+__host__ __device__ constexpr int col_b_part(int wcap, int by, int nbc) {
+  return col_strip(by, nbc) ? (nbc + 16 * (col_chunks(wcap, 0, nbc) - 1)) * 32
+                            : ((nbc + 2 * wcap + 15) / 16) * nbc * 32;
+}
+
 struct TcLayout {
   int kcr;  // 16-wide K chunks meeting the band of one NBR-output block (row pass)
-  int kcc;  // the same for one NBC-output block (column pass)
+  int kcc;  // the same for the first NBC-output block (column pass), clipped to the 128 ext rows
   int KX;   // K extent of the row pass (ext columns, multiple of 16)
   int A1C;  // TMEM columns per (channel, part) of A1 = KX / 2
   size_t lut16_off, lutf_off, a2_off, br_off, bc_off, tile_off, raw_off, trig_off, bar_off, bytes;
@@ -122,21 +148,21 @@ constexpr int kTrigMax = 1024;
 constexpr int kBoxW = 112;  // TMA box: 112 columns (>= 15 + KX) x 128 rows of bytes
 
 // Shared memory: [lut16 (one buffer)][lutf (three buffers)][A2 hi | lo]
-// [row Toeplitz blocks][column Toeplitz blocks][tile][TMA box][trig][barriers, TMEM address, flags].
-__host__ __device__ inline TcLayout tc_layout(int W, int wcap, int nbr, int nbc) {
+// [row Toeplitz blocks][column Toeplitz strip][tile][TMA box][trig][barriers, TMEM address, flags].
+__host__ __device__ inline TcLayout tc_layout(int W, int wcap, int by, int nbr, int nbc) {
   TcLayout L;
   L.kcr = (nbr + 2 * W + 15) / 16;
-  L.kcc = (nbc + 2 * W + 15) / 16;
+  L.kcc = col_chunks(W, 0, nbc);
   L.KX = kBX - nbr + 16 * L.kcr;
   L.A1C = L.KX / 2;
-  const int kcr_max = (nbr + 2 * wcap + 15) / 16, kcc_max = (nbc + 2 * wcap + 15) / 16;
+  const int kcr_max = (nbr + 2 * wcap + 15) / 16;
   const int KXmax = kBX - nbr + 16 * kcr_max;
   L.lut16_off = 0;
   L.lutf_off = L.lut16_off + (size_t)kLutStride * sizeof(uint4);
   L.a2_off = (L.lutf_off + 3ull * kLutStride * sizeof(float2) + 1023) & ~(size_t)1023;
   L.br_off = L.a2_off + 2ull * kA2Part;
   L.bc_off = L.br_off + (size_t)kcr_max * 2 * nbr * 32;
-  L.tile_off = L.bc_off + (size_t)kcc_max * 2 * nbc * 32;  // 32-byte aligned
+  L.tile_off = L.bc_off + 2ull * col_b_part(wcap, by, nbc);  // 32-byte aligned
   const size_t tile_bytes =
       tile_row_major(wcap) ? (size_t)kLanes * tile_pitch(KXmax) * 2 : (size_t)KXmax * kPT * 2;
   L.raw_off = (L.tile_off + tile_bytes + 1023) & ~(size_t)1023;  // TMA destination
@@ -220,6 +246,29 @@ __device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
   return d;
 }
 
+// Toeplitz strip of the column pass: the K chunk i block of an output block,
+// B_i(n, k) = w[16 i + k - n], equals S(n - 16 i, k) with S(r, k) = w[k - r]
+// inside the band and 0 outside, so one strip of the NB + 16 (kc - 1) rows
+// r = -16 (kc - 1) ... NB - 1 (same K-major layout, row r at index r + 16 (kc - 1))
+// serves every chunk i < kc of every block of up to NB outputs: chunk i's
+// descriptor starts 2 (kc - 1 - i) 8-row groups in.
+// Part 0 holds the 16-bit weights, part 1 (part_bytes further) their residuals.
+template <int BF, int NB, int NT>
+__device__ __forceinline__ void build_toeplitz_strip(unsigned char *B, int kc, int part_bytes, int W, const float *w,
+                                                     int tid) {
+  const int rows = NB + 16 * (kc - 1);
+  for (int e = tid; e < rows * 16; e += NT) {
+    const int n = e >> 4, k = e & 15;  // strip row n = r + 16 (kc - 1)
+    const int t = k - (n - 16 * (kc - 1));
+    const float wv = (t >= 0 && t <= 2 * W) ? w[t] : 0.f;
+    const unsigned short hi = to16<BF>(wv);
+    const unsigned short lo = to16<BF>(wv - from16<BF>(hi));
+    const int off = (n & 7) * 16 + (n >> 3) * 256 + (k & 7) * 2 + (k >> 3) * 128;
+    *reinterpret_cast<unsigned short *>(B + off) = hi;
+    *reinterpret_cast<unsigned short *>(B + part_bytes + off) = lo;
+  }
+}
+
 // Toeplitz blocks for output blocks of NB: block i (K chunk offset i) holds
 // element (n, k) = w[16 i + k - n] inside the band and 0 outside, K-major
 // without swizzle ((n % 8) * 16 + (n / 8) * 256 + (k % 8) * 2 + (k / 8) * 128);
@@ -248,9 +297,11 @@ __device__ __forceinline__ void build_toeplitz(unsigned char *B, int nblocks, in
 template <int BF, int NSPLIT, int BY, int WCAP, int NBR, int NBC, int PIPE, int NT>
 __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant__ FilterArgs a,
                                                            const __grid_constant__ CUtensorMap tmap, int use_tma) {
-  static_assert(BY + 2 * WCAP <= kLanes && BY % 32 == 0, "halo rows must fit the TMEM lanes");
-  static_assert(kBX % NBR == 0 && BY % NBC == 0 && NBR % 16 == 0 && NBC % 16 == 0, "output blocks");
-  static_assert(BY - NBC + 16 * ((NBC + 2 * WCAP + 15) / 16) <= kLanes, "column-pass K fits A2");
+  // Computed rows: BY (multiple of 16, up to 128); the demodulation reads the
+  // centre pixels of rows W ... W + BY - 1 of the 128 staged ext rows.
+  static_assert(BY <= kLanes && BY % 16 == 0 && BY + WCAP <= kLanes, "computed rows fit the TMEM lanes");
+  static_assert(tile_rows(BY, WCAP) >= 32, "output rows per tile");
+  static_assert(kBX % NBR == 0 && NBR % 16 == 0 && NBC % 16 == 0 && NBC <= 256, "output blocks");
   static_assert(NSPLIT >= 1 && NSPLIT <= 3, "products per step");
   constexpr int kParts = NSPLIT > 1 ? 2 : 1;  // data parts held in A1 / A2 (hi, lo)
   // A1 (4 kParts regions of KX/2 columns) must fit below D1: 256 columns when
@@ -261,16 +312,24 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
   constexpr int kGroups = NT / 128;   // warp groups; h = warp / 4 in [0, kGroups)
   constexpr int BYH = BY / kGroups;   // output rows per thread in the demodulation
   constexpr int XPT = kBX / kGroups;  // outputs x per thread in the re-split
-  static_assert(BYH % 8 == 0 && XPT % 8 == 0, "TMEM loads in groups of 8 columns");
+  static_assert(BYH % 4 == 0 && XPT % 8 == 0, "TMEM loads in groups of 4 / 8 columns");
+  static_assert(4 * (BY * kBX + 8) * 4 <= 2 * kA2Part, "combine planes fit the A2 region");
+  static_assert((PIPE ? 384 : 0) + BY <= 512, "D2 fits the TMEM columns");
   constexpr int NP = NSPLIT;   // products per (chunk, output block)
   // MMAs are issued by lane 0 of several warps (a single issuing thread would
   // spend ~50 cycles per small MMA); every issuer owns whole accumulator blocks.
   constexpr int kRowIssuers = 4;                                 // one per channel
-  constexpr int kColBlocks = BY / NBC;
+  constexpr int kColBlocks = (BY + NBC - 1) / NBC;
+  constexpr int kLastN = BY - (kColBlocks - 1) * NBC;  // outputs of the last column block
+  constexpr bool kStrip = col_strip(BY, NBC);
+  static_assert(kStrip || BY - NBC + 16 * ((NBC + 2 * WCAP + 15) / 16) <= kLanes, "column-pass K fits A2");
   constexpr int kColIssuers = kColBlocks < 4 ? kColBlocks : 4;  // output blocks j = w, w + 4, ...
   extern __shared__ __align__(1024) unsigned char smem[];
   const int W = a.W;
-  const TcLayout Ly = tc_layout(W, WCAP, NBR, NBC);
+  const TcLayout Ly = tc_layout(W, WCAP, BY, NBR, NBC);
+  // output rows of a tile (all BY computed rows when every window up to WCAP allows)
+  const int BYv = BY + 2 * WCAP <= kLanes ? BY : tile_rows(BY, W);
+  constexpr int kBcPart = col_b_part(WCAP, BY, NBC);
   uint4 *lut16 = reinterpret_cast<uint4 *>(smem + Ly.lut16_off);
   float2 *lutf = reinterpret_cast<float2 *>(smem + Ly.lutf_off);
   unsigned char *A2 = smem + Ly.a2_off;
@@ -290,8 +349,8 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, cp = lane & (kCopies - 1);
   const int q = warp & 3, h = warp >> 2;  // TMEM lane quadrant, warp group
-  const int H = a.H, Wd = a.Wd, HY = BY + 2 * W, HX = kBX + 2 * W;
-  const int kcr = Ly.kcr, kcc = Ly.kcc, A1C = Ly.A1C, KX = Ly.KX;
+  const int H = a.H, Wd = a.Wd, HY = BYv + 2 * W, HX = kBX + 2 * W;
+  const int kcr = Ly.kcr, kcc = kStrip ? Ly.kcc : (NBC + 2 * W + 15) / 16, A1C = Ly.A1C, KX = Ly.KX;
   const bool reflect = a.border == FBF_BORDER_REFLECT;
   const float c0 = 0.5f * a.T;  // intensity centre
   constexpr unsigned short kScale = kCopies * sizeof(uint4), kSent = kSentinel * kCopies * sizeof(uint4);
@@ -311,7 +370,7 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
   auto issue_tma = [&](int t) {  // one thread
     const int ty = t / a.tiles_x;
     mbar_arrive_expect_tx(mbarT, (uint32_t)(kBoxW * kLanes));
-    tma_load_2d(raw, &tmap, box_x(t), ty * BY - W, mbarT);
+    tma_load_2d(raw, &tmap, box_x(t), ty * BYv - W, mbarT);
   };
 
   if (warp == 0) {
@@ -331,7 +390,10 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
   if (a.twoT <= kTrigMax)
     for (int m = tid; m < a.twoT; m += NT) sincospif((float)m / a.T, &trig[m].y, &trig[m].x);
   build_toeplitz<BF, NBR, NT>(smem + Ly.br_off, kcr, W, a.w, tid);
-  build_toeplitz<BF, NBC, NT>(smem + Ly.bc_off, kcc, W, a.w, tid);
+  if constexpr (kStrip)
+    build_toeplitz_strip<BF, NBC, NT>(smem + Ly.bc_off, kcc, kBcPart, W, a.w, tid);
+  else
+    build_toeplitz<BF, NBC, NT>(smem + Ly.bc_off, kcc, W, a.w, tid);
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
@@ -343,6 +405,7 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
   const uint32_t kA1 = 0, kD1 = PIPE ? 256 : 384, kD2 = PIPE ? 384 : 0;
   constexpr uint32_t idesc_row = idesc_f16(128, NBR, BF, 0, 0);
   constexpr uint32_t idesc_col = idesc_f16(128, NBC, BF, 1, 0);
+  constexpr uint32_t idesc_col_last = idesc_f16(128, kLastN, BF, 1, 0);
   // Descriptor bases; offsets below 256 KB are added to the low address field.
   const uint64_t br_desc = smem_desc(smem_u32(smem + Ly.br_off), 128, 256);
   const uint64_t bc_desc = smem_desc(smem_u32(smem + Ly.bc_off), 128, 256);
@@ -467,18 +530,24 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
   auto issue_col = [&]() {
     fence_after_sync();
 #pragma unroll 1
-    for (int j = warp; j < kColBlocks; j += kColIssuers)
+    for (int j = warp; j < kColBlocks; j += kColIssuers) {
+      const bool last = j == kColBlocks - 1;
+      // K chunks of block j (the strip's kcc bounds them all)
+      const int kj = kStrip ? col_chunks(W, j * NBC, last ? kLastN : NBC) : kcc;
+      const uint32_t idesc = last ? idesc_col_last : idesc_col;
 #pragma unroll 1
-      for (int i = 0; i < kcc; ++i)
+      for (int i = 0; i < kj; ++i)
 #pragma unroll
         for (int pp = 0; pp < NP; ++pp) {
           const int ap = pp == 1 ? 1 : 0;
           const int bp = pp == 2 ? 1 : 0;
-          const uint64_t bd = bc_desc + (uint64_t)(((2 * i + bp) * NBC * 32) >> 4);
+          const uint64_t bd =
+              bc_desc + (uint64_t)((kStrip ? bp * kBcPart + 2 * (kcc - 1 - i) * 256 : (2 * i + bp) * NBC * 32) >> 4);
           const uint32_t ao = (uint32_t)(ap * kA2Part + (j * NBC / 16 + i) * 2 * kA2Group);
-          mma_ss(tmem + kD2 + (uint32_t)(j * NBC), a2_desc + (uint64_t)(ao >> 4), bd, idesc_col,
+          mma_ss(tmem + kD2 + (uint32_t)(j * NBC), a2_desc + (uint64_t)(ao >> 4), bd, idesc,
                  (i > 0 || pp > 0) ? 1u : 0u);
         }
+    }
     mma_commit(mbarC);
   };
 
@@ -488,7 +557,7 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
     const int c = lane & 3;
     const float dn = a.d[n];
     const char *Lf = reinterpret_cast<const char *>(lutf + (n % 3) * kLutStride + ((lane >> 2) & (kCopies - 1)));
-    constexpr int DG = BYH % 16 == 0 ? 16 : 8;  // columns per TMEM load
+    constexpr int DG = BYH % 16 == 0 ? 16 : (BYH % 8 == 0 ? 8 : 4);  // columns per TMEM load
     uint32_t v[BYH / DG][DG];
 #pragma unroll
     for (int g = 0; g < BYH / DG; ++g) tmem_ld(tmem + lane_base + kD2 + (uint32_t)(h * BYH + DG * g), v[g]);
@@ -523,7 +592,7 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
 
   for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
     const int tile_y = tile / a.tiles_x, tile_x = tile - tile_y * a.tiles_x;
-    const int ty0 = tile_y * BY, tx0 = tile_x * kBX;
+    const int ty0 = tile_y * BYv, tx0 = tile_x * kBX;
 
     // ---- stage this tile: 128 ext rows x KX ext columns of byte offsets v * 128.
     if (tma_tile(tile)) {
@@ -640,7 +709,7 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
 #pragma unroll
       for (int j = 0; j < BYH; ++j) comb[c * kCS + (h * BYH + j) * kBX + x] = part[j];
       __syncthreads();
-      for (int e = tid; e < BY * kBX; e += NT) {
+      for (int e = tid; e < BYv * kBX; e += NT) {
         const int y = e / kBX, xx = e - y * kBX;
         const int iy = ty0 + y, ix = tx0 + xx;
         if (iy < H && ix < Wd) {
@@ -667,14 +736,17 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
 #ifndef FBF_TC_NBR
 #define FBF_TC_NBR 32
 #endif
-#ifndef FBF_TC_NBC_96
-#define FBF_TC_NBC_96 48
+#ifndef FBF_TC_BY_16
+#define FBF_TC_BY_16 112  // computed rows per tile, windows up to 16 (output rows min(112, 128 - 2W))
+#endif
+#ifndef FBF_TC_NBC_16
+#define FBF_TC_NBC_16 112  // one column block (fewer, larger MMAs ran faster than 48 + 48 + 16)
 #endif
 #ifndef FBF_TC_NBC_64
 #define FBF_TC_NBC_64 32
 #endif
-#ifndef FBF_TC_NT_96
-#define FBF_TC_NT_96 512  // threads per CTA, 96-row tiles
+#ifndef FBF_TC_NT_16
+#define FBF_TC_NT_16 512  // threads per CTA, windows up to 16
 #endif
 #ifndef FBF_TC_NT_64
 #define FBF_TC_NT_64 512  // threads per CTA, 64-row tiles
@@ -719,9 +791,10 @@ bool make_box_map(const FilterArgs &a, CUtensorMap *map) {
 template <int BF, int NSPLIT, int BY, int WCAP, int NBR, int NBC, int PIPE, int NT>
 fbf_status launch_tc_cfg(const FilterArgs &a0, cudaStream_t s) {
   FilterArgs a = a0;
-  const TcLayout Ly = tc_layout(a.W, WCAP, NBR, NBC);
+  const TcLayout Ly = tc_layout(a.W, WCAP, BY, NBR, NBC);
   a.tiles_x = (a.Wd + kBX - 1) / kBX;
-  const int tiles_y = (a.H + BY - 1) / BY;
+  const int by = tile_rows(BY, a.W);
+  const int tiles_y = (a.H + by - 1) / by;
   a.ntiles = a.tiles_x * tiles_y;
   CUtensorMap map;
   const int use_tma = make_box_map(a, &map) ? 1 : 0;
@@ -744,10 +817,11 @@ fbf_status launch_tc_cfg(const FilterArgs &a0, cudaStream_t s) {
 // the 64-row tiles run the pipelined schedule too).
 fbf_status launch_tc_u8(const FilterArgs &a, int mode, cudaStream_t s) {
   if (mode < 0 || mode > 2) return FBF_ERR_INVALID_ARGUMENT;
+  constexpr int BY16 = FBF_TC_BY_16, NBC16 = FBF_TC_NBC_16, NT16 = FBF_TC_NT_16;
   if (a.W <= 16) {
-    if (mode == 1) return launch_tc_cfg<1, 3, 96, 16, FBF_TC_NBR, FBF_TC_NBC_96, FBF_TC_PIPE, FBF_TC_NT_96>(a, s);
-    if (mode == 2) return launch_tc_cfg<0, 1, 96, 16, FBF_TC_NBR, FBF_TC_NBC_96, FBF_TC_PIPE, FBF_TC_NT_96>(a, s);
-    return launch_tc_cfg<0, 2, 96, 16, FBF_TC_NBR, FBF_TC_NBC_96, FBF_TC_PIPE, FBF_TC_NT_96>(a, s);
+    if (mode == 1) return launch_tc_cfg<1, 3, BY16, 16, FBF_TC_NBR, NBC16, FBF_TC_PIPE, NT16>(a, s);
+    if (mode == 2) return launch_tc_cfg<0, 1, BY16, 16, FBF_TC_NBR, NBC16, FBF_TC_PIPE, NT16>(a, s);
+    return launch_tc_cfg<0, 2, BY16, 16, FBF_TC_NBR, NBC16, FBF_TC_PIPE, NT16>(a, s);
   }
   if (a.W <= 32) {
     if (mode == 1) return launch_tc_cfg<1, 3, 64, 32, FBF_TC_NBR, FBF_TC_NBC_64, 0, FBF_TC_NT_64>(a, s);

@@ -114,6 +114,21 @@ def test_every_window_tail(fbf, W, form):
         _check(got, _oracle_full(img, c, ss, W if W > 0 else 1, spatial, "reflect"), TOL[form])
 
 
+@pytest.mark.parametrize("form", ["tc_fp16", "tc_bf16", "tc_fp16_single"])
+@pytest.mark.parametrize("W", [1, 8, 9, 12, 15, 16, 17, 30])
+def test_tensor_core_tile_row_edges(fbf, W, form):
+    """Heights at and across the tensor-core tiles' row count, min(112,
+    128 - 2W) for W <= 16 (rows computed past it are discarded) and 64 above,
+    under both borders."""
+    rows = min(112, 128 - 2 * W) if W <= 16 else 64
+    c = fbf.fbf_fit_coeffs("gaussian", 30.0, 255.0, 1e-3)
+    for H in (rows, rows + 1, 2 * rows - 1, 2 * rows + 3):
+        img = make_image(H, 70, seed=H + W)
+        for border in ("reflect", "truncate"):
+            got = _gpu(fbf, img, c, W / 3.0, W=W, spatial="box", border=border, form=form)
+            _check(got, _oracle_full(img, c, W / 3.0, W, "box", border), TOL[form])
+
+
 @pytest.mark.parametrize("form", FORMS)
 def test_orders_from_one_to_255(fbf, form):
     img = make_image(80, 90, seed=3)
