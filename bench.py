@@ -216,14 +216,20 @@ TC_NSPLIT = {"tc_fp16": 2, "tc_bf16": 3, "tc_fp16_single": 1}
 def tc_issued_flops(K: int, W: int, form: str) -> float:
     """Dense MMA flops the tensor-core kernel issues for one 2048x2048 launch,
     band padding and split products included (mirrors its tiling: tiles of 32
-    columns x min(BY, 128 - 2W) output rows, BY = 112 computed rows for W <= 16
-    else 64; per harmonic and tile, the row pass issues 4 channels x
+    columns x min(BY, 128 - 2W) output rows, BY = 112 computed rows for W <= 16,
+    96 for W <= 26, else 64; per harmonic and tile, the row pass issues 4 channels x
     ceil((32 + 2W) / 16) K-chunks of M = 128, N = 32, K = 16; the column pass
-    output blocks of NBC rows (one of 112 for BY = 112; 32 and 32 for BY = 64),
-    each with the K chunks meeting its band inside the 128 ext rows, of N = its
-    rows; each chunk once per split product)."""
+    output blocks of NBC rows (one of BY for BY = 112 and 96; for BY = 64 one
+    of 64 in the single form, 32 and 32 in the split forms), each with the K chunks
+    meeting its band inside the 128 ext rows, of N = its rows; each chunk once
+    per split product)."""
     nsplit = TC_NSPLIT[form]
-    BY, NBC = (112, 112) if W <= 16 else (64, 32)
+    if W <= 16:
+        BY, NBC = 112, 112
+    elif W <= 26:
+        BY, NBC = 96, 96
+    else:
+        BY, NBC = 64, 64 if nsplit == 1 else 32
     rows = min(BY, 128 - 2 * W)
     kcr = (32 + 2 * W + 15) // 16
     tiles = math.ceil(W_IMG / 32) * math.ceil(H / rows)

@@ -70,9 +70,9 @@ typedef enum { FBF_U8 = 0, FBF_F32 = 1 } fbf_dtype;
  * Algorithm 1 stays near 0.02-0.05 gray level for sigma_r >= 20 and grows as
  * sigma_r shrinks (about 0.1 at sigma_r = 5), where the split forms stay below
  * 2e-3.  AUTO: the faster of FP32 and TC_FP16 for the window, as measured on
- * GB300 (TC_FP16 for Gaussian windows from W = 6 up; for the box kernel, which
- * the FP32 form runs as running window sums, TC_FP16 for W = 8..16 and from
- * W = 23 up); AUTO never picks TC_FP16_SINGLE. */
+ * GB300 (TC_FP16 from W = 4 up, for the Gaussian and the box kernel alike;
+ * FP32, which runs the box kernel as running window sums, below); AUTO never
+ * picks TC_FP16_SINGLE. */
 typedef enum {
   FBF_FORM_AUTO = 0,
   FBF_FORM_FP32 = 1,

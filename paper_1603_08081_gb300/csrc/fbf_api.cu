@@ -89,16 +89,14 @@ fbf_status launch_filter(const FilterArgs &a, fbf_form form, fbf_dtype dtype, cu
 }
 
 // AUTO: the faster of the FP32 and split tensor-core FP16 forms for the window,
-// from a sweep on GB300 (2048^2 u8, K = 17, ms FP32 / TC): Gaussian W = 5
-// 0.449 / 0.464, W = 6 0.483 / 0.464, W = 9 0.595 / 0.501, W = 30 1.50 / 0.94;
-// box (FP32 as running sums) W = 7 0.452 / 0.464, W = 8 0.488 / 0.464, W = 16
-// 0.662 / 0.499, W = 17 0.726 / 0.853, W = 22 ~0.85 / 0.854, W = 24 0.893 /
-// 0.854.  The tensor-core cost steps at W = 17 (64-row tiles), the FP32 cost
-// grows with the taps (slowly for the box sums).
-bool auto_picks_tc(const FilterArgs &a) {
-  if (!a.box) return a.W >= 6;
-  return (a.W >= 8 && a.W <= 16) || a.W >= 23;
-}
+// from a sweep on GB300 (2048^2 u8, K = 17, ms FP32 / TC): Gaussian W = 3
+// 0.363 / 0.379, W = 4 0.391 / 0.379, W = 9 0.580 / 0.412, W = 17 0.942 /
+// 0.600, W = 30 1.49 / 0.82; box (FP32 as running sums) W = 3 0.344 / 0.378,
+// W = 4 0.385 / 0.379, W = 16 0.645 / 0.512, W = 17 0.700 / 0.600, W = 26
+// 0.911 / 0.754.  The tensor-core cost steps with the row pass's K chunks and
+// with the tile rows (112 computed for W <= 16, 96 for W <= 26, 64 above); the
+// FP32 cost grows with the taps (slowly for the box sums).
+bool auto_picks_tc(const FilterArgs &a) { return a.W >= 4; }
 
 }  // namespace fbf
 

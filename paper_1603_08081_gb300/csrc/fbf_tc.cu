@@ -6,8 +6,8 @@
 // One CTA (512 threads: four groups of four warps, warp w reaching TMEM lanes
 // 32 (w % 4) ... + 31) owns a tile of 32 output columns and min(BY, 128 - 2W)
 // output rows, whose halo rows fill at most the 128 TMEM lanes (BY = 112
-// computed rows for W <= 16, 64 for W <= 32; rows computed past 128 - 2W have
-// a clipped band and are discarded).  Taller tiles mean fewer tiles: a 2048^2
+// computed rows for W <= 16, 96 for W <= 26, 64 for W <= 32; rows computed
+// past 128 - 2W have a clipped band and are discarded).  Taller tiles mean fewer tiles: a 2048^2
 // image at W = 9 is 19 x 64 tiles of 110 rows, 8 waves of 152 CTAs, where
 // 96-row tiles took 10.  For each harmonic n:
 //
@@ -28,8 +28,9 @@
 //             of the column pass, A2[m = 4 x + c][K = ext row] -- each thread
 //             writes its own row, so no transpose is needed;
 //   col MMA   D2 (lane m = 4 x + c, columns = output rows y) = sum A2 * T_i,
-//             in one output block of 112 rows (BY = 112; its Toeplitz blocks
-//             are windows of one shared strip) or two of 32 (BY = 64);
+//             in one output block of BY rows (BY = 112, 96) or, for BY = 64,
+//             one of 64 (single form) or two of 32 (split forms); wide
+//             blocks take their Toeplitz blocks as windows of one shared strip;
 //   demod     lane (c, x) accumulates d_n * trig(n w f(y, x)) * D2 into its
 //             own partial: cos for the G_r / F_r channels, sin for G_i / F_i.
 //
@@ -114,19 +115,19 @@ constexpr uint32_t kMaxPolls = 1u << 22;
 // Output rows of one tile: the BY computed rows, at most the kLanes - 2W rows
 // whose 2W + 1 taps all lie in the 128 ext rows (the rows past that are
 // computed with a truncated band and discarded).
-__host__ __device__ constexpr int tile_rows(int by, int W) { return by < kLanes - 2 * W ? by : kLanes - 2 * W; }
+__host__ __device__ __forceinline__ constexpr int tile_rows(int by, int W) { return by < kLanes - 2 * W ? by : kLanes - 2 * W; }
 // Column pass: output blocks of nbc rows (the last one by - (blocks - 1) nbc
 // rows).  K chunks of the block of n outputs starting at row `start`: those
 // meeting its band, clipped to the 128 ext rows (outputs whose band is clipped
 // lie past tile_rows and are discarded).
-__host__ __device__ constexpr int col_chunks(int W, int start, int n) {
+__host__ __device__ __forceinline__ constexpr int col_chunks(int W, int start, int n) {
   return (n + 2 * W + 15) / 16 < (kLanes - start) / 16 ? (n + 2 * W + 15) / 16 : (kLanes - start) / 16;
 }
 // The column pass's Toeplitz weights: a strip shared by all K chunks and
 // blocks when the blocks are uneven or wide (per-chunk blocks would hold kcc
 // blocks of nbc rows), one block per chunk otherwise.  Bytes of one part (sized
 // for the widest window):
-__host__ __device__ constexpr bool col_strip(int by, int nbc) { return by % nbc != 0 || nbc > 64; }
+__host__ __device__ constexpr bool col_strip(int by, int nbc) { return by % nbc != 0 || nbc >= 64; }
 __host__ __device__ constexpr int col_b_part(int wcap, int by, int nbc) {
   return col_strip(by, nbc) ? (nbc + 16 * (col_chunks(wcap, 0, nbc) - 1)) * 32
                             : ((nbc + 2 * wcap + 15) / 16) * nbc * 32;
@@ -149,7 +150,7 @@ constexpr int kBoxW = 112;  // TMA box: 112 columns (>= 15 + KX) x 128 rows of b
 
 // Shared memory: [lut16 (one buffer)][lutf (three buffers)][A2 hi | lo]
 // [row Toeplitz blocks][column Toeplitz strip][tile][TMA box][trig][barriers, TMEM address, flags].
-__host__ __device__ inline TcLayout tc_layout(int W, int wcap, int by, int nbr, int nbc) {
+__host__ __device__ __forceinline__ TcLayout tc_layout(int W, int wcap, int by, int nbr, int nbc) {
   TcLayout L;
   L.kcr = (nbr + 2 * W + 15) / 16;
   L.kcc = col_chunks(W, 0, nbc);
@@ -533,7 +534,7 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
     for (int j = warp; j < kColBlocks; j += kColIssuers) {
       const bool last = j == kColBlocks - 1;
       // K chunks of block j (the strip's kcc bounds them all)
-      const int kj = kStrip ? col_chunks(W, j * NBC, last ? kLastN : NBC) : kcc;
+      const int kj = kStrip && kColBlocks > 1 ? col_chunks(W, j * NBC, last ? kLastN : NBC) : kcc;
       const uint32_t idesc = last ? idesc_col_last : idesc_col;
 #pragma unroll 1
       for (int i = 0; i < kj; ++i)
@@ -743,13 +744,19 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
 #define FBF_TC_NBC_16 112  // one column block (fewer, larger MMAs ran faster than 48 + 48 + 16)
 #endif
 #ifndef FBF_TC_NBC_64
-#define FBF_TC_NBC_64 32
+#define FBF_TC_NBC_64 32  // split forms, 64-row tiles (a single 64-row block spilled registers there)
+#endif
+#ifndef FBF_TC_NBC_64_SINGLE
+#define FBF_TC_NBC_64_SINGLE 64  // single FP16 form, 64-row tiles: one column block
 #endif
 #ifndef FBF_TC_NT_16
 #define FBF_TC_NT_16 512  // threads per CTA, windows up to 16
 #endif
 #ifndef FBF_TC_NT_64
 #define FBF_TC_NT_64 512  // threads per CTA, 64-row tiles
+#endif
+#ifndef FBF_TC_WMAX_96
+#define FBF_TC_WMAX_96 26  // windows 17 .. this: 96 computed rows (output rows 128 - 2W), one column block
 #endif
 #ifndef FBF_TC_PIPE
 #define FBF_TC_PIPE 1  // W <= 16: pipelined schedule (A1, D1, D2 disjoint in TMEM)
@@ -823,9 +830,14 @@ fbf_status launch_tc_u8(const FilterArgs &a, int mode, cudaStream_t s) {
     if (mode == 2) return launch_tc_cfg<0, 1, BY16, 16, FBF_TC_NBR, NBC16, FBF_TC_PIPE, NT16>(a, s);
     return launch_tc_cfg<0, 2, BY16, 16, FBF_TC_NBR, NBC16, FBF_TC_PIPE, NT16>(a, s);
   }
+  if (a.W <= FBF_TC_WMAX_96) {
+    if (mode == 1) return launch_tc_cfg<1, 3, 96, 32, FBF_TC_NBR, 96, 0, FBF_TC_NT_64>(a, s);
+    if (mode == 2) return launch_tc_cfg<0, 1, 96, 32, FBF_TC_NBR, 96, 1, FBF_TC_NT_64>(a, s);
+    return launch_tc_cfg<0, 2, 96, 32, FBF_TC_NBR, 96, 0, FBF_TC_NT_64>(a, s);
+  }
   if (a.W <= 32) {
     if (mode == 1) return launch_tc_cfg<1, 3, 64, 32, FBF_TC_NBR, FBF_TC_NBC_64, 0, FBF_TC_NT_64>(a, s);
-    if (mode == 2) return launch_tc_cfg<0, 1, 64, 32, FBF_TC_NBR, FBF_TC_NBC_64, 1, FBF_TC_NT_64>(a, s);
+    if (mode == 2) return launch_tc_cfg<0, 1, 64, 32, FBF_TC_NBR, FBF_TC_NBC_64_SINGLE, 1, FBF_TC_NT_64>(a, s);
     return launch_tc_cfg<0, 2, 64, 32, FBF_TC_NBR, FBF_TC_NBC_64, 0, FBF_TC_NT_64>(a, s);
   }
   return FBF_ERR_RANGE;

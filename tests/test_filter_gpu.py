@@ -115,12 +115,12 @@ def test_every_window_tail(fbf, W, form):
 
 
 @pytest.mark.parametrize("form", ["tc_fp16", "tc_bf16", "tc_fp16_single"])
-@pytest.mark.parametrize("W", [1, 8, 9, 12, 15, 16, 17, 30])
+@pytest.mark.parametrize("W", [1, 8, 9, 12, 15, 16, 17, 20, 26, 27, 30])
 def test_tensor_core_tile_row_edges(fbf, W, form):
-    """Heights at and across the tensor-core tiles' row count, min(112,
-    128 - 2W) for W <= 16 (rows computed past it are discarded) and 64 above,
-    under both borders."""
-    rows = min(112, 128 - 2 * W) if W <= 16 else 64
+    """Heights at and across the tensor-core tiles' row count, min(BY, 128 - 2W)
+    with BY = 112 computed rows for W <= 16, 96 for W <= 26 (rows computed past
+    128 - 2W are discarded) and 64 above, under both borders."""
+    rows = min(112, 128 - 2 * W) if W <= 16 else (128 - 2 * W if W <= 26 else 64)
     c = fbf.fbf_fit_coeffs("gaussian", 30.0, 255.0, 1e-3)
     for H in (rows, rows + 1, 2 * rows - 1, 2 * rows + 3):
         img = make_image(H, 70, seed=H + W)
@@ -237,10 +237,11 @@ def test_box_4096_exponential_sampled(fbf, border):
         _check(got[ys, xs], ref, TOL[form])
 
 
-@pytest.mark.parametrize("spatial,W,expect", [("gaussian", 3, "fp32"), ("gaussian", 5, "fp32"),
+@pytest.mark.parametrize("spatial,W,expect", [("gaussian", 3, "fp32"), ("gaussian", 4, "tc_fp16"),
                                               ("gaussian", 6, "tc_fp16"), ("gaussian", 30, "tc_fp16"),
-                                              ("box", 4, "fp32"), ("box", 10, "tc_fp16"),
-                                              ("box", 20, "fp32"), ("box", 24, "tc_fp16")])
+                                              ("box", 3, "fp32"), ("box", 4, "tc_fp16"),
+                                              ("box", 10, "tc_fp16"), ("box", 17, "tc_fp16"),
+                                              ("box", 26, "tc_fp16"), ("box", 30, "tc_fp16")])
 def test_auto_form_picks_the_documented_kernel(fbf, spatial, W, expect):
     """AUTO runs exactly the kernel of the form its rule names (bit-identical output)."""
     img = make_image(150, 170, seed=W)
