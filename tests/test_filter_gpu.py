@@ -95,7 +95,7 @@ def test_ragged_and_tiny_images(fbf, shape, border, form):
     """Sizes off the tile grid, single rows/columns, windows wider than the image."""
     img = make_image(*shape, seed=17)
     c = fbf.fbf_fit_coeffs("gaussian", 20.0, 255.0, 1e-3)
-    for sigma_s in (3.0, 7.0):  # W = 9 (64x64 tiles) and W = 21 (32x128 tiles)
+    for sigma_s in (3.0, 7.0):  # W = 9 and W = 21: the small- and wide-window tiles of each form
         W = int(np.ceil(3 * sigma_s))
         got = _gpu(fbf, img, c, sigma_s, border=border, form=form)
         _check(got, _oracle_full(img, c, sigma_s, W, "gaussian", border), TOL[form])
