@@ -7,9 +7,9 @@
 // 32 (w % 4) ... + 31) owns a tile of 32 output columns and min(BY, 128 - 2W)
 // output rows, whose halo rows fill at most the 128 TMEM lanes (BY = 112
 // computed rows for W <= 16, 96 for W <= 26, 64 for W <= 32; rows computed
-// past 128 - 2W have a clipped band and are discarded).  Taller tiles mean fewer tiles: a 2048^2
-// image at W = 9 is 19 x 64 tiles of 110 rows, 8 waves of 152 CTAs, where
-// 96-row tiles took 10.  For each harmonic n:
+// past 128 - 2W have a clipped band and are discarded).  Taller tiles mean
+// fewer tiles: a 2048^2 image at W = 9 is 19 x 64 tiles of 110 rows, 8 waves
+// of 152 CTAs, where 96-row tiles took 10.  For each harmonic n:
 //
 //   modulate  thread (lane r, group h) gathers, for ext row r and its share
 //             of the ext columns, the per-harmonic table entry of each pixel
