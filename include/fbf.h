@@ -182,7 +182,9 @@ typedef enum {
   FBF_SCHEDULE_PERSISTENT = 0,      /* one persistent FP32 launch, 32 x 192 tiles     */
   FBF_SCHEDULE_PERSISTENT_WIDE = 1, /* one persistent FP32 launch, 64 x 96 tiles      */
   FBF_SCHEDULE_PER_IMAGE_FP32 = 2,  /* one single-image FP32 launch per image         */
-  FBF_SCHEDULE_PER_IMAGE_FORM = 3   /* one launch per image in the plan's form        */
+  FBF_SCHEDULE_PER_IMAGE_FORM = 3,  /* one launch per image in the plan's form        */
+  FBF_SCHEDULE_PER_IMAGE_FP32_STREAMS = 4, /* PER_IMAGE_FP32 on 4 concurrent branches */
+  FBF_SCHEDULE_PER_IMAGE_FORM_STREAMS = 5  /* PER_IMAGE_FORM on 4 concurrent branches */
 } fbf_schedule;
 
 /*
@@ -191,9 +193,15 @@ typedef enum {
  * Candidate schedules: PERSISTENT (one CTA per SM pulling cost-sorted (image,
  * tile) items from a counter; FP32 tile body with run-time taps), its 64 x 96
  * tile variant PERSISTENT_WIDE (when every W <= 16), PER_IMAGE_FP32 (the
- * single-image FP32 kernels, one launch each) and PER_IMAGE_FORM (one
- * launch per image in `form`).  form FP32: the first three; AUTO: all four
- * (per image as fbf_filter's AUTO); a tensor-core form: PER_IMAGE_FORM only.
+ * single-image FP32 kernels, one launch each), PER_IMAGE_FORM (one launch
+ * per image in `form`) and the two per-image schedules with their launches
+ * spread over four concurrent graph branches (largest images first, each to
+ * the least loaded branch), so that small images and the last wave of one
+ * image's tiles share the GPU with other images.  form FP32: PERSISTENT,
+ * PERSISTENT_WIDE and both PER_IMAGE_FP32 schedules; AUTO: all six (per image
+ * as fbf_filter's AUTO); a tensor-core form: both PER_IMAGE_FORM schedules.
+ * The concurrent schedules need images whose outputs overlap no other
+ * image's output or input.
  * With more than one candidate the plan autotunes: it replays every
  * candidate on the given images -- writing their outputs -- times each with
  * CUDA events and keeps the fastest (fbf_plan_schedule reports which); this
@@ -204,6 +212,11 @@ typedef enum {
  */
 fbf_status fbf_plan_create(const fbf_image_desc *descs, int n, fbf_form form, fbf_border border,
                            fbf_plan **out);
+/* As fbf_plan_create, but captures the one given schedule without autotuning
+ * (no replay at creation).  FBF_ERR_INVALID_ARGUMENT when `schedule` is not a
+ * candidate of `form` (or out of range). */
+fbf_status fbf_plan_create_schedule(const fbf_image_desc *descs, int n, fbf_form form, fbf_border border,
+                                    fbf_schedule schedule, fbf_plan **out);
 /* Filter every image of the plan: one cudaGraphLaunch on `stream`. */
 fbf_status fbf_filter_batched(fbf_plan *plan, cudaStream_t stream);
 /* Release the plan (the caller synchronises first if a launch is in flight). */

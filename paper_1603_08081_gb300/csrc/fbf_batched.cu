@@ -195,30 +195,73 @@ fbf_status capture_persistent(int device, int border, Candidate *c, cudaStream_t
   return cudaGraphInstantiate(&c->exec, c->graph, 0) == cudaSuccess ? FBF_OK : FBF_ERR_CUDA;
 }
 
-// Capture of one single-image launch per image in `form`.  Every launch runs
-// once before the capture, so that the kernels' one-time host set-up
-// (function attributes, driver entry points) happens outside it.
-fbf_status capture_per_image(const std::vector<FilterArgs> &args, fbf_form form, Candidate *c, cudaStream_t cs) {
+// Capture of one single-image launch per image in `form`, in image order on
+// one branch (nbranch = 1) or spread over nbranch concurrent branches of the
+// graph: images by decreasing cost (pixels x harmonics), each to the branch
+// with the least cost so far; the branches fork from and join the capturing
+// stream.  Every launch runs once before the capture, so that the kernels'
+// one-time host set-up (function attributes, driver entry points) happens
+// outside it.
+fbf_status capture_per_image(const std::vector<FilterArgs> &args, fbf_form form, int nbranch, Candidate *c,
+                             cudaStream_t cs) {
   for (const FilterArgs &a : args) {
     if (a.H == 0 || a.Wd == 0) continue;
     const fbf_status st = launch_filter(a, form, FBF_U8, cs);
     if (st != FBF_OK) return st;
   }
   if (cudaStreamSynchronize(cs) != cudaSuccess) return FBF_ERR_CUDA;
-  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return FBF_ERR_CUDA;
-  fbf_status st = FBF_OK;
-  for (const FilterArgs &a : args) {
-    if (a.H == 0 || a.Wd == 0) continue;
-    st = launch_filter(a, form, FBF_U8, cs);
-    if (st != FBF_OK) break;
+  std::vector<int> order;
+  for (int i = 0; i < (int)args.size(); ++i)
+    if (args[i].H > 0 && args[i].Wd > 0) order.push_back(i);
+  auto cost = [&](int i) { return (double)args[i].H * args[i].Wd * args[i].K; };
+  if (nbranch > 1) std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return cost(x) > cost(y); });
+  // side[b - 1] is branch b; branch 0 is the capturing stream; ev[0] forks, ev[b] joins branch b
+  std::vector<cudaStream_t> side(nbranch > 1 ? nbranch - 1 : 0, nullptr);
+  std::vector<cudaEvent_t> ev(side.size() + 1, nullptr);
+  bool ok = true;
+  for (auto &s : side) ok = ok && cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess;
+  for (auto &e : ev) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+  fbf_status st = ok ? FBF_OK : FBF_ERR_CUDA;
+  bool capturing = false;
+  if (st == FBF_OK) {
+    capturing = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+    if (!capturing) st = FBF_ERR_CUDA;
   }
+  bool forked = false;
+  if (st == FBF_OK && !side.empty()) {
+    forked = cudaEventRecord(ev[0], cs) == cudaSuccess;
+    for (auto &s : side) forked = forked && cudaStreamWaitEvent(s, ev[0], 0) == cudaSuccess;
+    if (!forked) st = FBF_ERR_CUDA;
+  }
+  std::vector<double> load(side.size() + 1, 0.0);
+  for (size_t k = 0; k < order.size() && st == FBF_OK; ++k) {
+    const int i = order[k];
+    size_t b = 0;
+    for (size_t j = 1; j < load.size(); ++j)
+      if (load[j] < load[b]) b = j;
+    load[b] += cost(i);
+    st = launch_filter(args[i], form, FBF_U8, b == 0 ? cs : side[b - 1]);
+  }
+  if (forked)  // every branch rejoins the capturing stream, also after a failed launch
+    for (size_t b = 1; b < ev.size(); ++b)
+      if (cudaEventRecord(ev[b], side[b - 1]) != cudaSuccess || cudaStreamWaitEvent(cs, ev[b], 0) != cudaSuccess)
+        st = FBF_ERR_CUDA;
   cudaGraph_t g = nullptr;
-  const bool ended = cudaStreamEndCapture(cs, &g) == cudaSuccess;
+  const bool ended = capturing && cudaStreamEndCapture(cs, &g) == cudaSuccess;
   c->graph = g;
+  for (auto &e : ev)
+    if (e) cudaEventDestroy(e);
+  for (auto &s : side)
+    if (s) cudaStreamDestroy(s);
   if (st != FBF_OK) return st;
   if (!ended || !g) return FBF_ERR_CUDA;
   return cudaGraphInstantiate(&c->exec, c->graph, 0) == cudaSuccess ? FBF_OK : FBF_ERR_CUDA;
 }
+
+#ifndef FBF_PLAN_BRANCHES
+#define FBF_PLAN_BRANCHES 4
+#endif
+constexpr int kPlanBranches = FBF_PLAN_BRANCHES;  // concurrent branches of the *_STREAMS schedules
 
 // Mean time of three replays of a candidate's graph (after one untimed replay).
 fbf_status time_candidate(Candidate *c, cudaStream_t cs) {
@@ -248,8 +291,10 @@ static void plan_free(fbf_plan *p) {
   delete p;
 }
 
-extern "C" fbf_status fbf_plan_create(const fbf_image_desc *descs, int n, fbf_form form, fbf_border border,
-                                      fbf_plan **out) {
+// Plan creation: `only` < 0 autotunes over the form's candidate schedules,
+// otherwise captures that one schedule (which must be a candidate of the form).
+static fbf_status plan_create(const fbf_image_desc *descs, int n, fbf_form form, fbf_border border, int only,
+                              fbf_plan **out) {
   if (!out) return FBF_ERR_INVALID_ARGUMENT;
   *out = nullptr;
   if (n < 0 || (n > 0 && !descs)) return FBF_ERR_INVALID_ARGUMENT;
@@ -296,11 +341,25 @@ extern "C" fbf_status fbf_plan_create(const fbf_image_desc *descs, int n, fbf_fo
   std::vector<fbf_schedule> kinds;
   if (tc) {
     kinds.push_back(FBF_SCHEDULE_PER_IMAGE_FORM);
+    kinds.push_back(FBF_SCHEDULE_PER_IMAGE_FORM_STREAMS);
   } else {
     kinds.push_back(FBF_SCHEDULE_PERSISTENT);
     if (wmax <= 16) kinds.push_back(FBF_SCHEDULE_PERSISTENT_WIDE);
     kinds.push_back(FBF_SCHEDULE_PER_IMAGE_FP32);
-    if (form == FBF_FORM_AUTO) kinds.push_back(FBF_SCHEDULE_PER_IMAGE_FORM);
+    kinds.push_back(FBF_SCHEDULE_PER_IMAGE_FP32_STREAMS);
+    if (form == FBF_FORM_AUTO) {
+      kinds.push_back(FBF_SCHEDULE_PER_IMAGE_FORM);
+      kinds.push_back(FBF_SCHEDULE_PER_IMAGE_FORM_STREAMS);
+    }
+  }
+
+  if (only >= 0) {
+    if (std::find(kinds.begin(), kinds.end(), (fbf_schedule)only) == kinds.end()) {
+      cudaStreamDestroy(cs);
+      plan_free(p);
+      return FBF_ERR_INVALID_ARGUMENT;
+    }
+    kinds.assign(1, (fbf_schedule)only);
   }
 
   fbf_status st = FBF_OK;
@@ -315,7 +374,9 @@ extern "C" fbf_status fbf_plan_create(const fbf_image_desc *descs, int n, fbf_fo
       st = build_persistent<64, 96>(args, &c.tables);
       if (st == FBF_OK) st = capture_persistent<64, 96, 1, 16>(p->device, (int)border, &c, cs);
     } else {
-      st = capture_per_image(args, k == FBF_SCHEDULE_PER_IMAGE_FP32 ? FBF_FORM_FP32 : form, &c, cs);
+      const bool fp32 = k == FBF_SCHEDULE_PER_IMAGE_FP32 || k == FBF_SCHEDULE_PER_IMAGE_FP32_STREAMS;
+      const bool streams = k == FBF_SCHEDULE_PER_IMAGE_FP32_STREAMS || k == FBF_SCHEDULE_PER_IMAGE_FORM_STREAMS;
+      st = capture_per_image(args, fp32 ? FBF_FORM_FP32 : form, streams ? kPlanBranches : 1, &c, cs);
     }
     cands.push_back(c);
     if (st != FBF_OK) break;
@@ -337,6 +398,18 @@ extern "C" fbf_status fbf_plan_create(const fbf_image_desc *descs, int n, fbf_fo
   p->chosen = cands[best];
   *out = p;
   return FBF_OK;
+}
+
+extern "C" fbf_status fbf_plan_create(const fbf_image_desc *descs, int n, fbf_form form, fbf_border border,
+                                      fbf_plan **out) {
+  return plan_create(descs, n, form, border, -1, out);
+}
+
+extern "C" fbf_status fbf_plan_create_schedule(const fbf_image_desc *descs, int n, fbf_form form,
+                                               fbf_border border, fbf_schedule schedule, fbf_plan **out) {
+  if (out) *out = nullptr;
+  if ((int)schedule < 0 || (int)schedule > (int)FBF_SCHEDULE_PER_IMAGE_FORM_STREAMS) return FBF_ERR_INVALID_ARGUMENT;
+  return plan_create(descs, n, form, border, (int)schedule, out);
 }
 
 extern "C" fbf_status fbf_filter_batched(fbf_plan *plan, cudaStream_t stream) {

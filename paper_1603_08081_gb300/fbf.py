@@ -24,7 +24,8 @@ FBF_BORDER_REFLECT, FBF_BORDER_TRUNCATE = 0, 1
 FBF_U8, FBF_F32 = 0, 1
 FBF_FORM_AUTO, FBF_FORM_FP32, FBF_FORM_TC_FP16, FBF_FORM_TC_BF16, FBF_FORM_TC_FP16_SINGLE = 0, 1, 2, 3, 4
 
-SCHEDULES = ["persistent", "persistent_wide", "per_image_fp32", "per_image_form"]
+SCHEDULES = ["persistent", "persistent_wide", "per_image_fp32", "per_image_form", "per_image_fp32_streams",
+             "per_image_form_streams"]
 
 _NAMES = {"gaussian": 0, "exponential": 1, "box": 1, "reflect": 0, "truncate": 1,
           "auto": 0, "fp32": 1, "tc_fp16": 2, "tc_bf16": 3, "tc_fp16_single": 4}
@@ -78,6 +79,8 @@ def _load():
     lib.fbf_filter_backward_noalloc.restype = i
     lib.fbf_plan_create.argtypes = [C.POINTER(fbf_image_desc), i, i, i, C.POINTER(p)]
     lib.fbf_plan_create.restype = i
+    lib.fbf_plan_create_schedule.argtypes = [C.POINTER(fbf_image_desc), i, i, i, i, C.POINTER(p)]
+    lib.fbf_plan_create_schedule.restype = i
     lib.fbf_filter_batched.argtypes = [p, p]
     lib.fbf_filter_batched.restype = i
     lib.fbf_plan_destroy.argtypes = [p]
@@ -287,9 +290,11 @@ class Plan:
             pass
 
 
-def fbf_plan_create(images, outs, specs, form="fp32", border="reflect"):
+def fbf_plan_create(images, outs, specs, form="fp32", border="reflect", schedule=None):
     """images / outs: lists of uint8 / float32 CUDA tensors; specs: list of dicts
-    with sigma_s, sigma_r and optionally W, spatial, range, T, eps, K_fixed, levels."""
+    with sigma_s, sigma_r and optionally W, spatial, range, T, eps, K_fixed, levels.
+    schedule: None autotunes (fbf_plan_create); a name of SCHEDULES captures
+    that schedule only (fbf_plan_create_schedule)."""
     n = len(images)
     arr = (fbf_image_desc * max(n, 1))()
     for k, (x, y, sp) in enumerate(zip(images, outs, specs)):
@@ -307,7 +312,10 @@ def fbf_plan_create(images, outs, specs, form="fp32", border="reflect"):
         d.K_fixed = int(sp.get("K_fixed", 0))
         d.levels = int(sp.get("levels", 0))
     h = C.c_void_p()
-    st = lib.fbf_plan_create(arr, n, _enum(form), _enum(border), C.byref(h))
+    if schedule is None:
+        st = lib.fbf_plan_create(arr, n, _enum(form), _enum(border), C.byref(h))
+    else:
+        st = lib.fbf_plan_create_schedule(arr, n, _enum(form), _enum(border), SCHEDULES.index(schedule), C.byref(h))
     if st != FBF_OK:
         raise FbfError(st, "fbf_plan_create")
     return Plan(h, (list(images), list(outs)))

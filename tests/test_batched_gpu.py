@@ -117,7 +117,8 @@ def test_autotuned_plan_equals_its_schedule(fbf, form):
     plan, xs, ys = _run_plan(fbf, imgs, specs, form=form)
     kind, ms = plan.schedule()
     assert kind in fbf.SCHEDULES and ms > 0
-    per_form = {"per_image_fp32": "fp32", "per_image_form": form}.get(kind, "fp32")
+    per_form = {"per_image_fp32": "fp32", "per_image_form": form, "per_image_fp32_streams": "fp32",
+                "per_image_form_streams": form}.get(kind, "fp32")
     for x, y, sp in zip(xs, ys, specs):
         c = fbf.fbf_fit_coeffs("gaussian", sp["sigma_r"], 255.0, 1e-3)
         p = fbf.make_params(c, sp["sigma_s"], sp.get("W", 0), sp.get("spatial", "gaussian"), "reflect", per_form)
@@ -131,10 +132,77 @@ def test_autotuned_plan_equals_its_schedule(fbf, form):
     plan.destroy()
 
 
+FORM_SCHEDULES = {
+    "fp32": ["persistent", "persistent_wide", "per_image_fp32", "per_image_fp32_streams"],
+    "auto": ["persistent", "persistent_wide", "per_image_fp32", "per_image_fp32_streams", "per_image_form",
+             "per_image_form_streams"],
+    "tc_fp16_single": ["per_image_form", "per_image_form_streams"],
+}
+
+
+@pytest.mark.parametrize("form,schedule", [(f, k) for f, ks in FORM_SCHEDULES.items() for k in ks])
+def test_every_schedule_explicitly(fbf, form, schedule):
+    """Each candidate schedule captured on its own (fbf_plan_create_schedule):
+    per-image schedules, sequential or on concurrent branches, replay exactly
+    the single-image kernels (bit-identical); the persistent ones the FP32 tile
+    body with run-time taps (within 1e-4).  Two replays give the same result."""
+    import torch
+
+    shapes = [(300, 260), (70, 90), (33, 200), (256, 40), (130, 131), (1, 64), (200, 180), (90, 300)]
+    specs = [dict(sigma_s=3.0, sigma_r=30.0), dict(sigma_s=0.7, sigma_r=15.0), dict(sigma_s=5.0, sigma_r=50.0),
+             dict(sigma_s=2.0, sigma_r=60.0, eps=1e-2), dict(sigma_s=4.0, sigma_r=25.0), dict(sigma_s=1.5, sigma_r=20.0),
+             dict(sigma_s=2.5, sigma_r=40.0), dict(sigma_s=1.0, sigma_r=35.0)]
+    imgs = [make_image(h, w, seed=1600 + k) for k, (h, w) in enumerate(shapes)]
+    xs = [torch.from_numpy(im).cuda() for im in imgs]
+    ys = [torch.full(im.shape, float("nan"), dtype=torch.float32, device="cuda") for im in imgs]
+    plan = fbf.fbf_plan_create(xs, ys, specs, form, "reflect", schedule=schedule)
+    assert plan.schedule() == (schedule, 0.0)
+    fbf.fbf_filter_batched(plan)
+    torch.cuda.synchronize()
+    first = [y.clone() for y in ys]
+    for y in ys:
+        y.fill_(float("nan"))
+    fbf.fbf_filter_batched(plan)
+    torch.cuda.synchronize()
+    per_form = "fp32" if schedule.startswith("per_image_fp32") or schedule.startswith("persistent") else form
+    for x, y, y0, sp in zip(xs, ys, first, specs):
+        assert torch.equal(y, y0)
+        c = fbf.fbf_fit_coeffs("gaussian", sp["sigma_r"], 255.0, sp.get("eps", 1e-3))
+        p = fbf.make_params(c, sp["sigma_s"], 0, "gaussian", "reflect", per_form)
+        single = fbf.fbf_filter(p, x)
+        torch.cuda.synchronize()
+        if schedule.startswith("per_image"):
+            assert torch.equal(single, y)
+        else:
+            assert torch.max(torch.abs(single - y)).item() <= 1e-4
+    plan.destroy()
+
+
+def test_schedule_not_of_the_form_is_rejected(fbf):
+    import ctypes as C
+
+    import torch
+
+    x = torch.zeros((40, 40), dtype=torch.uint8, device="cuda")
+    y = torch.zeros((40, 40), dtype=torch.float32, device="cuda")
+    for form, schedule in (("tc_fp16", "persistent"), ("tc_fp16", "per_image_fp32_streams"),
+                           ("fp32", "per_image_form")):
+        with pytest.raises(fbf.FbfError) as e:
+            fbf.fbf_plan_create([x], [y], [dict(sigma_s=2.0, sigma_r=30.0)], form, schedule=schedule)
+        assert e.value.status == fbf.FBF_ERR_INVALID_ARGUMENT
+    h = C.c_void_p()
+    arr = (fbf.fbf_image_desc * 1)()
+    assert fbf.lib.fbf_plan_create_schedule(arr, 0, fbf.FBF_FORM_FP32, 0, 6, C.byref(h)) == \
+        fbf.FBF_ERR_INVALID_ARGUMENT
+    assert fbf.lib.fbf_plan_create_schedule(arr, 0, fbf.FBF_FORM_FP32, 0, -1, C.byref(h)) == \
+        fbf.FBF_ERR_INVALID_ARGUMENT
+
+
 @pytest.mark.parametrize("form", ["tc_fp16", "tc_fp16_single", "tc_bf16"])
 def test_tensor_core_plan(fbf, form):
-    """Tensor-core plans replay one launch per image: identical to fbf_filter in
-    that form, and within the form's tolerance of the oracle."""
+    """Tensor-core plans replay one launch per image (on one or on concurrent
+    graph branches): identical to fbf_filter in that form, and within the
+    form's tolerance of the oracle."""
     import torch
 
     shapes = [(70, 90), (33, 200), (256, 40), (130, 131), (300, 260)]
@@ -142,7 +210,7 @@ def test_tensor_core_plan(fbf, form):
              dict(sigma_s=2.0, sigma_r=60.0, eps=1e-2), dict(sigma_s=10.0, sigma_r=25.0)]
     imgs = [make_image(h, w, seed=1500 + k) for k, (h, w) in enumerate(shapes)]
     plan, xs, ys = _run_plan(fbf, imgs, specs, form=form)
-    assert plan.schedule()[0] == "per_image_form"
+    assert plan.schedule()[0] in ("per_image_form", "per_image_form_streams")
     tol = 0.15 if form == "tc_fp16_single" else 0.02
     for im, x, y, sp in zip(imgs, xs, ys, specs):
         c = fbf.fbf_fit_coeffs("gaussian", sp["sigma_r"], 255.0, sp.get("eps", 1e-3))
