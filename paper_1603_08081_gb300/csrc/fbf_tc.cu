@@ -421,6 +421,12 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
   auto cen_off = [&](int j) -> uint32_t { return (j & 1) ? (cen_pk[j >> 1] >> 16) : (cen_pk[j >> 1] & 0xFFFFu); };
   uint32_t phR = 0, phC = 0, phT = 0;
   bool ok = true;
+  // The FP32 (cos, sin) table of harmonic n of the current tile is buffer
+  // (lbase + n) % 3; lbase advances by K per tile, so that in the pipelined
+  // schedule the next tile's tables of harmonic 0 are built as harmonic K of
+  // this one (in the phase that builds harmonic n + 2), not at its start.
+  int lbase = 0;
+  bool t0_ready = false;  // the tables of harmonic 0 of the current tile are built
   bool tma_pending = blockIdx.x < a.ntiles && tma_tile(blockIdx.x);  // a box copy is in flight
 
   // ---- modulate harmonic n: ext row r = 32 q + lane; units of 4 TMEM columns
@@ -557,7 +563,8 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
   auto demod = [&](int n) {
     const int c = lane & 3;
     const float dn = a.d[n];
-    const char *Lf = reinterpret_cast<const char *>(lutf + (n % 3) * kLutStride + ((lane >> 2) & (kCopies - 1)));
+    const char *Lf =
+        reinterpret_cast<const char *>(lutf + ((lbase + n) % 3) * kLutStride + ((lane >> 2) & (kCopies - 1)));
     constexpr int DG = BYH % 16 == 0 ? 16 : (BYH % 8 == 0 ? 8 : 4);  // columns per TMEM load
     uint32_t v[BYH / DG][DG];
 #pragma unroll
@@ -608,6 +615,19 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
       // source of halo pixels outside the image; pixels that touch no output
       // inside the image become the sentinel.
       const int bx0 = box_x(tile);
+      if (PIPE && ty0 - W >= 0 && ty0 - W + HY <= H && tx0 - W >= 0 && tx0 - W + HX <= Wd) {
+        // interior tile: every halo pixel is in the image, row ey of the box
+        // (pipelined schedule only: in the serial one the extra path cost spills)
+        for (int ey = warp; ey < kLanes; ey += NT / 32) {
+          const unsigned char *brow = raw + ey * kBoxW + (tx0 - W - bx0);
+#pragma unroll
+          for (int k4 = 0; k4 < 4; ++k4) {
+            const int ex = lane + 32 * k4;
+            if (ex < KX)
+              tileT[ey * kTY + ex * kTX] = ey < HY && ex < HX ? (unsigned short)(brow[ex] * kScale) : kSent;
+          }
+        }
+      } else {
       for (int ey = warp; ey < kLanes; ey += NT / 32) {
         const int iy = ty0 - W + ey;
         const bool row_ok = ey < HY && (reflect ? iy < H + W : (iy >= 0 && iy < H));
@@ -623,17 +643,19 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
           }
         }
       }
+      }
       fence_proxy_async_smem();  // the box is rewritten by the next TMA copy
     } else {
       stage_tile<NT>(static_cast<const unsigned char *>(a.in), a.in_pitch, H, Wd, a.border, ty0 - W, tx0 - W, HY,
                      HX, kLanes, KX, tileT, kTX, kTY, kScale, kSent);
     }
-    build_lut<BF, NT, kParts == 1>(lut16, lutf, trig, 0, a.twoT, a.T, c0, tid);
+    if (!t0_ready) build_lut<BF, NT, kParts == 1>(lut16, lutf + lbase * kLutStride, trig, 0, a.twoT, a.T, c0, tid);
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
     // prefetch the next tile of this CTA while this one is computed
     const int next = tile + gridDim.x;
+    const int lnext = (lbase + a.K) % 3;  // the next tile's buffer of harmonic 0
     if (next < a.ntiles && tma_tile(next)) {
       if (tid == 0) issue_tma(next);
       tma_pending = true;
@@ -657,8 +679,8 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
         if (!(ok = phase_sync())) break;
         if (row_issuer) issue_row();
         if (n + 1 < a.K)
-          build_lut<BF, NT, kParts == 1>(lut16, lutf + ((n + 1) % 3) * kLutStride, trig, n + 1, a.twoT, a.T, c0,
-                                         btid);
+          build_lut<BF, NT, kParts == 1>(lut16, lutf + ((lbase + n + 1) % 3) * kLutStride, trig, n + 1, a.twoT,
+                                         a.T, c0, btid);
         wait_mma(mbarR, phR);
         resplit();
         if (!(ok = phase_sync())) break;
@@ -675,7 +697,10 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
       ok = phase_sync();
       if (ok) {
         if (row_issuer) issue_row();
-        if (a.K > 1) build_lut<BF, NT, kParts == 1>(lut16, lutf + 1 * kLutStride, trig, 1, a.twoT, a.T, c0, btid);
+        // harmonic m = K is the next tile's harmonic 0 (its buffer (lbase + K) % 3)
+        if (a.K > 1 || next < a.ntiles)
+          build_lut<BF, NT, kParts == 1>(lut16, lutf + ((lbase + 1) % 3) * kLutStride, trig, a.K > 1 ? 1 : 0,
+                                         a.twoT, a.T, c0, btid);
         wait_mma(mbarR, phR);
         resplit();
         ok = phase_sync();
@@ -686,10 +711,11 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
         if (!(ok = phase_sync())) break;
         if (n + 1 < a.K && row_issuer) issue_row();  // R(n+1): A1 -> D1
         // Tables of n+2 while C(n) and R(n+1) run: lut16 (last read by the
-        // modulation of n+1, done) and lutf buffer (n+2) % 3 (not read by demod(n)).
-        if (n + 2 < a.K)
-          build_lut<BF, NT, kParts == 1>(lut16, lutf + ((n + 2) % 3) * kLutStride, trig, n + 2, a.twoT, a.T, c0,
-                                         btid);
+        // modulation of n+1, done) and lutf buffer (lbase + n + 2) % 3 (not read
+        // by demod(n) or demod(n + 1)); n + 2 = K is the next tile's harmonic 0.
+        if (n + 2 < a.K || (n + 2 == a.K && next < a.ntiles))
+          build_lut<BF, NT, kParts == 1>(lut16, lutf + ((lbase + n + 2) % 3) * kLutStride, trig,
+                                         n + 2 < a.K ? n + 2 : 0, a.twoT, a.T, c0, btid);
         wait_mma(mbarC, phC);
         demod(n);  // D2, table n
         if (n + 1 < a.K) {
@@ -725,6 +751,8 @@ __global__ void __launch_bounds__(NT, 1) fbf_tc_u8_kernel(const __grid_constant_
     }
     fence_before_sync();
     __syncthreads();
+    t0_ready = PIPE && next < a.ntiles;  // built as harmonic K (pipelined schedule)
+    lbase = PIPE ? lnext : 0;
   }
   // A prefetched box that no tile consumed (the loop was abandoned): let the
   // copy land (bounded wait) before the CTA exits.
