@@ -730,7 +730,8 @@ def main():
     ap.add_argument("--form", default="all", choices=["all"] + FORMS_ALL,
                     help="forms to time (default all; the headline is the fastest within 0.5 gray)")
     ap.add_argument("--slab-rows", type=int, default=384, help="rows of the CPU-baseline sample")
-    ap.add_argument("--ref-rows", type=int, default=8, help="rows per setting per reference step")
+    ap.add_argument("--ref-rows", type=int, default=64,
+                    help="rows per setting per reference step (the oracle also computes the 2W halo rows)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--batched", dest="batched", action="store_true", default=True,
                     help="also time the uneven 64-image batch (default on)")
