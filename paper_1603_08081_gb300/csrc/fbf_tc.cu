@@ -849,7 +849,7 @@ fbf_status launch_tc_cfg(const FilterArgs &a0, cudaStream_t s) {
 // mode 0: FP16 operands, split data, single weights (2 products per step);
 // 1: BF16 operands, split data and weights (3 products); 2: FP16 operands, data
 // and weights rounded once (1 product; A1 then takes half the TMEM columns, so
-// the 64-row tiles run the pipelined schedule too).
+// the tiles of windows above 16 run the pipelined schedule too).
 fbf_status launch_tc_u8(const FilterArgs &a, int mode, cudaStream_t s) {
   if (mode < 0 || mode > 2) return FBF_ERR_INVALID_ARGUMENT;
   constexpr int BY16 = FBF_TC_BY_16, NBC16 = FBF_TC_NBC_16, NT16 = FBF_TC_NT_16;
