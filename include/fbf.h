@@ -270,6 +270,24 @@ fbf_status fbf_filter_backward(const fbf_params *p, const float *d_in, const flo
  * two streams) race and give wrong results; serialise them.
  */
 #define FBF_NOALLOC_SCRATCH_BYTES (16u << 20)
+/*
+ * fbf_filter_stack / fbf_filter_backward_stack -- N images of one size under
+ * one set of parameters (a stack, e.g. a batch of a training step): image i
+ * starts at d_in + i * in_image_stride bytes (its output, gradient and
+ * gradient-input likewise with their own stride), and each image is filtered
+ * (or differentiated) exactly as fbf_filter (fbf_filter_backward) would, one
+ * launch after the other on `stream`.  Image strides must be at least H times
+ * the row pitch (images do not overlap); N = 0 does nothing.  The backward
+ * allocates its scratch once for the stack (one image's worth, reused
+ * stream-ordered).  Errors as for the single-image calls, plus
+ * FBF_ERR_INVALID_ARGUMENT for N < 0 or a short image stride.
+ */
+fbf_status fbf_filter_stack(const fbf_params *p, const void *d_in, fbf_dtype dtype, int N, int H, int Wd,
+                            size_t in_pitch, size_t in_image_stride, float *d_out, size_t out_pitch,
+                            size_t out_image_stride, cudaStream_t stream);
+fbf_status fbf_filter_backward_stack(const fbf_params *p, const float *d_in, const float *d_gout, float *d_gin,
+                                     int N, int H, int Wd, size_t pitch, size_t image_stride,
+                                     cudaStream_t stream);
 fbf_status fbf_filter_backward_noalloc(const fbf_params *p, const float *d_in, const float *d_gout,
                                        const float *d_out_fwd, float *d_gin, int H, int Wd, size_t pitch,
                                        cudaStream_t stream);

@@ -128,6 +128,50 @@ extern "C" fbf_status fbf_filter_backward(const fbf_params *p, const float *d_in
   return st;
 }
 
+extern "C" fbf_status fbf_filter_stack(const fbf_params *p, const void *d_in, fbf_dtype dtype, int N, int H,
+                                       int Wd, size_t in_pitch, size_t in_image_stride, float *d_out,
+                                       size_t out_pitch, size_t out_image_stride, cudaStream_t stream) {
+  if (N < 0) return FBF_ERR_INVALID_ARGUMENT;
+  FilterArgs a;
+  fbf_status st = pack_filter_args(p, d_in, dtype, H, Wd, in_pitch, d_out, out_pitch, &a);
+  if (st != FBF_OK) return st;
+  if (N == 0 || H == 0 || Wd == 0) return FBF_OK;
+  if (N > 1 && (in_image_stride < (size_t)H * in_pitch || out_image_stride < (size_t)H * out_pitch))
+    return FBF_ERR_INVALID_ARGUMENT;
+  for (int i = 0; i < N && st == FBF_OK; ++i) {
+    a.in = static_cast<const char *>(d_in) + (size_t)i * in_image_stride;
+    a.out = reinterpret_cast<float *>(reinterpret_cast<char *>(d_out) + (size_t)i * out_image_stride);
+    st = launch_filter(a, p->form, dtype, stream);
+  }
+  return st;
+}
+
+extern "C" fbf_status fbf_filter_backward_stack(const fbf_params *p, const float *d_in, const float *d_gout,
+                                                float *d_gin, int N, int H, int Wd, size_t pitch,
+                                                size_t image_stride, cudaStream_t stream) {
+  if (N < 0) return FBF_ERR_INVALID_ARGUMENT;
+  FilterArgs a;
+  fbf_status st = pack_filter_args(p, d_in, FBF_F32, H, Wd, pitch, d_gin, pitch, &a);
+  if (st != FBF_OK) return st;
+  if (N == 0 || H == 0 || Wd == 0) return FBF_OK;
+  if (!d_gout) return FBF_ERR_INVALID_ARGUMENT;
+  if (N > 1 && image_stride < (size_t)H * pitch) return FBF_ERR_INVALID_ARGUMENT;
+  if (p->form != FBF_FORM_AUTO && p->form != FBF_FORM_FP32) return FBF_ERR_UNSUPPORTED;
+  if (a.W > f32_wmax()) return FBF_ERR_RANGE;
+  const size_t bytes = backward_scratch_bytes(H, Wd, a.W, a.border);
+  void *scratch = nullptr;
+  if (cudaMallocAsync(&scratch, bytes, stream) != cudaSuccess) return FBF_ERR_CUDA;
+  for (int i = 0; i < N && st == FBF_OK; ++i) {
+    const size_t off = (size_t)i * image_stride;
+    a.in = reinterpret_cast<const char *>(d_in) + off;
+    a.out = reinterpret_cast<float *>(reinterpret_cast<char *>(d_gin) + off);
+    const float *g = reinterpret_cast<const float *>(reinterpret_cast<const char *>(d_gout) + off);
+    st = launch_backward(a, g, pitch, a.out, pitch, scratch, stream);
+  }
+  if (cudaFreeAsync(scratch, stream) != cudaSuccess && st == FBF_OK) st = FBF_ERR_CUDA;
+  return st;
+}
+
 extern "C" fbf_status fbf_device_error(unsigned int *code) {
   if (!code) return FBF_ERR_INVALID_ARGUMENT;
   if (cudaDeviceSynchronize() != cudaSuccess) return FBF_ERR_CUDA;

@@ -77,6 +77,10 @@ def _load():
     lib.fbf_filter_backward.restype = i
     lib.fbf_filter_backward_noalloc.argtypes = [C.POINTER(fbf_params), p, p, p, p, i, i, sz, p]
     lib.fbf_filter_backward_noalloc.restype = i
+    lib.fbf_filter_stack.argtypes = [C.POINTER(fbf_params), p, i, i, i, i, sz, sz, p, sz, sz, p]
+    lib.fbf_filter_stack.restype = i
+    lib.fbf_filter_backward_stack.argtypes = [C.POINTER(fbf_params), p, p, p, i, i, i, sz, sz, p]
+    lib.fbf_filter_backward_stack.restype = i
     lib.fbf_plan_create.argtypes = [C.POINTER(fbf_image_desc), i, i, i, C.POINTER(p)]
     lib.fbf_plan_create.restype = i
     lib.fbf_plan_create_schedule.argtypes = [C.POINTER(fbf_image_desc), i, i, i, i, C.POINTER(p)]
@@ -156,14 +160,18 @@ def _stream_handle(stream):
 
 
 def fbf_filter(params: fbf_params, x, out=None, stream=None):
-    """Filter a 2-D CUDA tensor (uint8 or float32).  Returns the float32 output.
+    """Filter a 2-D CUDA tensor (uint8 or float32), or a 3-D stack (N, H, W) of
+    images under the same parameters (fbf_filter_stack).  Returns the float32
+    output of the same shape.
 
     Rows may be padded (any row stride); columns must be contiguous.
     """
     import torch
 
+    if x.dim() == 3 and x.is_cuda:
+        return _filter_stack(params, x, out, stream)
     if x.dim() != 2 or not x.is_cuda:
-        raise ValueError("fbf_filter expects a 2-D CUDA tensor")
+        raise ValueError("fbf_filter expects a 2-D (or 3-D stacked) CUDA tensor")
     if x.dtype == torch.uint8:
         dt, esz = FBF_U8, 1
     elif x.dtype == torch.float32:
@@ -207,18 +215,49 @@ def fbf_local_range(x, W: int, out=None, stream=None) -> int:
     return int(out.item())
 
 
+def _filter_stack(params, x, out, stream):
+    import torch
+
+    if x.dtype == torch.uint8:
+        dt, esz = FBF_U8, 1
+    elif x.dtype == torch.float32:
+        dt, esz = FBF_F32, 4
+    else:
+        raise TypeError("fbf_filter: dtype must be uint8 or float32")
+    x = x.contiguous()
+    N, H, Wd = x.shape
+    if out is None:
+        out = torch.empty((N, H, Wd), dtype=torch.float32, device=x.device)
+    if out.dtype != torch.float32 or out.shape != x.shape or not out.is_contiguous():
+        raise ValueError("fbf_filter: out must be a contiguous float32 (N, H, W) tensor")
+    st = lib.fbf_filter_stack(C.byref(params), C.c_void_p(x.data_ptr()), dt, N, H, Wd, Wd * esz, H * Wd * esz,
+                              C.c_void_p(out.data_ptr()), Wd * 4, H * Wd * 4, _stream_handle(stream))
+    if st != FBF_OK:
+        raise FbfError(st, "fbf_filter_stack")
+    return out
+
+
 def fbf_filter_backward(params: fbf_params, x, g, grad=None, stream=None):
-    """dL/dx for L = sum(g * fbf_filter(params, x)); x and g float32 CUDA (H, W)."""
+    """dL/dx for L = sum(g * fbf_filter(params, x)); x and g float32 CUDA, one
+    image (H, W) or a stack (N, H, W) (fbf_filter_backward_stack)."""
     import torch
 
     if x.dtype != torch.float32 or g.dtype != torch.float32 or not (x.is_cuda and g.is_cuda):
         raise TypeError("fbf_filter_backward: x and g must be float32 CUDA tensors")
     x = x.contiguous()
     g = g.contiguous()
-    if g.shape != x.shape or x.dim() != 2:
-        raise ValueError("fbf_filter_backward: x and g must have the same 2-D shape")
+    if g.shape != x.shape or x.dim() not in (2, 3):
+        raise ValueError("fbf_filter_backward: x and g must have the same 2-D or 3-D shape")
     if grad is None:
         grad = torch.empty_like(x)
+    if x.dim() == 3:
+        N, H, Wd = x.shape
+        st = lib.fbf_filter_backward_stack(C.byref(params), C.c_void_p(x.data_ptr()), C.c_void_p(g.data_ptr()),
+                                           C.c_void_p(grad.data_ptr()), N, H, Wd, Wd * 4, H * Wd * 4,
+                                           _stream_handle(stream))
+        if st != FBF_OK:
+            raise FbfError(st, "fbf_filter_backward_stack")
+        return grad
     H, Wd = x.shape
     st = lib.fbf_filter_backward(C.byref(params), C.c_void_p(x.data_ptr()), C.c_void_p(g.data_ptr()), None,
                                  C.c_void_p(grad.data_ptr()), H, Wd, x.stride(0) * 4, _stream_handle(stream))
@@ -232,7 +271,8 @@ def _autograd_function():
 
     class FBFFunction(torch.autograd.Function):
         """Differentiable shiftable bilateral filter (in x only): forward is
-        fbf_filter (FP32 form, float input), backward the hand-written adjoint."""
+        fbf_filter (FP32 form, float input), backward the hand-written adjoint;
+        x is one image (H, W) or a stack (N, H, W) under the same parameters."""
 
         @staticmethod
         def forward(ctx, x, params):

@@ -158,3 +158,74 @@ def test_backward_rejects_tensor_core_forms_and_big_windows(fbf):
     st = fbf.lib.fbf_filter_backward(C.byref(p), C.c_void_p(x.data_ptr()), C.c_void_p(x.data_ptr()), None,
                                      C.c_void_p(x.data_ptr()), 8, 8, 32, None)
     assert st == fbf.FBF_ERR_RANGE
+
+
+@pytest.mark.parametrize("form", ["fp32", "tc_fp16", "tc_fp16_single"])
+def test_stack_forward_equals_each_image(fbf, form):
+    """fbf_filter_stack (3-D input) gives every image exactly what fbf_filter
+    gives it alone, for uint8 stacks in every form and float stacks (FP32)."""
+    import torch
+
+    from paper_1603_08081_gb300.synth import make_image
+
+    c = fbf.fbf_fit_coeffs("gaussian", 25.0, 255.0, 1e-3)
+    p = fbf.make_params(c, 3.0, 0, "gaussian", "reflect", form)
+    x = torch.stack([torch.from_numpy(make_image(70, 90, seed=900 + k)) for k in range(5)]).cuda()
+    y = fbf.fbf_filter(p, x)
+    torch.cuda.synchronize()
+    for k in range(5):
+        assert torch.equal(y[k], fbf.fbf_filter(p, x[k]))
+    if form == "fp32":
+        cf = _fit(fbf)
+        pf = fbf.make_params(cf, 2.0)
+        xf = torch.stack([torch.from_numpy(make_image_f32(40, 75, 950 + k)) for k in range(4)]).cuda()
+        yf = fbf.fbf_filter(pf, xf)
+        torch.cuda.synchronize()
+        for k in range(4):
+            assert torch.equal(yf[k], fbf.fbf_filter(pf, xf[k]))
+
+
+@pytest.mark.parametrize("border", ["reflect", "truncate"])
+def test_stack_backward_and_autograd_equal_each_image(fbf, border):
+    """fbf_filter_backward_stack and the autograd Function on a (N, H, W) stack
+    give every image the gradient of the single-image adjoint, bit for bit."""
+    import torch
+
+    c = _fit(fbf)
+    p = fbf.make_params(c, 3.0, 0, "gaussian", border)
+    x = torch.stack([torch.from_numpy(make_image_f32(48, 66, 960 + k)) for k in range(4)]).cuda()
+    g = torch.stack([torch.from_numpy(make_grad(48, 66, 970 + k)) for k in range(4)]).cuda()
+    gin = fbf.fbf_filter_backward(p, x, g)
+    xr = x.detach().requires_grad_(True)
+    (fbf.FBFFunction.apply(xr, p) * g).sum().backward()
+    torch.cuda.synchronize()
+    for k in range(4):
+        single = fbf.fbf_filter_backward(p, x[k], g[k])
+        torch.cuda.synchronize()
+        assert torch.equal(gin[k], single)
+        assert torch.equal(xr.grad[k], single)
+
+
+def test_stack_arguments(fbf):
+    import ctypes as C
+
+    import torch
+
+    c = _fit(fbf)
+    p = fbf.make_params(c, 2.0)
+    x = torch.zeros((3, 8, 8), dtype=torch.float32, device="cuda")
+    px, po = C.c_void_p(x.data_ptr()), C.c_void_p(x.data_ptr())
+    lib = fbf.lib
+    assert lib.fbf_filter_stack(C.byref(p), px, fbf.FBF_F32, -1, 8, 8, 32, 256, po, 32, 256, None) == \
+        fbf.FBF_ERR_INVALID_ARGUMENT
+    assert lib.fbf_filter_stack(C.byref(p), px, fbf.FBF_F32, 2, 8, 8, 32, 255, po, 32, 256, None) == \
+        fbf.FBF_ERR_INVALID_ARGUMENT
+    assert lib.fbf_filter_stack(C.byref(p), px, fbf.FBF_F32, 0, 8, 8, 32, 0, po, 32, 0, None) == fbf.FBF_OK
+    assert lib.fbf_filter_backward_stack(C.byref(p), px, px, po, 2, 8, 8, 32, 128, None) == \
+        fbf.FBF_ERR_INVALID_ARGUMENT
+    assert lib.fbf_filter_backward_stack(C.byref(p), px, None, po, 2, 8, 8, 32, 256, None) == \
+        fbf.FBF_ERR_INVALID_ARGUMENT
+    pt = fbf.make_params(c, 2.0, 0, "gaussian", "reflect", "tc_fp16")
+    assert lib.fbf_filter_backward_stack(C.byref(pt), px, px, po, 2, 8, 8, 32, 256, None) == \
+        fbf.FBF_ERR_UNSUPPORTED
+    torch.cuda.synchronize()
