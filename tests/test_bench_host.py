@@ -1,0 +1,48 @@
+"""Host-side accounting of bench.py (no GPU): the flop counts behind the
+roofline fractions it reports.
+
+The algorithmic count is the separable FIR over C = 4(K-1) + 2 real channels
+(two passes of 2W + 1 taps, 2 flops per multiply-add).  The tensor-core kernel
+issues MMAs over 4 channels for every harmonic, with band padding and the split
+products, so its issued count can never be below the algorithmic count times
+the products per step, and the padding stays bounded.
+"""
+import math
+
+import pytest
+
+import bench
+
+FORMS = sorted(bench.TC_NSPLIT)
+
+
+def test_algorithmic_flops_closed_form():
+    # K = 1: the n = 0 term only (channels f and 1); W = 0: a single tap
+    assert bench.algorithmic_flops_per_pixel(1, 0) == 2 * 2 * 1 * 2
+    # the 2048^2 setting sigma_s = 10 (W = 30), K = 17: C = 66 channels
+    assert bench.algorithmic_flops_per_pixel(17, 30) == 4 * 61 * 66
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("K", [1, 9, 17])
+def test_issued_flops_bound_the_algorithmic_count(form, K):
+    px = bench.H * bench.W_IMG
+    for W in range(0, 33):
+        issued = bench.tc_issued_flops(K, W, form)
+        useful = bench.algorithmic_flops_per_pixel(K, W) * px * bench.TC_NSPLIT[form]
+        assert issued >= useful, (form, K, W)
+        # padding: 16-wide K chunks around a 2W + 1 band, 4 channels where K = 1
+        # has 2, computed rows past 128 - 2W; bounded once the band fills a chunk
+        if W >= 9:
+            assert issued <= 12 * useful, (form, K, W)
+
+
+def test_issued_flops_follow_the_tile_count():
+    """2048^2 at W = 9: 19 x 64 tiles of 110 output rows (8 waves of 152 CTAs);
+    per tile and harmonic 4 channels x 4 row chunks of 128 x 32 x 16 and one
+    112-row column block of 8 chunks of 128 x 112 x 16."""
+    tiles = math.ceil(2048 / 32) * math.ceil(2048 / 110)
+    assert tiles == 1216 == 8 * 152
+    per_tile = 4 * 4 * 2 * 128 * 32 * 16 + 8 * 2 * 128 * 112 * 16
+    assert bench.tc_issued_flops(1, 9, "tc_fp16_single") == tiles * per_tile
+    assert bench.tc_issued_flops(17, 9, "tc_fp16") == 17 * 2 * tiles * per_tile
