@@ -66,7 +66,7 @@ def _load():
             lib.orc_grad_direct.argtypes = [dp, dp, i, i, dp, i, i, dp, i, d, dp]
             lib.orc_grad_direct.restype = None
             lib.orc_grad_at.argtypes = [dp, dp, i, i, dp, i, i, dp, i, d, ip, ip, lp, dp]
-            lib.orc_grad_at.restype = None
+            lib.orc_grad_at.restype = i
             lib.orc_set_threads.argtypes = [i]
             lib.orc_set_threads.restype = None
             lib.orc_local_range.argtypes = [dp, i, i, i, i]
@@ -241,8 +241,10 @@ def grad_at(f, g, w1, border: int, d, T: float, points):
     d = np.ascontiguousarray(d, np.float64)
     ys, xs, n = _points(points)
     out = np.empty(n, np.float64)
-    _load().orc_grad_at(_dp(f), _dp(g), H, Wd, _dp(w1), W, int(border), _dp(d), len(d), float(T),
-                        _ip(ys), _ip(xs), n, _dp(out))
+    st = _load().orc_grad_at(_dp(f), _dp(g), H, Wd, _dp(w1), W, int(border), _dp(d), len(d), float(T),
+                             _ip(ys), _ip(xs), n, _dp(out))
+    if st != 0:
+        raise MemoryError("orc_grad_at: could not allocate its preimage lists")
     return out
 
 

@@ -469,19 +469,31 @@ static void orc_pq_at(const double *f, int H, int Wd, const double *w1, int W, i
   *Q = den;
 }
 
-void orc_grad_at(const double *f, const double *g, int H, int Wd, const double *w1, int W, int border,
-                 const double *d, int K, double T, const int *ys, const int *xs, long npts, double *out) {
-#pragma omp parallel for schedule(dynamic, 1)
+int orc_grad_at(const double *f, const double *g, int H, int Wd, const double *w1, int W, int border,
+                const double *d, int K, double T, const int *ys, const int *xs, long npts, double *out) {
+  /* Each 1-D preimage list holds at most every extended position of its axis
+   * (H + 2W rows, Wd + 2W columns); the lists are sized for that, so no
+   * preimage is ever dropped.  Returns 0, or -1 when the lists cannot be
+   * allocated (then `out` is not filled). */
+  const long cap_y = (long)H + 2L * W, cap_x = (long)Wd + 2L * W;
+  int failed = 0;
+#pragma omp parallel for schedule(dynamic, 1) reduction(| : failed)
   for (long p = 0; p < npts; ++p) {
     long my = ys[p], mx = xs[p];
     double fm = f[my * Wd + mx], acc = 0.0;
     /* 1-D preimages of my / mx among the extended positions */
-    long qy[64], qx[64];
+    long *qy = malloc(sizeof(long) * (size_t)cap_y), *qx = malloc(sizeof(long) * (size_t)cap_x);
+    if (!qy || !qx) {
+      free(qy);
+      free(qx);
+      failed = 1;
+      continue;
+    }
     int ny = 0, nx = 0;
     if (border == ORC_BORDER_REFLECT) {
-      for (long q = -W; q < H + W && ny < 64; ++q)
+      for (long q = -W; q < H + W; ++q)
         if (orc_reflect(q, H) == my) qy[ny++] = q;
-      for (long q = -W; q < Wd + W && nx < 64; ++q)
+      for (long q = -W; q < Wd + W; ++q)
         if (orc_reflect(q, Wd) == mx) qx[nx++] = q;
     } else {
       qy[ny++] = my;
@@ -518,7 +530,10 @@ void orc_grad_at(const double *f, const double *g, int H, int Wd, const double *
       }
     }
     out[p] = acc;
+    free(qy);
+    free(qx);
   }
+  return failed ? -1 : 0;
 }
 
 /*

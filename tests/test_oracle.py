@@ -293,10 +293,11 @@ def test_gradient_against_central_differences(border):
 
 
 @pytest.mark.parametrize("border", [O.BORDER_REFLECT, O.BORDER_TRUNCATE])
-@pytest.mark.parametrize("shape,W", [((9, 11), 2), ((6, 5), 4), ((12, 10), 3)])
+@pytest.mark.parametrize("shape,W", [((9, 11), 2), ((6, 5), 4), ((12, 10), 3), ((1, 3), 32), ((2, 1), 33)])
 def test_gradient_at_points_equals_full_gradient(border, shape, W):
     """The sampled-pixel gradient enumerates the same pairs as the full one
-    (including windows wider than the image, where pixels reflect repeatedly)."""
+    (including windows wider than the image, where pixels reflect repeatedly:
+    a one-row image under W = 32 has 65 row preimages per pixel)."""
     rng = np.random.default_rng(1)
     f = rng.uniform(0.1, 0.9, size=shape)
     g = rng.normal(size=shape)
