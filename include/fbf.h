@@ -264,12 +264,18 @@ fbf_status fbf_filter_backward(const fbf_params *p, const float *d_in, const flo
  * device memory on every GPU that loads it, until the process exits; nothing is
  * allocated or freed.  A request needing more than that (8 bytes per pixel,
  * plus (H+2W)(Wd+2W) floats under REFLECT, rounded up to 256 bytes) returns
- * FBF_ERR_RANGE.  The first call on a device looks up the array's device
- * address (with that device current); make that first call before any stream
- * capture.  All calls share the array: calls whose GPU work overlaps (e.g. on
- * two streams) race and give wrong results; serialise them.
+ * FBF_ERR_RANGE.  Every call looks up the array's device address on the
+ * current device (cudaGetSymbolAddress, which allocates nothing); the first
+ * lookup on a device may load the library's device code, so make the first
+ * call on a device before any stream capture.  All calls share the array:
+ * calls whose GPU work overlaps (e.g. on two streams) race and give wrong
+ * results; serialise them.
  */
 #define FBF_NOALLOC_SCRATCH_BYTES (16u << 20)
+fbf_status fbf_filter_backward_noalloc(const fbf_params *p, const float *d_in, const float *d_gout,
+                                       const float *d_out_fwd, float *d_gin, int H, int Wd, size_t pitch,
+                                       cudaStream_t stream);
+
 /*
  * fbf_filter_stack / fbf_filter_backward_stack -- N images of one size under
  * one set of parameters (a stack, e.g. a batch of a training step): image i
@@ -288,9 +294,6 @@ fbf_status fbf_filter_stack(const fbf_params *p, const void *d_in, fbf_dtype dty
 fbf_status fbf_filter_backward_stack(const fbf_params *p, const float *d_in, const float *d_gout, float *d_gin,
                                      int N, int H, int Wd, size_t pitch, size_t image_stride,
                                      cudaStream_t stream);
-fbf_status fbf_filter_backward_noalloc(const fbf_params *p, const float *d_in, const float *d_gout,
-                                       const float *d_out_fwd, float *d_gin, int H, int Wd, size_t pitch,
-                                       cudaStream_t stream);
 
 /* Dynamic range T of an 8-bit image over the window Omega = [-W, W]^2: the
  * quantity defined at the start of Sec. III, T = max over pixels i and offsets

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstdint>
 #include <cstring>
 
 #include "fbf_internal.h"
@@ -36,6 +37,9 @@ fbf_status pack_filter_args(const fbf_params *p, const void *d_in, fbf_dtype dty
     if (in_pitch < (size_t)Wd * esz || out_pitch < (size_t)Wd * sizeof(float)) return FBF_ERR_INVALID_ARGUMENT;
     if (out_pitch % sizeof(float) != 0) return FBF_ERR_INVALID_ARGUMENT;
     if (dtype == FBF_F32 && in_pitch % sizeof(float) != 0) return FBF_ERR_INVALID_ARGUMENT;
+    // float rows are read and written as floats: their base pointers must be 4-byte aligned
+    if (reinterpret_cast<uintptr_t>(d_out) % sizeof(float) != 0) return FBF_ERR_INVALID_ARGUMENT;
+    if (dtype == FBF_F32 && reinterpret_cast<uintptr_t>(d_in) % sizeof(float) != 0) return FBF_ERR_INVALID_ARGUMENT;
     if ((size_t)H * out_pitch > ((size_t)1 << 62)) return FBF_ERR_INVALID_ARGUMENT;
   }
   if (dtype == FBF_U8) {
@@ -117,7 +121,7 @@ extern "C" fbf_status fbf_filter_backward(const fbf_params *p, const float *d_in
   fbf_status st = pack_filter_args(p, d_in, FBF_F32, H, Wd, pitch, d_gin, pitch, &a);
   if (st != FBF_OK) return st;
   if (H == 0 || Wd == 0) return FBF_OK;
-  if (!d_gout) return FBF_ERR_INVALID_ARGUMENT;
+  if (!d_gout || reinterpret_cast<uintptr_t>(d_gout) % sizeof(float) != 0) return FBF_ERR_INVALID_ARGUMENT;
   if (p->form != FBF_FORM_AUTO && p->form != FBF_FORM_FP32) return FBF_ERR_UNSUPPORTED;
   if (a.W > f32_wmax()) return FBF_ERR_RANGE;
   const size_t bytes = backward_scratch_bytes(H, Wd, a.W, a.border);
@@ -138,6 +142,9 @@ extern "C" fbf_status fbf_filter_stack(const fbf_params *p, const void *d_in, fb
   if (N == 0 || H == 0 || Wd == 0) return FBF_OK;
   if (N > 1 && (in_image_stride < (size_t)H * in_pitch || out_image_stride < (size_t)H * out_pitch))
     return FBF_ERR_INVALID_ARGUMENT;
+  // image i starts i strides in: float images need strides that keep 4-byte alignment
+  if (N > 1 && (out_image_stride % sizeof(float) != 0 || (dtype == FBF_F32 && in_image_stride % sizeof(float) != 0)))
+    return FBF_ERR_INVALID_ARGUMENT;
   for (int i = 0; i < N && st == FBF_OK; ++i) {
     a.in = static_cast<const char *>(d_in) + (size_t)i * in_image_stride;
     a.out = reinterpret_cast<float *>(reinterpret_cast<char *>(d_out) + (size_t)i * out_image_stride);
@@ -155,7 +162,9 @@ extern "C" fbf_status fbf_filter_backward_stack(const fbf_params *p, const float
   if (st != FBF_OK) return st;
   if (N == 0 || H == 0 || Wd == 0) return FBF_OK;
   if (!d_gout) return FBF_ERR_INVALID_ARGUMENT;
-  if (N > 1 && image_stride < (size_t)H * pitch) return FBF_ERR_INVALID_ARGUMENT;
+  if (N > 1 && (image_stride < (size_t)H * pitch || image_stride % sizeof(float) != 0))
+    return FBF_ERR_INVALID_ARGUMENT;
+  if (reinterpret_cast<uintptr_t>(d_gout) % sizeof(float) != 0) return FBF_ERR_INVALID_ARGUMENT;
   if (p->form != FBF_FORM_AUTO && p->form != FBF_FORM_FP32) return FBF_ERR_UNSUPPORTED;
   if (a.W > f32_wmax()) return FBF_ERR_RANGE;
   const size_t bytes = backward_scratch_bytes(H, Wd, a.W, a.border);

@@ -19,34 +19,24 @@
 // same device without ordering) race on the array and produce wrong results.
 #include <cuda_runtime.h>
 
-#include <mutex>
+#include <cstdint>
 
 #include "fbf_internal.h"
 
 // The shared scratch.  In host code this name is only a stand-in for the device
-// symbol: its device address is looked up once per device below.
+// symbol: its device address is looked up (with the device current) below.
 static __device__ __align__(256) unsigned char g_fbf_noalloc_scratch[FBF_NOALLOC_SCRATCH_BYTES];
 
 namespace fbf {
 namespace {
 
-constexpr int kMaxDevices = 64;
-std::mutex g_scratch_mu;
-void *g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device (looked up on the
-// first call per device, with that device current).
+// Device address of the scratch array on the current device.  Looked up on
+// every call (cudaGetSymbolAddress allocates nothing and is cheap), so that an
+// address is never reused after the device was reset or the module reloaded.
 fbf_status scratch_address(void **out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return FBF_ERR_CUDA;
-  if (dev < 0 || dev >= kMaxDevices) return FBF_ERR_UNSUPPORTED;
-  std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_ptr[dev]) {
-    void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_fbf_noalloc_scratch) != cudaSuccess || !p) return FBF_ERR_CUDA;
-    g_scratch_ptr[dev] = p;
-  }
-  *out = g_scratch_ptr[dev];
+  void *p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_fbf_noalloc_scratch) != cudaSuccess || !p) return FBF_ERR_CUDA;
+  *out = p;
   return FBF_OK;
 }
 
@@ -63,7 +53,7 @@ extern "C" fbf_status fbf_filter_backward_noalloc(const fbf_params *p, const flo
   fbf_status st = pack_filter_args(p, d_in, FBF_F32, H, Wd, pitch, d_gin, pitch, &a);
   if (st != FBF_OK) return st;
   if (H == 0 || Wd == 0) return FBF_OK;
-  if (!d_gout) return FBF_ERR_INVALID_ARGUMENT;
+  if (!d_gout || reinterpret_cast<uintptr_t>(d_gout) % sizeof(float) != 0) return FBF_ERR_INVALID_ARGUMENT;
   if (p->form != FBF_FORM_AUTO && p->form != FBF_FORM_FP32) return FBF_ERR_UNSUPPORTED;
   if (a.W > f32_wmax()) return FBF_ERR_RANGE;
   if (backward_scratch_bytes(H, Wd, a.W, a.border) > (size_t)FBF_NOALLOC_SCRATCH_BYTES) return FBF_ERR_RANGE;

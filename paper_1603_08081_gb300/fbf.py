@@ -250,6 +250,10 @@ def fbf_filter_backward(params: fbf_params, x, g, grad=None, stream=None):
         raise ValueError("fbf_filter_backward: x and g must have the same 2-D or 3-D shape")
     if grad is None:
         grad = torch.empty_like(x)
+    elif (grad.dtype != torch.float32 or grad.shape != x.shape or grad.device != x.device
+          or not grad.is_contiguous()):
+        # the library writes grad with x's (contiguous) layout
+        raise ValueError("fbf_filter_backward: grad must be a contiguous float32 tensor of x's shape and device")
     if x.dim() == 3:
         N, H, Wd = x.shape
         st = lib.fbf_filter_backward_stack(C.byref(params), C.c_void_p(x.data_ptr()), C.c_void_p(g.data_ptr()),

@@ -228,4 +228,27 @@ def test_stack_arguments(fbf):
     pt = fbf.make_params(c, 2.0, 0, "gaussian", "reflect", "tc_fp16")
     assert lib.fbf_filter_backward_stack(C.byref(pt), px, px, po, 2, 8, 8, 32, 256, None) == \
         fbf.FBF_ERR_UNSUPPORTED
+    # image strides that would misalign the float images after the first one
+    assert lib.fbf_filter_stack(C.byref(p), px, fbf.FBF_F32, 2, 8, 8, 32, 258, po, 32, 256, None) == \
+        fbf.FBF_ERR_INVALID_ARGUMENT
+    assert lib.fbf_filter_stack(C.byref(p), px, fbf.FBF_F32, 2, 8, 8, 32, 256, po, 32, 258, None) == \
+        fbf.FBF_ERR_INVALID_ARGUMENT
+    assert lib.fbf_filter_backward_stack(C.byref(p), px, px, po, 2, 8, 8, 32, 258, None) == \
+        fbf.FBF_ERR_INVALID_ARGUMENT
+    # misaligned float base pointers (input, output, upstream gradient)
+    odd = C.c_void_p(x.data_ptr() + 2)
+    assert lib.fbf_filter_stack(C.byref(p), odd, fbf.FBF_F32, 1, 8, 8, 32, 256, po, 32, 256, None) == \
+        fbf.FBF_ERR_INVALID_ARGUMENT
+    assert lib.fbf_filter_stack(C.byref(p), px, fbf.FBF_F32, 1, 8, 8, 32, 256, odd, 32, 256, None) == \
+        fbf.FBF_ERR_INVALID_ARGUMENT
+    assert lib.fbf_filter_backward_stack(C.byref(p), px, odd, po, 2, 8, 8, 32, 256, None) == \
+        fbf.FBF_ERR_INVALID_ARGUMENT
+    assert lib.fbf_filter_backward(C.byref(p), px, odd, None, po, 8, 8, 32, None) == fbf.FBF_ERR_INVALID_ARGUMENT
+    # a caller-supplied grad of the wrong shape, dtype or layout is refused before the call
+    x2, g2 = x[0].clone(), torch.ones((8, 8), dtype=torch.float32, device="cuda")
+    for bad in (torch.empty((4, 8), dtype=torch.float32, device="cuda"),
+                torch.empty((8, 8), dtype=torch.float64, device="cuda"),
+                torch.empty((8, 16), dtype=torch.float32, device="cuda")[:, ::2]):
+        with pytest.raises(ValueError):
+            fbf.fbf_filter_backward(p, x2, g2, grad=bad)
     torch.cuda.synchronize()

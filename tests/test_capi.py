@@ -128,6 +128,25 @@ def test_filter_validation_without_device_work(fbf):
     assert L.fbf_filter(C.byref(pb), dummy, 0, 4, 4, 4, dummy, 16, nul) == fbf.FBF_ERR_RANGE
 
 
+def test_stack_and_alignment_validation_without_device_work(fbf):
+    """Float images must stay 4-byte aligned: a misaligned base pointer or an
+    image stride that is not a multiple of 4 is refused before any launch."""
+    L = fbf.lib
+    c = fbf.fbf_fit_coeffs("gaussian", 30.0, 255.0, 1e-2)
+    p = fbf.make_params(c, 3.0)
+    nul = C.c_void_p(0)
+    a, odd = C.c_void_p(4096), C.c_void_p(4098)
+    # fbf_filter: FP32 output (and FP32 input) base pointers
+    assert L.fbf_filter(C.byref(p), a, 0, 4, 4, 4, odd, 16, nul) == fbf.FBF_ERR_INVALID_ARGUMENT
+    assert L.fbf_filter(C.byref(p), odd, 1, 4, 4, 16, a, 16, nul) == fbf.FBF_ERR_INVALID_ARGUMENT
+    # stacks: strides of float images
+    assert L.fbf_filter_stack(C.byref(p), a, 0, 2, 4, 4, 4, 16, a, 16, 66, nul) == fbf.FBF_ERR_INVALID_ARGUMENT
+    assert L.fbf_filter_stack(C.byref(p), a, 1, 2, 4, 4, 16, 66, a, 16, 64, nul) == fbf.FBF_ERR_INVALID_ARGUMENT
+    assert L.fbf_filter_backward_stack(C.byref(p), a, a, a, 2, 4, 4, 16, 66, nul) == fbf.FBF_ERR_INVALID_ARGUMENT
+    assert L.fbf_filter_backward_stack(C.byref(p), a, odd, a, 2, 4, 4, 16, 64, nul) == fbf.FBF_ERR_INVALID_ARGUMENT
+    assert L.fbf_filter_backward_noalloc(C.byref(p), a, odd, None, a, 4, 4, 16, nul) == fbf.FBF_ERR_INVALID_ARGUMENT
+
+
 def test_status_strings(fbf):
     for s in range(7):
         assert fbf.fbf_status_string(s).startswith("FBF_")
