@@ -129,6 +129,29 @@ fbf_status fbf_fit_coeffs(fbf_range_kernel kernel, double sigma_r, double T, dou
                           int K_fixed, int levels, fbf_coeffs *out);
 
 /*
+ * fbf_fit_coeffs_samples -- Algorithm 2 for a range kernel given by its
+ * samples, host, FP64.  Sec. III states that the progressive fit applies to
+ * any kernel whose Fourier series converges pointwise (the Gaussian and the
+ * exponential are two of them); this entry point takes such a kernel as
+ * samples instead of an enum.
+ *
+ *   phi      host array of L values phi(t_l) at t_l = l * T / (L - 1),
+ *            l = 0 .. L-1 (for integer T and L = T + 1: the grid {0, ..., T});
+ *            phi is even, so only [0, T] is sampled; read during the call only
+ *   L        number of samples (>= 2)
+ *   T        half period (> 0); omega = pi / T
+ *   eps      tolerance on ||b - A d||_2 (> 0) when K_fixed == 0
+ *   K_fixed  > 0: fit exactly this many coefficients, ignore eps
+ *   out      as fbf_fit_coeffs (out->levels = L)
+ * Returns FBF_ERR_INVALID_ARGUMENT for a null pointer, L < 2, a non-finite
+ * sample or bad T / eps; FBF_ERR_RANGE if K_fixed exceeds FBF_KMAX or L;
+ * FBF_ERR_NOT_CONVERGED (out filled) when eps is not reached by
+ * min(L, FBF_KMAX) coefficients.
+ */
+fbf_status fbf_fit_coeffs_samples(const double *phi, int L, double T, double eps, int K_fixed,
+                                  fbf_coeffs *out);
+
+/*
  * fbf_filter -- Algorithm 1 (Shiftable Bilateral Filtering) on the GPU.
  *
  * Computes, for every pixel, fhat(i) = P(i) / Q(i) with

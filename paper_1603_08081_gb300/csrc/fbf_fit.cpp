@@ -51,31 +51,17 @@ extern "C" int fbf_resolve_window(const fbf_params *p) {
 // start vector); each new column is orthogonalised against the previous q's
 // one at a time (MGS), normalised, appended to Q, and Q^T b and R grow by one
 // entry / column; R d = p is solved by back-substitution and the residual
-// E = ||b - A d|| decides whether to continue (Sec. III).
-extern "C" fbf_status fbf_fit_coeffs(fbf_range_kernel kernel, double sigma_r, double T,
-                                     double eps, int K_fixed, int levels, fbf_coeffs *out) {
-  if (!out) return FBF_ERR_INVALID_ARGUMENT;
-  if (kernel != FBF_RANGE_GAUSSIAN && kernel != FBF_RANGE_EXPONENTIAL) return FBF_ERR_INVALID_ARGUMENT;
-  if (!(sigma_r > 0.0) || !std::isfinite(sigma_r)) return FBF_ERR_INVALID_ARGUMENT;
-  if (!(T > 0.0) || !std::isfinite(T)) return FBF_ERR_INVALID_ARGUMENT;
-  if (K_fixed < 0 || levels < 0 || levels == 1) return FBF_ERR_INVALID_ARGUMENT;
-  if (K_fixed == 0 && !(eps > 0.0)) return FBF_ERR_INVALID_ARGUMENT;
-  int L;
-  if (levels == 0) {
-    if (T != std::floor(T) || T > 1e6) return FBF_ERR_INVALID_ARGUMENT;
-    L = (int)T + 1;
-  } else {
-    L = levels;
-  }
+// E = ||b - A d|| decides whether to continue (Sec. III).  b holds the samples
+// phi(t_l) on the grid t (L points), however they were obtained.
+namespace {
+
+fbf_status progressive_fit(const std::vector<double> &t, const std::vector<double> &b, int L, double T,
+                           double eps, int K_fixed, fbf_coeffs *out) {
   const int Kcap = L < FBF_KMAX ? L : FBF_KMAX;
   if (K_fixed > Kcap) return FBF_ERR_RANGE;
 
   const double omega = M_PI / T;
-  std::vector<double> t(L), b(L), a(L);
-  for (int l = 0; l < L; ++l) {
-    t[l] = levels == 0 ? (double)l : (double)l * T / (double)(levels - 1);
-    b[l] = range_kernel(kernel, sigma_r, t[l]);
-  }
+  std::vector<double> a(L);
   std::vector<double> Qm((size_t)L * Kcap);  // orthonormal columns q_1..q_N
   std::vector<double> R((size_t)Kcap * Kcap, 0.0);  // R[row * Kcap + col]
   std::vector<double> p(Kcap), d(Kcap);
@@ -148,6 +134,51 @@ extern "C" fbf_status fbf_fit_coeffs(fbf_range_kernel kernel, double sigma_r, do
   out->resid_linf = Einf;
   for (int k = 0; k < N; ++k) out->d[k] = d[k];
   return done() ? FBF_OK : FBF_ERR_NOT_CONVERGED;
+}
+
+}  // namespace
+
+extern "C" fbf_status fbf_fit_coeffs(fbf_range_kernel kernel, double sigma_r, double T,
+                                     double eps, int K_fixed, int levels, fbf_coeffs *out) {
+  if (!out) return FBF_ERR_INVALID_ARGUMENT;
+  if (kernel != FBF_RANGE_GAUSSIAN && kernel != FBF_RANGE_EXPONENTIAL) return FBF_ERR_INVALID_ARGUMENT;
+  if (!(sigma_r > 0.0) || !std::isfinite(sigma_r)) return FBF_ERR_INVALID_ARGUMENT;
+  if (!(T > 0.0) || !std::isfinite(T)) return FBF_ERR_INVALID_ARGUMENT;
+  if (K_fixed < 0 || levels < 0 || levels == 1) return FBF_ERR_INVALID_ARGUMENT;
+  if (K_fixed == 0 && !(eps > 0.0)) return FBF_ERR_INVALID_ARGUMENT;
+  int L;
+  if (levels == 0) {
+    if (T != std::floor(T) || T > 1e6) return FBF_ERR_INVALID_ARGUMENT;
+    L = (int)T + 1;
+  } else {
+    L = levels;
+  }
+  std::vector<double> t(L), b(L);
+  for (int l = 0; l < L; ++l) {
+    t[l] = levels == 0 ? (double)l : (double)l * T / (double)(levels - 1);
+    b[l] = range_kernel(kernel, sigma_r, t[l]);
+  }
+  return progressive_fit(t, b, L, T, eps, K_fixed, out);
+}
+
+// Any range kernel given by its samples (Sec. III: every kernel whose Fourier
+// series converges pointwise qualifies): phi[l] = phi(t_l) on the equispaced
+// grid t_l = l T / (L - 1), l = 0..L-1 (for integer T and L = T + 1, the grid
+// {0, 1, ..., T} of Algorithm 2).
+extern "C" fbf_status fbf_fit_coeffs_samples(const double *phi, int L, double T, double eps, int K_fixed,
+                                             fbf_coeffs *out) {
+  if (!out || !phi) return FBF_ERR_INVALID_ARGUMENT;
+  if (L < 2 || L > (1 << 20)) return FBF_ERR_INVALID_ARGUMENT;
+  if (!(T > 0.0) || !std::isfinite(T)) return FBF_ERR_INVALID_ARGUMENT;
+  if (K_fixed < 0) return FBF_ERR_INVALID_ARGUMENT;
+  if (K_fixed == 0 && !(eps > 0.0)) return FBF_ERR_INVALID_ARGUMENT;
+  std::vector<double> t(L), b(L);
+  for (int l = 0; l < L; ++l) {
+    if (!std::isfinite(phi[l])) return FBF_ERR_INVALID_ARGUMENT;
+    t[l] = (double)l * T / (double)(L - 1);
+    b[l] = phi[l];
+  }
+  return progressive_fit(t, b, L, T, eps, K_fixed, out);
 }
 
 extern "C" const char *fbf_status_string(fbf_status s) {

@@ -71,6 +71,8 @@ def _load():
     i, d, p, sz = C.c_int, C.c_double, C.c_void_p, C.c_size_t
     lib.fbf_fit_coeffs.argtypes = [i, d, d, d, i, i, C.POINTER(fbf_coeffs)]
     lib.fbf_fit_coeffs.restype = i
+    lib.fbf_fit_coeffs_samples.argtypes = [C.POINTER(C.c_double), i, d, d, i, C.POINTER(fbf_coeffs)]
+    lib.fbf_fit_coeffs_samples.restype = i
     lib.fbf_filter.argtypes = [C.POINTER(fbf_params), p, i, i, i, sz, p, sz, p]
     lib.fbf_filter.restype = i
     lib.fbf_filter_backward.argtypes = [C.POINTER(fbf_params), p, p, p, p, i, i, sz, p]
@@ -131,6 +133,19 @@ def fbf_fit_coeffs(kernel="gaussian", sigma_r: float = 30.0, T: float = 255.0, e
                             int(levels), C.byref(out))
     if st != FBF_OK and not (st == FBF_ERR_NOT_CONVERGED and allow_not_converged):
         raise FbfError(st, "fbf_fit_coeffs")
+    return out
+
+
+def fbf_fit_coeffs_samples(phi, T: float, eps: float = 1e-3, K_fixed: int = 0,
+                           allow_not_converged: bool = False) -> fbf_coeffs:
+    """Algorithm 2 for a range kernel given by samples phi(t_l), t_l = l T / (L - 1)
+    (see fbf.h)."""
+    vals = [float(v) for v in phi]
+    arr = (C.c_double * max(len(vals), 1))(*vals)
+    out = fbf_coeffs()
+    st = lib.fbf_fit_coeffs_samples(arr, len(vals), float(T), float(eps), int(K_fixed), C.byref(out))
+    if st != FBF_OK and not (st == FBF_ERR_NOT_CONVERGED and allow_not_converged):
+        raise FbfError(st, "fbf_fit_coeffs_samples")
     return out
 
 

@@ -63,6 +63,69 @@ def test_host_fit_matches_oracle(fbf, kernel, sigma_r, T, eps, K, levels):
     assert c.omega == pytest.approx(np.pi / T)
 
 
+def _tukey(t, c=60.0):
+    # Tukey's biweight: (1 - (t/c)^2)^2 inside |t| <= c, 0 outside (continuous, C^1)
+    u = np.clip(np.abs(t) / c, 0.0, 1.0)
+    return (1.0 - u * u) ** 2
+
+
+def _huber(t, k=25.0):
+    # Huber-type weight: 1 inside |t| <= k, k/|t| outside (continuous, one kink)
+    a = np.abs(t)
+    return np.where(a <= k, 1.0, k / np.maximum(a, 1e-300))
+
+
+@pytest.mark.parametrize("name,phi,T,L,eps,K", [
+    ("tukey", _tukey, 255.0, 256, 1e-3, 0),
+    ("huber", _huber, 255.0, 256, 1e-3, 0),
+    ("lorentz", lambda t: 1.0 / (1.0 + (t / 30.0) ** 2), 255.0, 256, 1e-3, 0),
+    ("tukey_fixed", _tukey, 255.0, 256, 0.0, 40),
+    ("tukey_unit", lambda t: _tukey(t, 60.0 / 255.0), 1.0, 256, 1e-3, 0),
+    ("huber_coarse", _huber, 255.0, 64, 1e-2, 0),
+])
+def test_fit_from_samples_matches_oracle(fbf, name, phi, T, L, eps, K):
+    """Algorithm 2 on user samples of a kernel (Sec. III: any kernel whose Fourier
+    series converges pointwise) reaches the oracle's least-squares solution
+    (Householder QR of the same samples): same order, d within 1e-10."""
+    t = np.arange(L) * T / (L - 1)
+    b = phi(t)
+    c = fbf.fbf_fit_coeffs_samples(b, T, eps, K)
+    o = O.fit_samples(t, b, T, eps, K)
+    assert c.K == o.K and c.levels == L
+    assert np.max(np.abs(np.array(c.coefficients) - o.d)) <= 1e-10
+    assert c.resid_l2 == pytest.approx(o.E, rel=1e-8, abs=1e-13)
+    assert c.resid_linf == pytest.approx(o.linf, rel=1e-8, abs=1e-13)
+    if K == 0:
+        assert c.resid_l2 <= eps and c.resid_linf <= c.resid_l2 * (1 + 1e-12)
+
+
+def test_fit_from_samples_equals_enum_fit_on_the_same_grid(fbf):
+    """Samples of the Gaussian on {0..T} are what fbf_fit_coeffs fits."""
+    t = np.arange(256.0)
+    for sr, eps in ((20.0, 1e-3), (30.0, 1e-2)):
+        a = fbf.fbf_fit_coeffs("gaussian", sr, 255.0, eps)
+        b = fbf.fbf_fit_coeffs_samples(np.exp(-t * t / (2 * sr * sr)), 255.0, eps)
+        assert a.K == b.K  # (numpy's exp and the library's may differ in the last bit)
+        assert np.max(np.abs(np.array(a.coefficients) - np.array(b.coefficients))) <= 1e-13
+
+
+def test_fit_from_samples_errors(fbf):
+    L = fbf.lib
+    out = fbf.fbf_coeffs()
+    arr = (C.c_double * 4)(1.0, 0.5, 0.2, 0.1)
+    assert L.fbf_fit_coeffs_samples(None, 4, 3.0, 1e-3, 0, C.byref(out)) == fbf.FBF_ERR_INVALID_ARGUMENT
+    assert L.fbf_fit_coeffs_samples(arr, 1, 3.0, 1e-3, 0, C.byref(out)) == fbf.FBF_ERR_INVALID_ARGUMENT
+    assert L.fbf_fit_coeffs_samples(arr, 4, 0.0, 1e-3, 0, C.byref(out)) == fbf.FBF_ERR_INVALID_ARGUMENT
+    assert L.fbf_fit_coeffs_samples(arr, 4, 3.0, 0.0, 0, C.byref(out)) == fbf.FBF_ERR_INVALID_ARGUMENT
+    assert L.fbf_fit_coeffs_samples(arr, 4, 3.0, 1e-3, 5, C.byref(out)) == fbf.FBF_ERR_RANGE
+    assert L.fbf_fit_coeffs_samples(arr, 4, 3.0, 1e-3, 0, None) == fbf.FBF_ERR_INVALID_ARGUMENT
+    nan = (C.c_double * 4)(1.0, float("nan"), 0.2, 0.1)
+    assert L.fbf_fit_coeffs_samples(nan, 4, 3.0, 1e-3, 0, C.byref(out)) == fbf.FBF_ERR_INVALID_ARGUMENT
+    # 4 samples are fitted exactly by 4 columns
+    assert L.fbf_fit_coeffs_samples(arr, 4, 3.0, 1e-14, 0, C.byref(out)) in (fbf.FBF_OK, fbf.FBF_ERR_NOT_CONVERGED)
+    assert out.K == 4 and out.resid_l2 < 1e-12
+
+
 def test_host_fit_tables_3_and_4(fbf):
     for eps, N in ((1e-8, 15), (1e-5, 12), (1e-4, 11), (1e-3, 10), (1e-2, 8), (1e-1, 7)):
         assert fbf.fbf_fit_coeffs("gaussian", 30.0, 217.0, eps).K == N

@@ -221,6 +221,26 @@ def test_single_form_small_range_scale(fbf, sigma_r):
     _check(_gpu(fbf, img, c, 3.0, form="tc_fp16"), ref, TOL_TC)
 
 
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("kernel", ["tukey", "huber"])
+def test_user_sampled_range_kernel(fbf, kernel, form):
+    """A range kernel given only by samples (Sec. III: any kernel with a pointwise-
+    convergent Fourier series), fitted by fbf_fit_coeffs_samples: Tukey's biweight
+    (1 - (t/60)^2)^2 on |t| <= 60, or the Huber-type weight min(1, 25/|t|).  Every
+    form against Algorithm 1 in FP64 with the same coefficients, both borders."""
+    t = np.arange(256.0)
+    if kernel == "tukey":
+        phi = (1.0 - np.clip(t / 60.0, 0.0, 1.0) ** 2) ** 2
+    else:
+        phi = np.minimum(1.0, 25.0 / np.maximum(t, 1e-300))
+    c = fbf.fbf_fit_coeffs_samples(phi, 255.0, 1e-3)
+    assert c.K > 5
+    img = make_image(150, 130, seed=21)
+    for border, ss in (("reflect", 3.0), ("truncate", 5.0)):
+        got = _gpu(fbf, img, c, ss, border=border, form=form)
+        _check(got, _oracle_full(img, c, ss, int(np.ceil(3 * ss)), "gaussian", border), TOL[form])
+
+
 @pytest.mark.parametrize("border", ["reflect", "truncate"])
 def test_box_4096_exponential_sampled(fbf, border):
     """The 4096x4096 exponential-kernel workload with the box kernel W = 8 (the
