@@ -18,8 +18,14 @@ pinned host buffers (H2D of the image and D2H of every output of every step
 inside the timed region, steps pipelined with double buffers).  The L2 is flushed (256 MiB write) between timed steps, outside the
 per-step events.  `roofline` is for the headline form's dominant launch (largest
 share of the step): FP32-pipe bound for fp32 (against an FMA peak measured in
-the same process), tensor-pipe for the tensor-core forms (issued MMA flops
-against the measured bf16 peak).  `cpu_baseline` times the FP64 oracle (Algorithm 1 form) on a
+the same process), tensor-pipe for the tensor-core forms; `achieved` / `frac`
+count the method's own work (the FIR flops of Algorithm 1, 2 (2W+1) MACs per
+channel per pass) against the measured bf16 peak, `pipe_frac` the dense MMA
+flops the kernel issues (band padding and split products included), and
+`padding_ratio` their quotient.  `value_bf16` and `value_fp32` repeat the two
+forms the metric names beside the headline, each with its own roofline
+fraction; `cfg0` times the plain 256x256 configuration (K = 10) per form with
+its errors and the host time per call.  `cpu_baseline` times the FP64 oracle (Algorithm 1 form) on a
 bounded row slab of the same workload and reports its agreement with the GPU
 output on that slab (the max-error condition of the metric).
 
@@ -210,10 +216,50 @@ FORMS_ALL = ["fp32", "tc_fp16", "tc_bf16", "tc_fp16_single"]
 FORM_DTYPE = {"fp32": "f32", "tc_fp16": "f16", "tc_bf16": "bf16", "tc_fp16_single": "f16"}
 FORM_KERNEL = {"fp32": "fbf_fp32_u8_kernel", "tc_fp16": "fbf_tc_u8_kernel<0,2,..>",
                "tc_bf16": "fbf_tc_u8_kernel<1,3,..>", "tc_fp16_single": "fbf_tc_u8_kernel<0,1,..>"}
+FORM_KERNEL2 = {"tc_fp16": "fbf_tc2_u8_kernel<0,2,..>", "tc_bf16": "fbf_tc2_u8_kernel<1,3,..>",
+                "tc_fp16_single": "fbf_tc2_u8_kernel<0,1,..>"}
+
+
+def form_kernel(form: str, W: int) -> str:
+    if form != "fp32" and tc_layout(form, W) == "tc2":
+        return FORM_KERNEL2[form]
+    return FORM_KERNEL[form]
 TC_NSPLIT = {"tc_fp16": 2, "tc_bf16": 3, "tc_fp16_single": 1}
 
 
+TC2_WMAX = {"tc_fp16_single": 48, "tc_fp16": 24, "tc_bf16": 16}  # windows of the second layout
+
+
+def tc_layout(form: str, W: int) -> str:
+    """Which tensor-core layout runs the form at this window (T <= 255)."""
+    return "tc2" if W <= TC2_WMAX[form] else "tc1"
+
+
 def tc_issued_flops(K: int, W: int, form: str) -> float:
+    """Dense MMA flops of one 2048x2048 launch of the tensor-core form, band
+    padding and split products included (see tc1_issued_flops and
+    tc2_issued_flops)."""
+    if tc_layout(form, W) == "tc2":
+        return tc2_issued_flops(K, W, form)
+    return tc1_issued_flops(K, W, form)
+
+
+def tc2_issued_flops(K: int, W: int, form: str) -> float:
+    """Second layout: tiles of 32 columns x (128 - 2W) output rows; per harmonic
+    and tile the row pass issues 4 channels x KX/16 chunks of M = 128, N = 32,
+    K = 16 (KX = ext columns, Wp + 32 + W rounded up to 16, Wp = W rounded up
+    to 8), the column pass 8 chunks of M = 128, N = 128, K = 16; each once per
+    split product."""
+    nsplit = TC_NSPLIT[form]
+    Wp = (W + 7) // 8 * 8
+    kcr = (Wp + 32 + W + 15) // 16
+    tiles = math.ceil(W_IMG / 32) * math.ceil(H / (128 - 2 * W))
+    row = 4 * kcr * (2.0 * 128 * 32 * 16)
+    col = 8 * (2.0 * 128 * 128 * 16)
+    return tiles * K * (row + col) * nsplit
+
+
+def tc1_issued_flops(K: int, W: int, form: str) -> float:
     """Dense MMA flops the tensor-core kernel issues for one 2048x2048 launch,
     band padding and split products included (mirrors its tiling: tiles of 32
     columns x min(BY, 128 - 2W) output rows, BY = 112 computed rows for W <= 16,
@@ -358,6 +404,51 @@ def _timed_steps(torch, dev, stream, fn, steps, flush=None):
         e1.synchronize()
         tot += e0.elapsed_time(e1)
     return tot / steps
+
+
+def run_cfg0(fbf, torch, dev, stream, forms, steps, flush, with_oracle):
+    """The plain small configuration: one 256x256 u8 image (seed 1000),
+    Gaussian sigma_s = 3 (W = 9), sigma_r = 30, eps = 1e-2 (K = 10), REFLECT.
+    Per form: device ms per launch (CUDA events, L2 flushed before each), the
+    host time of one fbf_filter call through the Python API (back-to-back calls,
+    no synchronisation: argument checks, packing and the launch), the max and
+    RMS error against the FP64 oracle (Algorithm 1, whole image) and the max
+    error against the exact filter eq. (1) (whole image)."""
+    from paper_1603_08081_gb300.synth import make_image
+
+    img = make_image(256, 256, 1000)
+    x = torch.from_numpy(img).to(dev)
+    y = torch.empty((256, 256), dtype=torch.float32, device=dev)
+    c = fbf.fbf_fit_coeffs("gaussian", 30.0, T, 1e-2)
+    res = {"workload": "256x256 u8 synthetic (seed 1000), sigma_s=3 (W=9), sigma_r=30, eps=1e-2, K=%d, reflect"
+                       % c.K, "pixels": int(img.size), "runs": []}
+    ref = direct = None
+    if with_oracle:
+        import oracle as O
+
+        w1 = O.weights_1d(O.SPATIAL_GAUSSIAN, 3.0, 9)
+        ref = O.alg1(img.astype(np.float64), w1, O.BORDER_REFLECT, np.array(c.coefficients), T)[0]
+        direct = O.direct_bf(img.astype(np.float64), w1, O.BORDER_REFLECT, O.RANGE_GAUSSIAN, 30.0)[0]
+        res["bound_eq12"] = round(O.bound12(T, 1e-2, float(w1[9]) ** 2), 3)
+    for f in forms:
+        p = fbf.make_params(c, 3.0, 0, "gaussian", "reflect", f)
+        ms = _timed_steps(torch, dev, stream, lambda: fbf.fbf_filter(p, x, out=y, stream=stream), steps, flush)
+        torch.cuda.synchronize(dev)
+        n_calls = 200
+        t0 = time.perf_counter()
+        for _ in range(n_calls):
+            fbf.fbf_filter(p, x, out=y, stream=stream)
+        host_us = (time.perf_counter() - t0) / n_calls * 1e6
+        torch.cuda.synchronize(dev)
+        row = {"form": f, "ms": round(ms, 5), "mpix_s": round(img.size / ms / 1e3, 1),
+               "host_us_per_call": round(host_us, 2)}
+        if ref is not None:
+            got = y.cpu().numpy().astype(np.float64)
+            row["max_err_vs_oracle"] = round(float(np.max(np.abs(got - ref))), 6)
+            row["rms_err_vs_oracle"] = round(float(np.sqrt(np.mean((got - ref) ** 2))), 7)
+            row["max_err_vs_direct_eq1"] = round(float(np.max(np.abs(got - direct))), 5)
+        res["runs"].append(row)
+    return res
 
 
 def run_exponential(fbf, torch, dev, stream, steps, flush, with_oracle, slab_rows=32):
@@ -554,18 +645,22 @@ def run_ours(args):
         t_dom = mean_launch[dom] * 1e-3
         if f == "fp32":
             ach = algorithmic_flops_per_pixel(K_dom, W_dom) * H * W_IMG / t_dom / 1e12
-            roof = {"bound": "alu", "kernel": FORM_KERNEL[f], "launch": launch, "achieved": round(ach, 3),
+            roof = {"bound": "alu", "kernel": form_kernel(f, W_dom), "launch": launch, "achieved": round(ach, 3),
                     "peak": round(fp32_peak, 3), "unit": "TFLOP/s", "frac": round(ach / fp32_peak, 4),
                     "traffic": None,
                     "peak_source": "FP32 FMA probe (fbf_measure_fp32_peak) in this process (of measured)"}
         else:
-            ach = tc_issued_flops(K_dom, W_dom, f) / t_dom / 1e12
+            # achieved / frac: the method's own work (the FIR flops of Algorithm 1);
+            # pipe_frac: the dense MMA flops the kernel issues (band padding and
+            # split products included) -- their ratio is the padding the tiling pays
+            issued = tc_issued_flops(K_dom, W_dom, f) / t_dom / 1e12
             alg = algorithmic_flops_per_pixel(K_dom, W_dom) * H * W_IMG / t_dom / 1e12
-            roof = {"bound": "tensor", "kernel": FORM_KERNEL[f], "launch": launch, "achieved": round(ach, 3),
-                    "peak": round(tpeak, 1), "unit": "TFLOP/s", "frac": round(ach / tpeak, 4),
-                    "traffic": recorded_traffic(FORM_KERNEL[f], launch), "peak_source": tpeak_src,
-                    "fir_equivalent_tflops": round(alg, 3),
-                    "fir_equivalent_frac_of_fp32_peak": round(alg / fp32_peak, 4)}
+            roof = {"bound": "tensor", "kernel": form_kernel(f, W_dom), "launch": launch, "achieved": round(alg, 3),
+                    "peak": round(tpeak, 1), "unit": "TFLOP/s", "frac": round(alg / tpeak, 4),
+                    "traffic": recorded_traffic(form_kernel(f, W_dom), launch), "peak_source": tpeak_src,
+                    "issued_mma_tflops": round(issued, 3), "pipe_frac": round(issued / tpeak, 4),
+                    "padding_ratio": round(issued / alg, 3),
+                    "fir_frac_of_fp32_peak": round(alg / fp32_peak, 4)}
         per_form[f] = {"value": world * px_step * args.steps / (total_ms * 1e-3) / 1e6,
                        "ms_per_step": total_ms / args.steps, "per_setting": per_setting, "roofline": roof}
 
@@ -669,7 +764,24 @@ def run_ours(args):
                                                         not args.no_cpu_baseline)
         extras["local_range"] = run_local_range(fbf, torch, dev, stream, x, ex_steps)
 
+    def flush_l2_cfg0():
+        with torch.cuda.stream(stream):
+            flush.zero_()
+
+    cfg0 = run_cfg0(fbf, torch, dev, stream, forms, max(20, args.steps), flush_l2_cfg0,
+                    with_oracle=rank == 0 and not args.no_cpu_baseline) if rank == 0 else None
+
     hf = per_form[head]
+
+    def form_line(f):
+        if f not in per_form:
+            return None
+        r = per_form[f]["roofline"]
+        return {"value": round(per_form[f]["value"], 1), "unit": "Mpixel/s",
+                "max_err_vs_oracle": per_form[f].get("max_err_vs_oracle"),
+                "frac": r["frac"], "bound": r["bound"], "peak": r["peak"], "achieved": r["achieved"],
+                "launch": r["launch"]}
+
     result = {
         "metric": METRIC, "value": round(hf["value"], 1), "unit": "Mpixel/s", "n_gpus": world,
         "steps": args.steps, "warmup": max(args.warmup, 3),
@@ -682,6 +794,9 @@ def run_ours(args):
                    "l2": "flushed between steps (256 MiB write, outside the timed events)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": hf["roofline"],
+        # the two forms the metric names, side by side with the headline
+        "value_bf16": form_line("tc_bf16"),
+        "value_fp32": form_line("fp32"),
         "forms": {f: {"value": round(per_form[f]["value"], 1), "ms_per_step": round(per_form[f]["ms_per_step"], 4),
                       "max_err_vs_oracle": per_form[f].get("max_err_vs_oracle"),
                       "roofline": per_form[f]["roofline"], "per_setting": per_form[f]["per_setting"]}
@@ -695,6 +810,8 @@ def run_ours(args):
         "gpu_launches": n_set * args.steps * len(forms),
         "clocks": clk.summary(),
     }
+    if cfg0 is not None:
+        result["cfg0"] = cfg0
     if batched is not None:
         result["batched"] = batched
     result.update(extras)

@@ -340,9 +340,20 @@ fbf_status fbf_local_range(const void *d_in, fbf_dtype dtype, int H, int Wd, siz
 int fbf_resolve_window(const fbf_params *p);
 
 /* Reads and clears the library's device-side error word on the current device
- * (non-zero when a bounded wait inside a kernel gave up).  Synchronises the
- * device.  *code receives the word. */
+ * (non-zero when a bounded wait inside a kernel gave up: that kernel then
+ * abandoned its remaining tiles, so its output is incomplete).  Synchronises
+ * the device.  *code receives the word; returns FBF_ERR_TIMEOUT when it is
+ * non-zero, FBF_OK when it is zero, FBF_ERR_CUDA when the device cannot be
+ * read. */
 fbf_status fbf_device_error(unsigned int *code);
+
+/* Poll limit of the tensor-core kernels' bounded waits (mbarrier waits on
+ * their MMAs and TMA copies), for the calls launched after it: polls >= 0 sets
+ * it (0: every wait gives up at once -- a way to exercise the failure path,
+ * which then leaves the outputs incomplete and sets the device error word),
+ * polls < 0 restores the default (about a second of polling).  A process-wide
+ * setting; not part of the filter.  FBF_ERR_RANGE above 2^32 - 1. */
+fbf_status fbf_set_wait_limit(long long polls);
 
 /* FP32-pipe throughput probe (the roofline denominator of the FP32 form).
  * Runs independent FMA chains on every SM of `device` -- scalar FFMA when

@@ -190,5 +190,15 @@ extern "C" fbf_status fbf_device_error(unsigned int *code) {
   unsigned int vt = 0;
   if (tc_read_clear_error(&vt) != FBF_OK) return FBF_ERR_CUDA;
   *code = v | vt;
-  return FBF_OK;
+  return *code != 0 ? FBF_ERR_TIMEOUT : FBF_OK;
 }
+
+namespace fbf {
+// Device address of g_fbf_device_error on the current device (passed to the
+// kernels that record their failures through a pointer).
+unsigned int *device_error_word() {
+  void *p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_fbf_device_error) != cudaSuccess) return nullptr;
+  return static_cast<unsigned int *>(p);
+}
+}  // namespace fbf

@@ -5,6 +5,8 @@
 #include <cstddef>
 #include <cstdint>
 
+#include <cuda.h>
+
 #include "fbf.h"
 
 #ifndef M_PI
@@ -62,5 +64,28 @@ fbf_status launch_backward(const FilterArgs &a, const float *g, size_t g_pitch, 
                            void *scratch, cudaStream_t s);
 
 inline fbf_status cuda_status(cudaError_t e) { return e == cudaSuccess ? FBF_OK : FBF_ERR_CUDA; }
+
+// Second tensor-core layout (fbf_tc2_*.cu): FBF_ERR_UNSUPPORTED when the
+// request lies outside its instantiations (the caller then runs the first one).
+fbf_status launch_tc2_u8(const FilterArgs &a, int mode, cudaStream_t s);
+fbf_status launch_tc2_single(const FilterArgs &a, cudaStream_t s);
+fbf_status launch_tc2_fp16(const FilterArgs &a, cudaStream_t s);
+fbf_status launch_tc2_bf16(const FilterArgs &a, cudaStream_t s);
+
+// Host helpers shared by the launchers (fbf_host.cu, fbf_api.cu).
+// 2-D u8 TMA map of an image with a box of bw x bh bytes, cached per (device,
+// pointer, shape, pitch, box); false when TMA's 16-byte rules are not met.
+bool cached_box_map(const void *ptr, int Wd, int H, size_t pitch, int bw, int bh, CUtensorMap *out);
+int sm_count(int dev);                // multiprocessor count, cached per device
+unsigned int *device_error_word();    // device address of the library's error word (current device)
+unsigned int wait_polls();            // poll limit of the kernels' bounded waits
+// cudaFuncSetAttribute once per kernel and device (a bit per device ordinal < 64).
+struct FuncAttrOnce {
+  unsigned long long mask = 0;
+  bool done(int dev) const { return dev >= 0 && dev < 64 && ((__atomic_load_n(&mask, __ATOMIC_ACQUIRE) >> dev) & 1); }
+  void set(int dev) {
+    if (dev >= 0 && dev < 64) __atomic_fetch_or(&mask, 1ull << dev, __ATOMIC_RELEASE);
+  }
+};
 
 }  // namespace fbf

@@ -99,6 +99,8 @@ def _load():
     lib.fbf_local_range.restype = i
     lib.fbf_resolve_window.argtypes = [C.POINTER(fbf_params)]
     lib.fbf_resolve_window.restype = i
+    lib.fbf_set_wait_limit.argtypes = [C.c_longlong]
+    lib.fbf_set_wait_limit.restype = i
     lib.fbf_device_error.argtypes = [C.POINTER(C.c_uint)]
     lib.fbf_device_error.restype = i
     lib.fbf_measure_fp32_peak.argtypes = [i, i, C.POINTER(C.c_double)]
@@ -391,11 +393,21 @@ def fbf_plan_destroy(plan: Plan):
 
 
 def fbf_device_error() -> int:
+    """Read and clear the device error word (synchronises the device); non-zero
+    when a bounded wait inside a kernel gave up (fbf_device_error returns
+    FBF_ERR_TIMEOUT then)."""
     v = C.c_uint(0)
     st = lib.fbf_device_error(C.byref(v))
-    if st != FBF_OK:
+    if st not in (FBF_OK, FBF_ERR_TIMEOUT):
         raise FbfError(st, "fbf_device_error")
     return int(v.value)
+
+
+def fbf_set_wait_limit(polls: int):
+    """Poll limit of the tensor-core kernels' bounded waits (< 0: the default)."""
+    st = lib.fbf_set_wait_limit(int(polls))
+    if st != FBF_OK:
+        raise FbfError(st, "fbf_set_wait_limit")
 
 
 def fbf_measure_fp32_peak(device: int = 0, packed=None) -> float:
