@@ -769,7 +769,7 @@ def run_ours(args):
             flush.zero_()
 
     cfg0 = run_cfg0(fbf, torch, dev, stream, forms, max(20, args.steps), flush_l2_cfg0,
-                    with_oracle=rank == 0 and not args.no_cpu_baseline) if rank == 0 else None
+                    with_oracle=rank == 0 and not args.no_cpu_baseline) if rank == 0 and args.cfg0 else None
 
     hf = per_form[head]
 
@@ -887,6 +887,8 @@ def main():
                     help="also time the 4096^2 exponential-kernel, differentiation and local-range"
                          " workloads (default on; rank 0 only)")
     ap.add_argument("--no-extras", dest="extras", action="store_false")
+    ap.add_argument("--no-cfg0", dest="cfg0", action="store_false", default=True,
+                    help="skip the 256x256 plain-configuration block")
     ap.add_argument("--only", type=int, default=None,
                     help="run a single setting (index into the six) -- for profiling")
     args = ap.parse_args()

@@ -44,8 +44,8 @@ int g_map_next = 0;
 constexpr int kMaxDev = 64;
 std::atomic<int> g_sms[kMaxDev];
 
-// Default poll limit of the bounded waits (about a second of polling on GB300),
-// or the one set by fbf_set_wait_limit.
+// Default poll limit of the tensor-core kernels' bounded waits (about a second
+// of polling on GB300), or the limit set by fbf_set_wait_limit.
 constexpr unsigned int kDefaultPolls = 1u << 22;
 std::atomic<long long> g_polls{-1};
 

@@ -11,15 +11,19 @@
 // of ext row r in a few 8-column units: its demodulation unit (the 8 output
 // columns 8h .. 8h + 7, ext columns Wp + 8h ..) and up to HPG halo units
 // (Wp = W rounded up to a multiple of 8, so that units are 8-column aligned).
-// Per pixel it keeps the exact integer phase index m = n v mod 2T in a
-// register (advanced by v each harmonic) and reads (cos, sin)(pi m / T) from
-// a 16-copy table built once per CTA: no per-harmonic table and no gathers of
-// pixel values.  For each harmonic n:
+// It keeps each pixel's offset into the per-harmonic channel table in a
+// register, and for its demodulation unit the exact integer phase index
+// m = n v mod 2T (advanced by v each harmonic).  For each harmonic n:
 //
-//   modulate  (cos, sin, f cos, f sin)(n w f) of the thread's pixels, the f
-//             channels centred (f - T/2), rounded to 16 bits (hi, and lo =
-//             the residual for the split forms), written with tcgen05.st into
-//             A1[channel][part] (lane = ext row, K = ext column);
+//   table     entry v = 0..255 of harmonic n: d_n (cos, sin, f cos, f sin)
+//             (n w v) with the f channels centred (f - T/2), rounded to 16
+//             bits (hi, and lo = the residual for the split forms), in 16 or 8
+//             copies (conflict-free gathers); built from the exact phase
+//             n v mod 2T and a (cos, sin) table of the 2T phases (built once
+//             per CTA), two harmonics ahead, into one of two buffers;
+//   modulate  one table gather per pixel, byte permutes pairing neighbouring
+//             columns, tcgen05.st into A1[channel][part] (lane = ext row, K =
+//             ext column);
 //   row MMA   D1[lane r][32 c + x] = sum over the K chunks meeting the band of
 //             A1[c] (TMEM) x T_i (16 x 32 Toeplitz block in shared memory);
 //   re-split  thread (r, h) reads D1 of its 8 output columns and 4 channels,
@@ -29,9 +33,10 @@
 //   col MMA   D2[lane r][N = 4 x + slot] = sum over the 8 K chunks of
 //             C (TMEM, lane = ext row r of the output, K = ext row of the
 //             input, entries w[k - r + W]) x B2 chunk: M = 128, N = 128;
-//   demod     thread (r, h) reads D2 of its 8 pixels (all four channels) and
-//             accumulates P += d_n (cos F_r + sin F_i), Q += d_n (cos G_r +
-//             sin G_i) in registers; ext row r is output row r - W, valid for
+//   demod     thread (r, h) reads D2 of its 8 pixels (all four channels, d_n
+//             already folded in) and accumulates P += cos F_r + sin F_i,
+//             Q += cos G_r + sin G_i with (cos, sin)(n w f) in FP32 from the
+//             2T-phase table; ext row r is output row r - W, valid for
 //             W <= r < 128 - W.
 //
 // fhat = P / Q + T/2 is written by the thread itself: no combine pass.  The
@@ -68,7 +73,10 @@ namespace tc2 {
 
 using namespace tc;
 
-constexpr int kNT = 512;           // threads per CTA
+constexpr int kNC = 512;           // compute threads per CTA (four groups of four warps)
+constexpr int kNT = kNC + 128;     // + one warpgroup of MMA / TMA issuers
+constexpr int kRegCompute = 112;   // registers per thread after setmaxnreg: compute warpgroups
+constexpr int kRegIssue = 24;      //   and the issuing warpgroup (4 x 112 + 24 <= 5 x 96 per SM sub-partition)
 constexpr int kLanes = 128;        // TMEM lanes = ext rows per tile
 constexpr int kBX = 32;            // output columns per tile
 constexpr int kCopies = 16;        // trig table copies (conflict-free 8-byte gathers per half warp)
@@ -77,8 +85,10 @@ constexpr int kTrigBytes = (kTrigEntries + 1) * kCopies * 8;  // + the zero entr
 constexpr int kB2Part = kLanes * 128 * 2;  // one part of B2: 128 (K) x 128 (N) x 16 bit
 constexpr int kB2Group = 128 * 2 * 8;      // bytes per 8-row K group of B2 (16 N groups x 128 B)
 constexpr int kBoxW = 144;                 // TMA box: 144 columns (>= 8 + KX) x 128 rows of bytes
-constexpr uint32_t kMaxPolls = 1u << 22;
+constexpr uint32_t kDrainPolls = 1u << 16;  // polls of the exit path's waits (suspending, <= 20 us each)
+constexpr uint32_t kWaitHintNs = 20000;     // suspend hint of one poll
 constexpr int kErrTimeout = 2;             // device error word bit: a bounded wait gave up
+constexpr int kErrTmem = 4;                // device error word bit: TMEM not allocated at column 0
 
 // Half window rounded up to the 8-column units of the tile (ext column Wp + x
 // is output column x).
@@ -88,15 +98,24 @@ __host__ __device__ constexpr int kx_of(int W) { return (wpad(W) + kBX + W + 15)
 // halo units per group for a maximum of KXC row chunks
 __host__ __device__ constexpr int hpg_of(int kxc) { return (2 * kxc - 4 + 3) / 4; }
 
+// Channel table of one harmonic: 257 entries (v = 0..255 and the zero entry
+// 256 for pixels outside the image) of 128 bytes: 16 copies of 8 bytes
+// (single form: hi words of (cos, sin) and (f cos, f sin)) or 8 copies of 16
+// bytes (split forms: the hi and the lo words).
+constexpr int kEntry = 128;
+constexpr int kT16Bytes = 257 * kEntry;
+constexpr int kZeroV = 256;
+
 struct Layout {
-  size_t trig, b2, br, box, bar, bytes;
+  size_t trig, t16, b2, br, box, bar, bytes;
 };
 template <int NSPLIT, int KXC>
 __host__ __device__ constexpr Layout layout() {
   constexpr int kParts = NSPLIT > 1 ? 2 : 1, kWParts = NSPLIT == 3 ? 2 : 1;
   Layout L{};
   L.trig = 0;
-  L.b2 = ((size_t)kTrigBytes + 1023) & ~(size_t)1023;
+  L.t16 = ((size_t)kTrigBytes + 1023) & ~(size_t)1023;
+  L.b2 = (L.t16 + 2 * (size_t)kT16Bytes + 1023) & ~(size_t)1023;
   L.br = L.b2 + (size_t)kParts * kB2Part;
   L.box = (L.br + (size_t)KXC * kWParts * 1024 + 1023) & ~(size_t)1023;
   L.bar = L.box + (size_t)kBoxW * kLanes;
@@ -131,6 +150,37 @@ __device__ __forceinline__ void split2(float a, float b, uint32_t &hi, uint32_t 
   hi = pack2<BF>(a, b);
   const float2 h = unpack2<BF>(hi);
   lo = pack2<BF>(a - h.x, b - h.y);
+}
+typedef unsigned long long u64;
+// Two floats as one f32x2 register pair (first in the low half).
+__device__ __forceinline__ u64 f2(float lo, float hi) {
+  u64 d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+  return d;
+}
+__device__ __forceinline__ u64 u2(uint32_t lo, uint32_t hi) {
+  u64 d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "r"(lo), "r"(hi));
+  return d;
+}
+__device__ __forceinline__ float lo32(u64 x) { return __uint_as_float((uint32_t)x); }
+__device__ __forceinline__ float hi32(u64 x) { return __uint_as_float((uint32_t)(x >> 32)); }
+// d += a * b on both halves (fma.rn.f32x2); mul and sub likewise.
+__device__ __forceinline__ void ffma2(u64 &d, u64 a, u64 b) { asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(a), "l"(b)); }
+__device__ __forceinline__ u64 fmul2(u64 a, u64 b) {
+  u64 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ u64 fsub2(u64 a, u64 b) {
+  u64 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ uint32_t prmt(uint32_t a, uint32_t b, uint32_t sel) {
+  uint32_t d;
+  asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+  return d;
 }
 template <int BF>
 __device__ __forceinline__ unsigned short to16(float x) {
@@ -169,7 +219,16 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constan
   extern __shared__ __align__(1024) unsigned char smem[];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int q = warp & 3, h = warp >> 2;  // TMEM lane quadrant, warp group
+  // warps 0..15 compute (TMEM lane quadrant q, column group h); warps 16..19
+  // only issue (lane 0): warp 16 the column MMAs, warps 17 and 18 the row MMAs
+  // of channels 0, 1 and 2, 3, warp 19 the TMA copies.  One thread issues an
+  // MMA about every 50 cycles, so the small row MMAs take two issuers, and no
+  // compute warp is held up while an issuer waits for room in the MMA queue.
+  const bool compute = warp < kNC / 32;
+  const int q = warp & 3, h = compute ? warp >> 2 : 0;
+  const int iw = warp - kNC / 32;  // issuer warp index 0..3 (compute warps: negative)
+  const bool col_issuer = lane == 0 && iw == 0, row_issuer = lane == 0 && (iw == 1 || iw == 2),
+             tma_issuer = lane == 0 && iw == 3;
   const int r = 32 * q + lane;            // ext row = TMEM lane of this thread
   const int W = a.W, Wp = wpad(W), KX = kx_of(W), kcr = KX / 16;
   const int H = a.H, Wd = a.Wd, BYv = kLanes - 2 * W;
@@ -205,10 +264,10 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constan
     tmem_relinquish();
   }
   if (tid == 0) {
-    mbar_init(mbarR, 4);  // one commit per row-issuing warp
+    mbar_init(mbarR, 2);  // one commit per MMA-issuing warp
     mbar_init(mbarC, 1);
     mbar_init(mbarT, 1);
-    mbar_init(mbarD, 4);  // drain: one commit per MMA-issuing thread
+    mbar_init(mbarD, 3);  // drain: one commit per MMA-issuing thread
     mbar_fence_init();
   }
   // trig table: entry m (cos, sin)(pi m / T) in 16 copies; the zero entry
@@ -233,15 +292,23 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constan
     const int off = (n & 7) * 16 + (n >> 3) * 256 + (k & 7) * 2 + (k >> 3) * 128;
     *reinterpret_cast<unsigned short *>(BR + (size_t)blk * 1024 + off) = v;
   }
+  // zero entries (v = 256) of both channel-table buffers: pixels outside the image
+  if (tid < 2 * kEntry / 16)
+    *reinterpret_cast<uint4 *>(smem + Ly.t16 + (size_t)(tid / (kEntry / 16)) * kT16Bytes + kZeroV * kEntry +
+                               (tid % (kEntry / 16)) * 16) = make_uint4(0u, 0u, 0u, 0u);
   fence_proxy_async_smem();
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
-  const uint32_t tmem = *tmem_base_s;
+  // All 512 columns are allocated, so the allocation starts at lane 0, column 0:
+  // the MMA operands below are compile-time TMEM addresses (issued from uniform
+  // registers).  Anything else is refused as a failed launch.
+  constexpr uint32_t tmem = 0;
+  const bool tmem_ok = *tmem_base_s == 0;
   const uint32_t lane_base = (uint32_t)(32 * q) << 16;
   // Column Toeplitz matrix in TMEM: lane m (output ext row), K = input ext row
   // 16 i + k: w[16 i + k - m + W] inside the band; group h writes chunks 2h, 2h+1.
-  {
+  if (tmem_ok && compute) {
     const int m = r;
 #pragma unroll
     for (int ii = 0; ii < 2; ++ii) {
@@ -285,19 +352,24 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constan
   __syncthreads();
   fence_after_sync();
   if (use_tma && blockIdx.x < a.ntiles) {
-    if (tid == 0) issue_tma(blockIdx.x);
+    if (tma_issuer) issue_tma(blockIdx.x);
     tma_pending = true;
   }
 
-  // ---- per-thread pixel state: per unit and pixel the byte offset of its
-  // current table entry (m * 128 + copy * 8, or the zero entry), its phase
-  // step (v mod 2T) * 128 (two per register), and f - c0 (FP16 pairs, exact).
-  int mo[UPT][8];
-  uint32_t vo[UPT][4];
-  uint32_t fh[UPT][4];
+  // ---- per-thread state.  po: per unit and pixel the byte offset of its entry
+  // in a channel table (v * 128 + this lane's copy, or the zero entry).  For the
+  // demodulation unit, mo: the byte offset of (cos, sin)(pi m / T) in the
+  // 2T-phase table (m * 128 + copy, or its zero entry) for the current
+  // harmonic, and vo: its step (v mod 2T) * 128, two per register.
+  constexpr int kCp = kParts == 2 ? 8 : 16;             // table copies
+  const int copy_off = kParts == 2 ? (lane & 7) * 16 : (lane & 15) * 8;
+  int po[UPT][8];
+  int mo[8];
+  uint32_t vo[4];
   const int copy8 = (lane & (kCopies - 1)) * 8;
   const int lim = twoT * kCopies * 8;  // offset of entry 2T
   auto wrap = [&](int m) -> int { return m >= lim ? m - lim : m; };
+  unsigned char *t16 = smem + Ly.t16;
 
   uint32_t phR = 0, phC = 0, phT = 0;
   bool fail = false;
@@ -314,38 +386,64 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constan
     return ok;
   };
 
-  // ---- modulate harmonic n: table entries of the thread's pixels -> the 16-bit
-  // channels of its units in A1.  The demodulation unit's offsets are advanced by
-  // the demodulation (its entry for harmonic n is read again there), the halo
-  // units' here; `first`: the demodulation unit's offsets already point at n.
-  auto modulate = [&](bool first) {
+  // ---- channel table of harmonic n into buffer b: thread t builds entry
+  // v = t % 256 (half of its copies); bm is the byte offset of its phase
+  // n v mod 2T in the 2T-phase table (advanced here, harmonics in order).
+  const int bv = tid & 255, bhalf = tid >> 8;
+  const int bstep = (bv % twoT) * (kCopies * 8);
+  int bm = 0;
+  auto build_table = [&](int n, int b) {
+    const float2 cs = *reinterpret_cast<const float2 *>(trig + tb + bm + copy8);
+    bm = wrap(bm + bstep);
+    const float dn = a.d[n], fv = (float)bv - c0;
+    const float dc = dn * cs.x, ds = dn * cs.y, dfc = dn * (fv * cs.x), dfs = dn * (fv * cs.y);
+    unsigned char *ent = t16 + (size_t)b * kT16Bytes + bv * kEntry;
+    if constexpr (kParts == 2) {
+      uint4 e;
+      split2<BF>(dc, ds, e.x, e.z);
+      split2<BF>(dfc, dfs, e.y, e.w);
+      // the two threads of an entry write disjoint halves of its copies, each
+      // lane starting at its own copy (neighbouring lanes hit different banks)
+#pragma unroll
+      for (int k = 0; k < kCp / 2; ++k)
+        *reinterpret_cast<uint4 *>(ent + ((lane + bhalf * (kCp / 2) + k) & (kCp - 1)) * 16) = e;
+    } else {
+      const uint2 e = make_uint2(pack2<BF>(dc, ds), pack2<BF>(dfc, dfs));
+#pragma unroll
+      for (int k = 0; k < kCp / 2; ++k)
+        *reinterpret_cast<uint2 *>(ent + ((lane + bhalf * (kCp / 2) + k) & (kCp - 1)) * 8) = e;
+    }
+  };
+
+  // ---- modulate with the table in buffer b: per unit, one gather per pixel,
+  // neighbouring columns paired by byte permutes, four (eight) x4 TMEM stores.
+  auto modulate = [&](int b) {
+    const unsigned char *tb16 = t16 + (size_t)b * kT16Bytes;
 #pragma unroll
     for (int uu = 0; uu < UPT; ++uu) {
       const int u = uu == 0 ? demod_u : halo_unit(uu - 1);
       if (u < 0) continue;
-      float2 cs[8];
-#pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        int off = mo[uu][j];
-        if (uu == 0 && !first) off = wrap(off + (int)((j & 1) ? (vo[uu][j >> 1] >> 16) : (vo[uu][j >> 1] & 0xFFFFu)));
-        cs[j] = *reinterpret_cast<const float2 *>(trig + tb + off);
-        if (uu > 0) mo[uu][j] = wrap(mo[uu][j] + (int)((j & 1) ? (vo[uu][j >> 1] >> 16) : (vo[uu][j >> 1] & 0xFFFFu)));
-      }
       uint32_t ch[4][kParts][4];  // [channel][part][column pair]
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
-        const float2 f2 = __half22float2(*reinterpret_cast<const __half2 *>(&fh[uu][k]));
-        const float c_a = cs[2 * k].x, s_a = cs[2 * k].y, c_b = cs[2 * k + 1].x, s_b = cs[2 * k + 1].y;
         if constexpr (kParts == 2) {
-          split2<BF>(c_a, c_b, ch[0][0][k], ch[0][kParts - 1][k]);
-          split2<BF>(s_a, s_b, ch[1][0][k], ch[1][kParts - 1][k]);
-          split2<BF>(f2.x * c_a, f2.y * c_b, ch[2][0][k], ch[2][kParts - 1][k]);
-          split2<BF>(f2.x * s_a, f2.y * s_b, ch[3][0][k], ch[3][kParts - 1][k]);
+          const uint4 e0 = *reinterpret_cast<const uint4 *>(tb16 + po[uu][2 * k]);
+          const uint4 e1 = *reinterpret_cast<const uint4 *>(tb16 + po[uu][2 * k + 1]);
+          ch[0][0][k] = prmt(e0.x, e1.x, 0x5410);
+          ch[1][0][k] = prmt(e0.x, e1.x, 0x7632);
+          ch[2][0][k] = prmt(e0.y, e1.y, 0x5410);
+          ch[3][0][k] = prmt(e0.y, e1.y, 0x7632);
+          ch[0][kParts - 1][k] = prmt(e0.z, e1.z, 0x5410);
+          ch[1][kParts - 1][k] = prmt(e0.z, e1.z, 0x7632);
+          ch[2][kParts - 1][k] = prmt(e0.w, e1.w, 0x5410);
+          ch[3][kParts - 1][k] = prmt(e0.w, e1.w, 0x7632);
         } else {
-          ch[0][0][k] = pack2<BF>(c_a, c_b);
-          ch[1][0][k] = pack2<BF>(s_a, s_b);
-          ch[2][0][k] = pack2<BF>(f2.x * c_a, f2.y * c_b);
-          ch[3][0][k] = pack2<BF>(f2.x * s_a, f2.y * s_b);
+          const uint2 e0 = *reinterpret_cast<const uint2 *>(tb16 + po[uu][2 * k]);
+          const uint2 e1 = *reinterpret_cast<const uint2 *>(tb16 + po[uu][2 * k + 1]);
+          ch[0][0][k] = prmt(e0.x, e1.x, 0x5410);
+          ch[1][0][k] = prmt(e0.x, e1.x, 0x7632);
+          ch[2][0][k] = prmt(e0.y, e1.y, 0x5410);
+          ch[3][0][k] = prmt(e0.y, e1.y, 0x7632);
         }
       }
 #pragma unroll
@@ -358,20 +456,24 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constan
     tmem_st_wait();
   };
 
-  // ---- row MMAs: lane 0 of warp c issues channel c into D1[32 c ..].
+  // ---- row MMAs: issuer warp 17 + j issues channels 2 j, 2 j + 1 into D1[32 c ..],
+  // the two channels' chunks interleaved.
   auto issue_row = [&]() {
-    const int c = warp;
+    const int c0 = 2 * (iw - 1);
     const uint64_t br_desc = smem_desc(smem_u32(BR), 128, 256);
     constexpr uint32_t idesc = idesc_f16(128, 32, BF, 0, 0);
 #pragma unroll
     for (int i = 0; i < KXC; ++i) {
       if (i < kcr) {
 #pragma unroll
-        for (int pp = 0; pp < NSPLIT; ++pp) {
-          const int ap = pp == 1 ? 1 : 0, bp = pp == 2 ? 1 : 0;
-          mma_ts(tmem + kD1 + (uint32_t)(32 * c), tmem + kA1 + (uint32_t)((c * kParts + ap) * kA1Stride + 8 * i),
-                 br_desc + (uint64_t)(((i * kWParts + bp) * 1024) >> 4), idesc, (i > 0 || pp > 0) ? 1u : 0u);
-        }
+        for (int pp = 0; pp < NSPLIT; ++pp)
+#pragma unroll
+          for (int cc = 0; cc < 2; ++cc) {
+            const int c = c0 + cc, ap = pp == 1 ? 1 : 0, bp = pp == 2 ? 1 : 0;
+            mma_ts(tmem + kD1 + (uint32_t)(32 * c),
+                   tmem + kA1 + (uint32_t)((c * kParts + ap) * kA1Stride + 8 * i),
+                   br_desc + (uint64_t)(((i * kWParts + bp) * 1024) >> 4), idesc, (i > 0 || pp > 0) ? 1u : 0u);
+          }
       }
     }
     mma_commit(mbarR);
@@ -423,158 +525,208 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constan
   };
 
   // ---- demodulate harmonic n: D2 row r, N = 32 h .. 32 h + 31 = pixels x in
-  // [8h, 8h + 8) x slots (G_r, F_r, G_i, F_i); the table entries of harmonic n of
-  // the demodulation unit, then its offsets advance to n + 1.
+  // [8h, 8h + 8) x slots (G_r, F_r, G_i, F_i), d_n already folded in; (cos,
+  // sin)(n w f) of the demodulation unit from the 2T-phase table, whose offsets
+  // then advance to n + 1.
   float P[8], Q[8];
-  auto demod = [&](int n) {
+  auto demod = [&]() {
     uint32_t v[32];
     tmem_ld_x16(tmem + lane_base + kD2 + (uint32_t)(32 * h), *reinterpret_cast<uint32_t(*)[16]>(&v[0]));
     tmem_ld_x16(tmem + lane_base + kD2 + (uint32_t)(32 * h + 16), *reinterpret_cast<uint32_t(*)[16]>(&v[16]));
-    const float dn = a.d[n];
     float2 cs[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      cs[j] = *reinterpret_cast<const float2 *>(trig + tb + mo[0][j]);
-      mo[0][j] = wrap(mo[0][j] + (int)((j & 1) ? (vo[0][j >> 1] >> 16) : (vo[0][j >> 1] & 0xFFFFu)));
+      cs[j] = *reinterpret_cast<const float2 *>(trig + tb + mo[j]);
+      mo[j] = wrap(mo[j] + (int)((j & 1) ? (vo[j >> 1] >> 16) : (vo[j >> 1] & 0xFFFFu)));
     }
     tmem_ld_wait_dep(*reinterpret_cast<uint32_t(*)[16]>(&v[0]));
     tmem_ld_wait_dep(*reinterpret_cast<uint32_t(*)[16]>(&v[16]));
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      const float tc = dn * cs[j].x, ts = dn * cs[j].y;
-      Q[j] = fmaf(tc, __uint_as_float(v[4 * j + 0]), fmaf(ts, __uint_as_float(v[4 * j + 2]), Q[j]));
-      P[j] = fmaf(tc, __uint_as_float(v[4 * j + 1]), fmaf(ts, __uint_as_float(v[4 * j + 3]), P[j]));
+      Q[j] = fmaf(cs[j].x, __uint_as_float(v[4 * j + 0]), fmaf(cs[j].y, __uint_as_float(v[4 * j + 2]), Q[j]));
+      P[j] = fmaf(cs[j].x, __uint_as_float(v[4 * j + 1]), fmaf(cs[j].y, __uint_as_float(v[4 * j + 3]), P[j]));
     }
   };
 
-  bool ok = true;
-  for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
-    int ty0, tx0;
-    tile_org(tile, ty0, tx0);
-    const int iy = ty0 - W + r;  // image row of this thread's ext row
-    if (use_tma) {
-      if (mbar_wait_bounded(mbarT, phT, polls)) {
-        phT ^= 1;
-        tma_pending = false;
-      } else {
-        fail = true;  // the copy is still in flight: the exit path waits for this phase
+  // End of the CTA (each role calls it once, after its loop): when a bounded
+  // wait gave up, let this CTA's MMAs and TMA copy in flight land (full limit)
+  // and record the failure; then release the TMEM.
+  auto finish = [&](bool ok) {
+    if (!ok) {
+      if (col_issuer || row_issuer) mma_commit(mbarD);
+      mbar_wait_suspend(mbarD, 0, kDrainPolls, kWaitHintNs);
+      if (tma_pending) mbar_wait_suspend(mbarT, phT, kDrainPolls, kWaitHintNs);
+      if (tid == 0) atomicOr(x.err, (unsigned)(tmem_ok ? kErrTimeout : kErrTmem));
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(*tmem_base_s, 512);
+  };
+
+  // Issuing warpgroup: the same sequence of CTA barriers as the compute loop
+  // below, issuing at each point what the barrier made ready.
+  bool ok = tmem_ok;
+  if (!compute) {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegIssue));
+    for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
+      if (use_tma) {
+        if (mbar_wait_bounded(mbarT, phT, polls)) {
+          phT ^= 1;
+          tma_pending = false;
+        } else {
+          fail = true;
+        }
+        if (!phase_sync()) {
+          ok = false;
+          break;
+        }
       }
+      if (!phase_sync()) {  // the compute warps have read the box
+        ok = false;
+        break;
+      }
+      if (use_tma && tile + (int)gridDim.x < a.ntiles) {
+        if (tma_issuer) issue_tma(tile + gridDim.x);
+        tma_pending = true;
+      }
+      if (!(ok = phase_sync())) break;  // table of harmonic 0
+      if (!(ok = phase_sync())) break;  // A1 <- harmonic 0
+      if (row_issuer) issue_row();      // R(0)
+      if (!(ok = phase_sync())) break;  // B2 <- harmonic 0
+      for (int n = 0; n < a.K; ++n) {
+        const bool more = n + 1 < a.K;
+        if (col_issuer) issue_col();  // C(n)
+        if (!(ok = phase_sync())) break;  // A1 <- harmonic n + 1
+        if (SHARED) {
+          if (!(ok = phase_sync())) break;  // D2 (= D1) read
+          if (more && row_issuer) issue_row();
+        } else {
+          if (more && row_issuer) issue_row();  // R(n+1)
+        }
+        if (!(ok = phase_sync())) break;  // B2 <- harmonic n + 1
+      }
+    }
+    finish(ok);
+  } else {
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegCompute));
+    for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
+      int ty0, tx0;
+      tile_org(tile, ty0, tx0);
+      const int iy = ty0 - W + r;  // image row of this thread's ext row
+      if (use_tma) {
+        if (mbar_wait_bounded(mbarT, phT, polls)) {
+          phT ^= 1;
+          tma_pending = false;
+        } else {
+          fail = true;  // the copy is still in flight: the exit path waits for this phase
+        }
+        if (!phase_sync()) {
+          ok = false;
+          break;
+        }
+      }
+      // ---- load the thread's pixels: REFLECT mirrors (repeatedly, for windows
+      // wider than the image); TRUNCATE marks pixels outside the image, whose
+      // channels are zero (the zero table entries, no phase step).
+      {
+        const int bx0 = box_x0(tx0), by0 = ty0 - W;
+        bool row_in = iy >= 0 && iy < H;
+        const int sy = reflect ? reflect_index(iy, H) : iy;
+  #pragma unroll
+        for (int uu = 0; uu < UPT; ++uu) {
+          const int u = uu == 0 ? demod_u : halo_unit(uu - 1);
+          int vm[8];
+  #pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int ix = tx0 - Wp + 8 * (u < 0 ? 0 : u) + j;
+            bool in = row_in && ix >= 0 && ix < Wd;
+            int sx = ix;
+            if (reflect) {
+              sx = reflect_index(ix, Wd);
+              in = true;
+            }
+            int v = 0;
+            if (in && u >= 0) {
+              const int by = (reflect ? sy : iy) - by0, bx = sx - bx0;
+              if (use_tma && by >= 0 && by < kLanes && bx >= 0 && bx < kBoxW)
+                v = box[by * kBoxW + bx];
+              else
+                v = __ldg(static_cast<const unsigned char *>(a.in) + (size_t)(reflect ? sy : iy) * a.in_pitch + sx);
+            }
+            const bool valid = in && u >= 0;
+            po[uu][j] = (valid ? v : kZeroV) * kEntry + copy_off;
+            if (uu == 0) {
+              mo[j] = valid ? copy8 : copy8 - kCopies * 8;  // entry m = 0, or the zero entry
+              vm[j] = valid ? (v % twoT) * (kCopies * 8) : 0;
+            }
+          }
+          if (uu == 0) {
+  #pragma unroll
+            for (int k = 0; k < 4; ++k) vo[k] = (uint32_t)vm[2 * k] | ((uint32_t)vm[2 * k + 1] << 16);
+          }
+        }
+      }
+      // every thread has read the box: the next tile's copy may overwrite it
+      fence_proxy_async_smem();
       if (!phase_sync()) {
         ok = false;
         break;
       }
-    }
-    // ---- load the thread's pixels: REFLECT mirrors (repeatedly, for windows
-    // wider than the image); TRUNCATE marks pixels outside the image, whose
-    // channels are zero (the zero table entry, f = 0, no phase step).
-    {
-      const int bx0 = box_x0(tx0), by0 = ty0 - W;
-      bool row_in = iy >= 0 && iy < H;
-      const int sy = reflect ? reflect_index(iy, H) : iy;
-#pragma unroll
-      for (int uu = 0; uu < UPT; ++uu) {
-        const int u = uu == 0 ? demod_u : halo_unit(uu - 1);
-        float fv[8];
-        int vm[8];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int ix = tx0 - Wp + 8 * (u < 0 ? 0 : u) + j;
-          bool in = row_in && ix >= 0 && ix < Wd;
-          int sx = ix;
-          if (reflect) {
-            sx = reflect_index(ix, Wd);
-            in = true;
-          }
-          int v = 0;
-          if (in && u >= 0) {
-            const int by = (reflect ? sy : iy) - by0, bx = sx - bx0;
-            if (use_tma && by >= 0 && by < kLanes && bx >= 0 && bx < kBoxW)
-              v = box[by * kBoxW + bx];
-            else
-              v = __ldg(static_cast<const unsigned char *>(a.in) + (size_t)(reflect ? sy : iy) * a.in_pitch + sx);
-          }
-          const bool valid = in && u >= 0;
-          mo[uu][j] = valid ? copy8 : copy8 - kCopies * 8;  // entry m = 0, or the zero entry
-          vm[j] = valid ? (v % twoT) * (kCopies * 8) : 0;
-          fv[j] = valid ? (float)v - c0 : 0.f;
-        }
-#pragma unroll
-        for (int k = 0; k < 4; ++k) {
-          vo[uu][k] = (uint32_t)vm[2 * k] | ((uint32_t)vm[2 * k + 1] << 16);
-          const __half2 f2 = __floats2half2_rn(fv[2 * k], fv[2 * k + 1]);
-          fh[uu][k] = *reinterpret_cast<const uint32_t *>(&f2);
-        }
-      }
-    }
-    // every thread has read the box: the next tile's copy may overwrite it
-    fence_proxy_async_smem();
-    if (!phase_sync()) {
-      ok = false;
-      break;
-    }
-    if (use_tma && tile + (int)gridDim.x < a.ntiles) {
-      if (tid == 0) issue_tma(tile + gridDim.x);
-      tma_pending = true;
-    }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) P[j] = Q[j] = 0.f;
+      if (use_tma && tile + (int)gridDim.x < a.ntiles) tma_pending = true;
+  #pragma unroll
+      for (int j = 0; j < 8; ++j) P[j] = Q[j] = 0.f;
 
-    // ---- prologue: harmonic 0 through the row pass and the re-split
-    modulate(true);
-    if (!(ok = phase_sync())) break;
-    if (lane == 0 && warp < 4) issue_row();
-    wait_bar(mbarR, phR);
-    resplit();
-    if (!(ok = phase_sync())) break;
-
-    for (int n = 0; n < a.K; ++n) {
-      const bool more = n + 1 < a.K;
-      if (tid == 0) issue_col();           // C(n): B2 -> D2
-      if (more) modulate(false);           // A1 <- harmonic n + 1
+      // ---- prologue: the tables of harmonics 0 and 1; harmonic 0 through the row
+      // pass and the re-split.  The table of harmonic n is in buffer n % 2.
+      bm = 0;
+      build_table(0, 0);
       if (!(ok = phase_sync())) break;
-      if (SHARED) {
-        wait_bar(mbarC, phC);
-        demod(n);
+      modulate(0);
+      if (!(ok = phase_sync())) break;
+      if (a.K > 1) build_table(1, 1);
+      wait_bar(mbarR, phR);
+      resplit();
+      if (!(ok = phase_sync())) break;
+
+      for (int n = 0; n < a.K; ++n) {
+        const bool more = n + 1 < a.K;
+        if (more) modulate((n + 1) & 1);   // A1 <- harmonic n + 1 (while C(n): B2 -> D2 runs)
         if (!(ok = phase_sync())) break;
-        if (more) {
-          if (lane == 0 && warp < 4) issue_row();  // R(n+1): A1 -> D (= D2, read)
-          wait_bar(mbarR, phR);
-          resplit();
+        // the table of n + 2 replaces that of n (read by the modulation of n, done)
+        if (SHARED) {
+          if (n + 2 < a.K) build_table(n + 2, n & 1);
+          wait_bar(mbarC, phC);
+          demod();
+          if (!(ok = phase_sync())) break;
+          if (more) {  // R(n+1): A1 -> D (= D2, read)
+            wait_bar(mbarR, phR);
+            resplit();
+          }
+        } else {
+          // R(n+1): A1 -> D1 runs meanwhile
+          if (n + 2 < a.K) build_table(n + 2, n & 1);
+          wait_bar(mbarC, phC);
+          demod();
+          if (more) {
+            wait_bar(mbarR, phR);  // C(n) is complete too: B2 may be rewritten
+            resplit();
+          }
         }
-      } else {
-        if (more && lane == 0 && warp < 4) issue_row();  // R(n+1): A1 -> D1
-        wait_bar(mbarC, phC);
-        demod(n);
-        if (more) {
-          wait_bar(mbarR, phR);  // C(n) is complete too: B2 may be rewritten
-          resplit();
-        }
+        if (!(ok = phase_sync())) break;
       }
-      if (!(ok = phase_sync())) break;
-    }
-    if (!ok) break;
+      if (!ok) break;
 
-    // ---- fhat = P / Q + c0 for this thread's 8 pixels of output row iy
-    if (r >= W && r < kLanes - W && iy < H) {
-      float *orow = reinterpret_cast<float *>(reinterpret_cast<char *>(a.out) + (size_t)iy * a.out_pitch);
-      const int x0 = tx0 + 8 * h;
-#pragma unroll
-      for (int j = 0; j < 8; ++j)
-        if (x0 + j < Wd) orow[x0 + j] = P[j] / Q[j] + c0;
+      // ---- fhat = P / Q + c0 for this thread's 8 pixels of output row iy
+      if (r >= W && r < kLanes - W && iy < H) {
+        float *orow = reinterpret_cast<float *>(reinterpret_cast<char *>(a.out) + (size_t)iy * a.out_pitch);
+        const int x0 = tx0 + 8 * h;
+  #pragma unroll
+        for (int j = 0; j < 8; ++j)
+          if (x0 + j < Wd) orow[x0 + j] = P[j] / Q[j] + c0;
+      }
     }
+    finish(ok);
   }
-
-  if (!ok) {
-    // A bounded wait gave up: let this CTA's MMAs and TMA copy in flight land
-    // (full limit) before the TMEM is released and the CTA exits.
-    if (lane == 0 && warp < 4) mma_commit(mbarD);
-    if (!mbar_wait_bounded(mbarD, 0, kMaxPolls)) fail = true;
-    if (tma_pending) mbar_wait_bounded(mbarT, phT, kMaxPolls);
-    if (tid == 0) atomicOr(x.err, (unsigned)kErrTimeout);
-  }
-  fence_before_sync();
-  __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, 512);
 }
 
 }  // namespace tc2

@@ -159,6 +159,26 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *m, uint32_t parity) {
       : "memory");
   return ok != 0;
 }
+// One try_wait that may suspend the thread for up to `hint_ns` nanoseconds
+// (a hint; the hardware may return earlier) while the phase is incomplete.
+__device__ __forceinline__ bool mbar_try_wait_hint(uint64_t *m, uint32_t parity, uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(m)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait with suspending polls: at most max_polls try_waits of up to
+// hint_ns each (a waiting thread issues almost no instructions).
+__device__ __forceinline__ bool mbar_wait_suspend(uint64_t *m, uint32_t parity, uint32_t max_polls,
+                                                  uint32_t hint_ns) {
+  for (uint32_t i = 0; i < max_polls; ++i)
+    if (mbar_try_wait_hint(m, parity, hint_ns)) return true;
+  return false;
+}
 // Bounded wait for the phase with the given parity; false when the poll limit
 // is reached (the caller records an error and abandons the tile).
 __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *m, uint32_t parity, uint32_t max_polls) {
