@@ -227,12 +227,10 @@ def form_kernel(form: str, W: int) -> str:
 TC_NSPLIT = {"tc_fp16": 2, "tc_bf16": 3, "tc_fp16_single": 1}
 
 
-TC2_WMAX = {"tc_fp16_single": 48, "tc_fp16": 24, "tc_bf16": 16}  # windows of the second layout
-
-
 def tc_layout(form: str, W: int) -> str:
-    """Which tensor-core layout runs the form at this window (T <= 255)."""
-    return "tc2" if W <= TC2_WMAX[form] else "tc1"
+    """Which tensor-core layout runs the form at this window (T <= 255): the
+    second for the single form, and for the split forms beyond W = 32."""
+    return "tc2" if form == "tc_fp16_single" or W > 32 else "tc1"
 
 
 def tc_issued_flops(K: int, W: int, form: str) -> float:
@@ -448,6 +446,40 @@ def run_cfg0(fbf, torch, dev, stream, forms, steps, flush, with_oracle):
             row["rms_err_vs_oracle"] = round(float(np.sqrt(np.mean((got - ref) ** 2))), 7)
             row["max_err_vs_direct_eq1"] = round(float(np.max(np.abs(got - direct))), 5)
         res["runs"].append(row)
+    return res
+
+
+def run_wide(fbf, torch, dev, stream, forms, steps, flush, with_oracle, slab_rows=32):
+    """Windows beyond 32 (Table 1 of Sec. V runs sigma_s up to 12): the 2048x2048
+    image (seed 1100) at sigma_s = 12 (W = 36), sigma_r in {20, 40}, eps = 1e-3,
+    every form, with the max error against the FP64 oracle on rows 0..slab_rows-1
+    and the FIR-equivalent TFLOP/s."""
+    from paper_1603_08081_gb300.synth import make_image
+
+    img = make_image(H, W_IMG, SEED)
+    x = torch.from_numpy(img).to(dev)
+    y = torch.empty((H, W_IMG), dtype=torch.float32, device=dev)
+    res = {"workload": "2048x2048 u8 synthetic (seed 1100), sigma_s=12 (W=36), eps=1e-3, reflect", "runs": []}
+    for sr in (20.0, 40.0):
+        c = fbf.fbf_fit_coeffs("gaussian", sr, T, EPS)
+        ref = None
+        if with_oracle:
+            import oracle as O
+
+            w1 = O.weights_1d(O.SPATIAL_GAUSSIAN, 12.0, 36)
+            ref = O.alg1(img.astype(np.float64), w1, O.BORDER_REFLECT, np.array(c.coefficients), T,
+                         rows=(0, slab_rows))[0]
+        for f in forms:
+            p = fbf.make_params(c, 12.0, 0, "gaussian", "reflect", f)
+            ms = _timed_steps(torch, dev, stream, lambda: fbf.fbf_filter(p, x, out=y, stream=stream), steps, flush)
+            alg = algorithmic_flops_per_pixel(c.K, 36) * H * W_IMG / (ms * 1e-3) / 1e12
+            row = {"sigma_r": sr, "K": c.K, "W": 36, "form": f, "ms": round(ms, 4),
+                   "mpix_s": round(H * W_IMG / ms / 1e3, 1), "fir_tflops_algorithmic": round(alg, 2)}
+            if ref is not None:
+                torch.cuda.synchronize(dev)
+                got = y[:slab_rows].cpu().numpy().astype(np.float64)
+                row["max_err_vs_oracle"] = round(float(np.max(np.abs(got - ref))), 6)
+            res["runs"].append(row)
     return res
 
 
@@ -758,6 +790,8 @@ def run_ours(args):
             with torch.cuda.stream(stream):
                 flush.zero_()
 
+        extras["wide_window_2048"] = run_wide(fbf, torch, dev, stream, forms, ex_steps, flush_l2,
+                                              not args.no_cpu_baseline)
         extras["exponential_4096"] = run_exponential(fbf, torch, dev, stream, ex_steps, flush_l2,
                                                      not args.no_cpu_baseline)
         extras["differentiation"] = run_differentiation(fbf, torch, dev, stream, ex_steps,

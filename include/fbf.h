@@ -82,7 +82,7 @@ typedef enum {
 } fbf_form;
 
 #define FBF_KMAX 256 /* maximum number of coefficients K                 */
-#define FBF_WMAX 32  /* maximum half window W (taps 2W+1 <= 65)           */
+#define FBF_WMAX 48  /* maximum half window W (taps 2W+1 <= 97)           */
 
 /* Fitted range-kernel approximation, eq. (6): phi_N(t) = sum_k d[k] cos(k omega t). */
 typedef struct {
@@ -194,7 +194,7 @@ typedef struct {
   size_t in_pitch, out_pitch; /* bytes                                                   */
   fbf_spatial_kernel spatial;
   double sigma_s;
-  int W;                      /* half window; <= 0 selects ceil(3 sigma_s); <= 32        */
+  int W;                      /* half window; <= 0 selects ceil(3 sigma_s); <= FBF_WMAX  */
   fbf_range_kernel range;
   double sigma_r, T, eps;     /* as fbf_fit_coeffs (T an integer for uint8 images)       */
   int K_fixed, levels;        /* as fbf_fit_coeffs                                       */
@@ -220,7 +220,8 @@ typedef enum {
  * per image in `form`) and the two per-image schedules with their launches
  * spread over four concurrent graph branches (largest images first, each to
  * the least loaded branch), so that small images and the last wave of one
- * image's tiles share the GPU with other images.  form FP32: PERSISTENT,
+ * image's tiles share the GPU with other images (PERSISTENT needs every
+ * W <= 32).  form FP32: PERSISTENT,
  * PERSISTENT_WIDE and both PER_IMAGE_FP32 schedules; AUTO: all six (per image
  * as fbf_filter's AUTO); a tensor-core form: both PER_IMAGE_FORM schedules.
  * The concurrent schedules need images whose outputs overlap no other

@@ -11,7 +11,7 @@
 //                    and coefficients to shared memory and runs the fused
 //                    FP32 tile body with run-time taps.  Items are sorted by
 //                    estimated cost (K x taps per tile, largest first).  32 x
-//                    192 tiles, any W <= 32;
+//                    192 tiles, any W <= 32 (a candidate only then);
 //   PERSISTENT_WIDE  the same with 64 x 96 tiles (when every W <= 16);
 //   PER_IMAGE_FP32   one launch per image of the single-image FP32 kernel
 //                    (compile-time tap counts, running sums for box windows);
@@ -343,7 +343,7 @@ static fbf_status plan_create(const fbf_image_desc *descs, int n, fbf_form form,
     kinds.push_back(FBF_SCHEDULE_PER_IMAGE_FORM);
     kinds.push_back(FBF_SCHEDULE_PER_IMAGE_FORM_STREAMS);
   } else {
-    kinds.push_back(FBF_SCHEDULE_PERSISTENT);
+    if (wmax <= 32) kinds.push_back(FBF_SCHEDULE_PERSISTENT);  // its 32 x 192 tiles stage W <= 32
     if (wmax <= 16) kinds.push_back(FBF_SCHEDULE_PERSISTENT_WIDE);
     kinds.push_back(FBF_SCHEDULE_PER_IMAGE_FP32);
     kinds.push_back(FBF_SCHEDULE_PER_IMAGE_FP32_STREAMS);

@@ -18,13 +18,13 @@ __device__ __forceinline__ int reflect_index(int i, int n) {
 }
 
 // Stage the halo tile whose ext pixel (0, 0) is image pixel (y0, x0) into
-// tileT[ex * sx + ey * sy], for ey < nrows and ex < ncols.  Each
+// tileT[ex * sx + ey * sy], for ey < nrows and ex < ncols <= 32 * CG.  Each
 // entry is (pixel value) * scale -- the byte offset of that value's row in a
 // channel table -- or `sentinel` for padding (ey >= rows_valid or ex >=
 // cols_valid) and, under TRUNCATE, for pixels outside the image.  Warps take
 // rows, lanes take columns (coalesced global reads; column-major writes, sy = 1,
 // hit distinct banks when sx / 2 is odd); up to 8 loads per thread are in flight.
-template <int NT>
+template <int NT, int CG = 4>
 __device__ __forceinline__ void stage_tile(const unsigned char *__restrict__ in, size_t pitch, int H, int Wd,
                                            int border, int y0, int x0, int rows_valid, int cols_valid,
                                            int nrows, int ncols, unsigned short *tileT, int sx, int sy,
@@ -33,7 +33,7 @@ __device__ __forceinline__ void stage_tile(const unsigned char *__restrict__ in,
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool reflect = border == FBF_BORDER_REFLECT;
   for (int ey0 = warp; ey0 < nrows; ey0 += 2 * NW) {
-    unsigned short v[2][4];
+    unsigned short v[2][CG];
 #pragma unroll
     for (int rr = 0; rr < 2; ++rr) {
       const int ey = ey0 + rr * NW;
@@ -45,7 +45,7 @@ __device__ __forceinline__ void stage_tile(const unsigned char *__restrict__ in,
         row_ok = row_ok && iy >= 0 && iy < H;
       const unsigned char *rowp = in + (size_t)(row_ok ? iy : 0) * pitch;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
+      for (int k = 0; k < CG; ++k) {
         const int ex = lane + 32 * k;
         int ix = x0 + ex;
         bool ok = row_ok && ex < cols_valid;
@@ -61,7 +61,7 @@ __device__ __forceinline__ void stage_tile(const unsigned char *__restrict__ in,
       const int ey = ey0 + rr * NW;
       if (ey < nrows) {
 #pragma unroll
-        for (int k = 0; k < 4; ++k) {
+        for (int k = 0; k < CG; ++k) {
           const int ex = lane + 32 * k;
           if (ex < ncols) tileT[ex * sx + ey * sy] = v[rr][k];
         }

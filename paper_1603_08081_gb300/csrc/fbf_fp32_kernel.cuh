@@ -241,8 +241,8 @@ __device__ __forceinline__ void k1_tile(const K1View &a, int ty0, int tx0, unsig
   }
 
   // Stage the halo tile, transposed: tileT[ex * PT + ey] (byte offsets into a table buffer).
-  static_assert(BX + 2 * WCAP + kRun <= 128, "staging covers at most 128 ext columns");
-  stage_tile<NT>(a.in, a.in_pitch, H, Wd, a.border, ty0 - W, tx0 - W,
+  constexpr int kCG = (BX + 2 * WCAP + kRun + 31) / 32;  // column groups of 32 staged
+  stage_tile<NT, kCG>(a.in, a.in_pitch, H, Wd, a.border, ty0 - W, tx0 - W,
                  Ly.HY, Ly.HX, Ly.HYP, Ly.HXA, tileT, Ly.PT, 1, (unsigned short)(kCopies * sizeof(float4)),
                  (unsigned short)(kSentinel * kCopies * sizeof(float4)));
   build_lut(lut, 0, a.twoT, a.T, tid, NT);
@@ -359,7 +359,9 @@ fbf_status launch_cfg(const FilterArgs &a0, cudaStream_t s) {
 }  // namespace
 
 // Tile shapes: 64 x 96 outputs with two table buffers for W <= 16 (<= 227 KB
-// of shared memory), 32 x 192 with one buffer for 17 <= W <= 32 (<= 222 KB).
+// of shared memory), 32 x 192 with one buffer for 17 <= W <= 32 (<= 222 KB),
+// and for 33 <= W <= 48 32 x 128 with one buffer and a run-time tap count
+// (launch_wide, 213 KB).
 // Both keep the padded halo rows of the row pass at <= 1.33x the output rows
 // and split the row and column units evenly over 8 warps.  The tap count is a
 // template parameter (one instantiation per W), so both FIR loops unroll
@@ -370,6 +372,12 @@ fbf_status launch_w(const FilterArgs &a, cudaStream_t s) {
     return launch_cfg<64, 96, 256, 2, 16, 2 * Wv + 1>(a, s);
   else
     return launch_cfg<32, 192, 256, 1, 32, 2 * Wv + 1>(a, s);
+}
+
+// Windows 33..48: one instantiation with run-time taps (FIR or box sums).
+inline fbf_status launch_wide(const FilterArgs &a, cudaStream_t s) {
+  if (a.box) return launch_cfg<32, 128, 256, 1, 48, 0, 1>(a, s);
+  return launch_cfg<32, 128, 256, 1, 48, 0, 0>(a, s);
 }
 
 #define FBF_K1_CASE(Wv) \

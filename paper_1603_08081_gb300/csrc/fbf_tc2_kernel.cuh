@@ -15,8 +15,8 @@
 // register, and for its demodulation unit the exact integer phase index
 // m = n v mod 2T (advanced by v each harmonic).  For each harmonic n:
 //
-//   table     entry v = 0..255 of harmonic n: d_n (cos, sin, f cos, f sin)
-//             (n w v) with the f channels centred (f - T/2), rounded to 16
+//   table     entry v = 0..255 of harmonic n: (cos, sin, f cos, f sin)(n w v)
+//             (times d_n in the split forms) with the f channels centred (f - T/2), rounded to 16
 //             bits (hi, and lo = the residual for the split forms), in 16 or 8
 //             copies (conflict-free gathers); built from the exact phase
 //             n v mod 2T and a (cos, sin) table of the 2T phases (built once
@@ -33,11 +33,11 @@
 //   col MMA   D2[lane r][N = 4 x + slot] = sum over the 8 K chunks of
 //             C (TMEM, lane = ext row r of the output, K = ext row of the
 //             input, entries w[k - r + W]) x B2 chunk: M = 128, N = 128;
-//   demod     thread (r, h) reads D2 of its 8 pixels (all four channels, d_n
-//             already folded in) and accumulates P += cos F_r + sin F_i,
-//             Q += cos G_r + sin G_i with (cos, sin)(n w f) in FP32 from the
-//             2T-phase table; ext row r is output row r - W, valid for
-//             W <= r < 128 - W.
+//   demod     thread (r, h) reads D2 of its 8 pixels (all four channels) and
+//             accumulates P += d_n (cos F_r + sin F_i), Q += d_n (cos G_r +
+//             sin G_i) with (cos, sin)(n w f) in FP32 from the 2T-phase table
+//             (d_n already in D2 for the split forms); ext row r is output row
+//             r - W, valid for W <= r < 128 - W.
 //
 // fhat = P / Q + T/2 is written by the thread itself: no combine pass.  The
 // column Toeplitz matrix lives in TMEM (written once per CTA), so the column
@@ -79,9 +79,12 @@ constexpr int kRegCompute = 112;   // registers per thread after setmaxnreg: com
 constexpr int kRegIssue = 24;      //   and the issuing warpgroup (4 x 112 + 24 <= 5 x 96 per SM sub-partition)
 constexpr int kLanes = 128;        // TMEM lanes = ext rows per tile
 constexpr int kBX = 32;            // output columns per tile
-constexpr int kCopies = 16;        // trig table copies (conflict-free 8-byte gathers per half warp)
 constexpr int kTrigEntries = 510;  // 2T <= 510 (T <= 255)
-constexpr int kTrigBytes = (kTrigEntries + 1) * kCopies * 8;  // + the zero entry in front
+// Copies of the 2T-phase table: 16 (conflict-free 8-byte gathers per half warp)
+// for the single form, 8 for the split forms (their larger B2 and channel
+// tables leave no room for 16).
+__host__ __device__ constexpr int trig_copies(int nsplit) { return nsplit > 1 ? 8 : 16; }
+__host__ __device__ constexpr int trig_bytes(int nsplit) { return (kTrigEntries + 1) * trig_copies(nsplit) * 8; }
 constexpr int kB2Part = kLanes * 128 * 2;  // one part of B2: 128 (K) x 128 (N) x 16 bit
 constexpr int kB2Group = 128 * 2 * 8;      // bytes per 8-row K group of B2 (16 N groups x 128 B)
 constexpr int kBoxW = 144;                 // TMA box: 144 columns (>= 8 + KX) x 128 rows of bytes
@@ -114,7 +117,7 @@ __host__ __device__ constexpr Layout layout() {
   constexpr int kParts = NSPLIT > 1 ? 2 : 1, kWParts = NSPLIT == 3 ? 2 : 1;
   Layout L{};
   L.trig = 0;
-  L.t16 = ((size_t)kTrigBytes + 1023) & ~(size_t)1023;
+  L.t16 = ((size_t)trig_bytes(NSPLIT) + 1023) & ~(size_t)1023;
   L.b2 = (L.t16 + 2 * (size_t)kT16Bytes + 1023) & ~(size_t)1023;
   L.br = L.b2 + (size_t)kParts * kB2Part;
   L.box = (L.br + (size_t)KXC * kWParts * 1024 + 1023) & ~(size_t)1023;
@@ -200,12 +203,19 @@ __device__ __forceinline__ float from16(unsigned short x) {
 // BF: 0 = FP16, 1 = BF16 operands.  NSPLIT: 1 = data hi x weights hi; 2 = data
 // hi/lo x weights hi; 3 = plus data hi x weights lo.  KXC: row chunks the
 // instantiation is sized for (KX = 16 KXC ext columns: W <= 16 for 4, 24 for
-// 5, 32 for 6, 48 for 8).  SHARED: D1 and D2 share their TMEM columns.
-template <int BF, int NSPLIT, int KXC, int SHARED>
+// 5, 32 for 6, 48 for 8).  SHARED: D1 and D2 share their TMEM columns.  SEQ
+// (split forms, with SHARED): A1 holds one data part at a time -- the row MMAs
+// of a harmonic run in two rounds, hi part then lo part, with the lo part
+// modulated into A1 between them -- so that wide windows fit the TMEM.
+template <int BF, int NSPLIT, int KXC, int SHARED, int SEQ = 0>
 __global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constant__ FilterArgs a,
                                                              const __grid_constant__ CUtensorMap tmap,
                                                              const Tc2Extra x) {
   constexpr int kParts = NSPLIT > 1 ? 2 : 1;   // data parts (hi, lo)
+  constexpr int kA1Parts = SEQ ? 1 : kParts;   // data parts held in A1 at a time
+  constexpr int kCopies = trig_copies(NSPLIT);
+  constexpr bool kFold = kParts == 2;          // d_n folded into the channel table (split forms)
+  static_assert(!SEQ || (kParts == 2 && SHARED), "the sequential schedule is for split forms with D1 = D2");
   constexpr int kWParts = NSPLIT == 3 ? 2 : 1; // weight parts (hi, lo)
   constexpr int HPG = hpg_of(KXC);             // halo units per thread at most
   constexpr int UPT = 1 + HPG;                 // units per thread
@@ -213,7 +223,7 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constan
   constexpr uint32_t kT = 0;                   // column Toeplitz matrix (64 columns per weight part)
   constexpr uint32_t kA1 = 64 * kWParts;
   constexpr uint32_t kD1 = SHARED ? 384 : 256, kD2 = 384;
-  static_assert(kA1 + 4 * kParts * kA1Stride <= kD1, "A1 fits below D1");
+  static_assert(kA1 + 4 * kA1Parts * kA1Stride <= kD1, "A1 fits below D1");
   static_assert(KXC >= 2 && KXC <= 8, "row chunks");
   constexpr Layout Ly = layout<NSPLIT, KXC>();
   extern __shared__ __align__(1024) unsigned char smem[];
@@ -395,7 +405,11 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constan
   auto build_table = [&](int n, int b) {
     const float2 cs = *reinterpret_cast<const float2 *>(trig + tb + bm + copy8);
     bm = wrap(bm + bstep);
-    const float dn = a.d[n], fv = (float)bv - c0;
+    // the split forms fold d_n into the table; the single form keeps the plain
+    // channels (rounding d_n-scaled values to FP16 once doubles its error: an
+    // FP64 emulation of both on the 2048^2 image, sigma_s = 3, sigma_r = 40
+    // gives 0.043 against 0.020 gray) and multiplies by d_n when demodulating
+    const float dn = kFold ? a.d[n] : 1.f, fv = (float)bv - c0;
     const float dc = dn * cs.x, ds = dn * cs.y, dfc = dn * (fv * cs.x), dfs = dn * (fv * cs.y);
     unsigned char *ent = t16 + (size_t)b * kT16Bytes + bv * kEntry;
     if constexpr (kParts == 2) {
@@ -416,27 +430,37 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constan
   };
 
   // ---- modulate with the table in buffer b: per unit, one gather per pixel,
-  // neighbouring columns paired by byte permutes, four (eight) x4 TMEM stores.
-  auto modulate = [&](int b) {
+  // neighbouring columns paired by byte permutes, two-column TMEM stores.  SEQ:
+  // only data part `part` (0 = hi, 1 = lo), into the one set of A1 regions.
+  auto modulate = [&](int b, int part) {
     const unsigned char *tb16 = t16 + (size_t)b * kT16Bytes;
 #pragma unroll
     for (int uu = 0; uu < UPT; ++uu) {
       const int u = uu == 0 ? demod_u : halo_unit(uu - 1);
       if (u < 0) continue;
-      uint32_t ch[4][kParts][4];  // [channel][part][column pair]
+      uint32_t ch[4][kA1Parts][4];  // [channel][part held][column pair]
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         if constexpr (kParts == 2) {
           const uint4 e0 = *reinterpret_cast<const uint4 *>(tb16 + po[uu][2 * k]);
           const uint4 e1 = *reinterpret_cast<const uint4 *>(tb16 + po[uu][2 * k + 1]);
-          ch[0][0][k] = prmt(e0.x, e1.x, 0x5410);
-          ch[1][0][k] = prmt(e0.x, e1.x, 0x7632);
-          ch[2][0][k] = prmt(e0.y, e1.y, 0x5410);
-          ch[3][0][k] = prmt(e0.y, e1.y, 0x7632);
-          ch[0][kParts - 1][k] = prmt(e0.z, e1.z, 0x5410);
-          ch[1][kParts - 1][k] = prmt(e0.z, e1.z, 0x7632);
-          ch[2][kParts - 1][k] = prmt(e0.w, e1.w, 0x5410);
-          ch[3][kParts - 1][k] = prmt(e0.w, e1.w, 0x7632);
+          if constexpr (SEQ) {
+            const uint32_t a0 = part ? e0.z : e0.x, a1 = part ? e1.z : e1.x;
+            const uint32_t b0 = part ? e0.w : e0.y, b1 = part ? e1.w : e1.y;
+            ch[0][0][k] = prmt(a0, a1, 0x5410);
+            ch[1][0][k] = prmt(a0, a1, 0x7632);
+            ch[2][0][k] = prmt(b0, b1, 0x5410);
+            ch[3][0][k] = prmt(b0, b1, 0x7632);
+          } else {
+            ch[0][0][k] = prmt(e0.x, e1.x, 0x5410);
+            ch[1][0][k] = prmt(e0.x, e1.x, 0x7632);
+            ch[2][0][k] = prmt(e0.y, e1.y, 0x5410);
+            ch[3][0][k] = prmt(e0.y, e1.y, 0x7632);
+            ch[0][kA1Parts - 1][k] = prmt(e0.z, e1.z, 0x5410);
+            ch[1][kA1Parts - 1][k] = prmt(e0.z, e1.z, 0x7632);
+            ch[2][kA1Parts - 1][k] = prmt(e0.w, e1.w, 0x5410);
+            ch[3][kA1Parts - 1][k] = prmt(e0.w, e1.w, 0x7632);
+          }
         } else {
           const uint2 e0 = *reinterpret_cast<const uint2 *>(tb16 + po[uu][2 * k]);
           const uint2 e1 = *reinterpret_cast<const uint2 *>(tb16 + po[uu][2 * k + 1]);
@@ -449,16 +473,18 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constan
 #pragma unroll
       for (int c = 0; c < 4; ++c)
 #pragma unroll
-        for (int p = 0; p < kParts; ++p)
-          tmem_st_x4(tmem + lane_base + kA1 + (uint32_t)((c * kParts + p) * kA1Stride + 4 * u), ch[c][p][0],
-                     ch[c][p][1], ch[c][p][2], ch[c][p][3]);
+        for (int p = 0; p < kA1Parts; ++p) {
+          const uint32_t ta = tmem + lane_base + kA1 + (uint32_t)((c * kA1Parts + p) * kA1Stride + 4 * u);
+          tmem_st_x2(ta, ch[c][p][0], ch[c][p][1]);
+          tmem_st_x2(ta + 2, ch[c][p][2], ch[c][p][3]);
+        }
     }
     tmem_st_wait();
   };
 
   // ---- row MMAs: issuer warp 17 + j issues channels 2 j, 2 j + 1 into D1[32 c ..],
   // the two channels' chunks interleaved.
-  auto issue_row = [&]() {
+  auto issue_row = [&](int part) {
     const int c0 = 2 * (iw - 1);
     const uint64_t br_desc = smem_desc(smem_u32(BR), 128, 256);
     constexpr uint32_t idesc = idesc_f16(128, 32, BF, 0, 0);
@@ -469,10 +495,13 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constan
         for (int pp = 0; pp < NSPLIT; ++pp)
 #pragma unroll
           for (int cc = 0; cc < 2; ++cc) {
+            // products: (data hi, w hi), (data lo, w hi), (data hi, w lo)
             const int c = c0 + cc, ap = pp == 1 ? 1 : 0, bp = pp == 2 ? 1 : 0;
-            mma_ts(tmem + kD1 + (uint32_t)(32 * c),
-                   tmem + kA1 + (uint32_t)((c * kParts + ap) * kA1Stride + 8 * i),
-                   br_desc + (uint64_t)(((i * kWParts + bp) * 1024) >> 4), idesc, (i > 0 || pp > 0) ? 1u : 0u);
+            if (SEQ && ap != part) continue;  // SEQ: A1 holds data part `part` only
+            const uint32_t region = SEQ ? (uint32_t)c : (uint32_t)(c * kParts + ap);
+            const bool first = i == 0 && (SEQ ? (part == 0 && pp == 0) : pp == 0);
+            mma_ts(tmem + kD1 + (uint32_t)(32 * c), tmem + kA1 + region * kA1Stride + (uint32_t)(8 * i),
+                   br_desc + (uint64_t)(((i * kWParts + bp) * 1024) >> 4), idesc, first ? 0u : 1u);
           }
       }
     }
@@ -529,7 +558,7 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constan
   // sin)(n w f) of the demodulation unit from the 2T-phase table, whose offsets
   // then advance to n + 1.
   float P[8], Q[8];
-  auto demod = [&]() {
+  auto demod = [&](int n) {
     uint32_t v[32];
     tmem_ld_x16(tmem + lane_base + kD2 + (uint32_t)(32 * h), *reinterpret_cast<uint32_t(*)[16]>(&v[0]));
     tmem_ld_x16(tmem + lane_base + kD2 + (uint32_t)(32 * h + 16), *reinterpret_cast<uint32_t(*)[16]>(&v[16]));
@@ -541,10 +570,12 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constan
     }
     tmem_ld_wait_dep(*reinterpret_cast<uint32_t(*)[16]>(&v[0]));
     tmem_ld_wait_dep(*reinterpret_cast<uint32_t(*)[16]>(&v[16]));
+    const float dn = kFold ? 1.f : a.d[n];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
-      Q[j] = fmaf(cs[j].x, __uint_as_float(v[4 * j + 0]), fmaf(cs[j].y, __uint_as_float(v[4 * j + 2]), Q[j]));
-      P[j] = fmaf(cs[j].x, __uint_as_float(v[4 * j + 1]), fmaf(cs[j].y, __uint_as_float(v[4 * j + 3]), P[j]));
+      const float tc = dn * cs[j].x, ts = dn * cs[j].y;
+      Q[j] = fmaf(tc, __uint_as_float(v[4 * j + 0]), fmaf(ts, __uint_as_float(v[4 * j + 2]), Q[j]));
+      P[j] = fmaf(tc, __uint_as_float(v[4 * j + 1]), fmaf(ts, __uint_as_float(v[4 * j + 3]), P[j]));
     }
   };
 
@@ -590,18 +621,26 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constan
         tma_pending = true;
       }
       if (!(ok = phase_sync())) break;  // table of harmonic 0
-      if (!(ok = phase_sync())) break;  // A1 <- harmonic 0
-      if (row_issuer) issue_row();      // R(0)
+      if (!(ok = phase_sync())) break;  // A1 <- harmonic 0 (SEQ: its hi part)
+      if (row_issuer) issue_row(0);     // R(0) (SEQ: hi part)
+      if (SEQ) {
+        if (!(ok = phase_sync())) break;  // A1 <- lo part
+        if (row_issuer) issue_row(1);
+      }
       if (!(ok = phase_sync())) break;  // B2 <- harmonic 0
       for (int n = 0; n < a.K; ++n) {
         const bool more = n + 1 < a.K;
         if (col_issuer) issue_col();  // C(n)
-        if (!(ok = phase_sync())) break;  // A1 <- harmonic n + 1
+        if (!(ok = phase_sync())) break;  // A1 <- harmonic n + 1 (SEQ: hi part)
         if (SHARED) {
           if (!(ok = phase_sync())) break;  // D2 (= D1) read
-          if (more && row_issuer) issue_row();
+          if (more && row_issuer) issue_row(0);
+          if (SEQ && more) {
+            if (!(ok = phase_sync())) break;  // A1 <- lo part
+            if (row_issuer) issue_row(1);
+          }
         } else {
-          if (more && row_issuer) issue_row();  // R(n+1)
+          if (more && row_issuer) issue_row(0);  // R(n+1)
         }
         if (!(ok = phase_sync())) break;  // B2 <- harmonic n + 1
       }
@@ -681,32 +720,42 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constan
       bm = 0;
       build_table(0, 0);
       if (!(ok = phase_sync())) break;
-      modulate(0);
+      modulate(0, 0);
       if (!(ok = phase_sync())) break;
       if (a.K > 1) build_table(1, 1);
       wait_bar(mbarR, phR);
+      if (SEQ) {  // the lo part through the same A1
+        modulate(0, 1);
+        if (!(ok = phase_sync())) break;
+        wait_bar(mbarR, phR);
+      }
       resplit();
       if (!(ok = phase_sync())) break;
 
       for (int n = 0; n < a.K; ++n) {
         const bool more = n + 1 < a.K;
-        if (more) modulate((n + 1) & 1);   // A1 <- harmonic n + 1 (while C(n): B2 -> D2 runs)
+        if (more) modulate((n + 1) & 1, 0);  // A1 <- harmonic n + 1 (while C(n): B2 -> D2 runs)
         if (!(ok = phase_sync())) break;
         // the table of n + 2 replaces that of n (read by the modulation of n, done)
         if (SHARED) {
           if (n + 2 < a.K) build_table(n + 2, n & 1);
           wait_bar(mbarC, phC);
-          demod();
+          demod(n);
           if (!(ok = phase_sync())) break;
           if (more) {  // R(n+1): A1 -> D (= D2, read)
             wait_bar(mbarR, phR);
+            if (SEQ) {  // then the lo part of harmonic n + 1 through the same A1
+              modulate((n + 1) & 1, 1);
+              if (!(ok = phase_sync())) break;
+              wait_bar(mbarR, phR);
+            }
             resplit();
           }
         } else {
           // R(n+1): A1 -> D1 runs meanwhile
           if (n + 2 < a.K) build_table(n + 2, n & 1);
           wait_bar(mbarC, phC);
-          demod();
+          demod(n);
           if (more) {
             wait_bar(mbarR, phR);  // C(n) is complete too: B2 may be rewritten
             resplit();
@@ -738,7 +787,7 @@ namespace tc2 {
 // Host launcher of one instantiation: tiles of 32 x (128 - 2W), one persistent
 // CTA per SM (at most one per tile), the box tensor map from the per-pointer
 // cache, the shared-memory attribute set once per device.
-template <int BF, int NSPLIT, int KXC, int SHARED>
+template <int BF, int NSPLIT, int KXC, int SHARED, int SEQ = 0>
 fbf_status launch_cfg(const FilterArgs &a0, cudaStream_t s) {
   FilterArgs a = a0;
   const int BYv = kLanes - 2 * a.W;
@@ -753,7 +802,7 @@ fbf_status launch_cfg(const FilterArgs &a0, cudaStream_t s) {
   if (sms <= 0) return FBF_ERR_CUDA;
   const int grid = a.ntiles < sms ? a.ntiles : sms;
   constexpr Layout Ly = layout<NSPLIT, KXC>();
-  auto kern = fbf_tc2_u8_kernel<BF, NSPLIT, KXC, SHARED>;
+  auto kern = fbf_tc2_u8_kernel<BF, NSPLIT, KXC, SHARED, SEQ>;
   static FuncAttrOnce once;
   if (!once.done(dev)) {
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Ly.bytes) != cudaSuccess)

@@ -50,6 +50,12 @@ __device__ __forceinline__ void tmem_st_x4(uint32_t taddr, uint32_t r0, uint32_t
   asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr), "r"(r0), "r"(r1),
                "r"(r2), "r"(r3));
 }
+// Two columns per thread: on GB300 stores of 1-2 columns per thread reach
+// ~300 B/cycle per SM where 4-16 columns reach ~40-190 (measured), so the
+// per-harmonic stores of the tensor-core kernels use this shape.
+__device__ __forceinline__ void tmem_st_x2(uint32_t taddr, uint32_t r0, uint32_t r1) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x2.b32 [%0], {%1, %2};" ::"r"(taddr), "r"(r0), "r"(r1));
+}
 __device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void tmem_ld_x4(uint32_t taddr, uint32_t (&r)[4]) {

@@ -14,7 +14,7 @@ import os
 from . import build as _build
 
 KMAX = 256
-WMAX = 32
+WMAX = 48
 
 FBF_OK, FBF_ERR_INVALID_ARGUMENT, FBF_ERR_NOT_CONVERGED, FBF_ERR_RANGE = 0, 1, 2, 3
 FBF_ERR_UNSUPPORTED, FBF_ERR_CUDA, FBF_ERR_TIMEOUT = 4, 5, 6

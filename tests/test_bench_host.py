@@ -38,20 +38,19 @@ def test_issued_flops_bound_the_algorithmic_count(form, K):
 
 
 def test_issued_flops_follow_the_tile_count():
-    """2048^2 at W = 9 in the second tensor-core layout (single and split FP16
-    forms): 64 x 19 tiles of 128 - 2W = 110 output rows (8 waves of 152 CTAs);
-    per tile and harmonic 4 channels x 4 row chunks (Wp = 16, 16 + 32 + 9
-    ext columns -> 64) of 128 x 32 x 16 and 8 column chunks of 128 x 128 x 16.
-    The BF16 form at W = 30 runs the first layout: 64 x 32 tiles of 64 rows, 6
-    row chunks, two 32-row column blocks of ceil((32 + 2W) / 16) = 6 chunks
-    each."""
+    """2048^2 at W = 9, single FP16 form (second tensor-core layout): 64 x 19
+    tiles of 128 - 2W = 110 output rows (8 waves of 152 CTAs); per tile and
+    harmonic 4 channels x 4 row chunks (Wp = 16, 16 + 32 + 9 ext columns -> 64)
+    of 128 x 32 x 16 and 8 column chunks of 128 x 128 x 16.  The split forms up
+    to W = 32 run the first layout: at W = 30 64 x 32 tiles of 64 rows, 6 row
+    chunks, two 32-row column blocks of ceil((32 + 2W) / 16) = 6 chunks each."""
     tiles = math.ceil(2048 / 32) * math.ceil(2048 / 110)
     assert tiles == 1216 == 8 * 152
     per_tile = 4 * 4 * 2 * 128 * 32 * 16 + 8 * 2 * 128 * 128 * 16
-    assert bench.tc_layout("tc_fp16_single", 9) == bench.tc_layout("tc_fp16", 9) == "tc2"
+    assert bench.tc_layout("tc_fp16_single", 9) == "tc2"
     assert bench.tc_issued_flops(1, 9, "tc_fp16_single") == tiles * per_tile
-    assert bench.tc_issued_flops(17, 9, "tc_fp16") == 17 * 2 * tiles * per_tile
-    assert bench.tc_layout("tc_bf16", 30) == "tc1"
+    assert bench.tc_layout("tc_fp16", 9) == bench.tc_layout("tc_bf16", 30) == "tc1"
+    assert bench.tc_layout("tc_fp16", 36) == "tc2"
     tiles1 = 64 * 32
     per_tile1 = 4 * 6 * 2 * 128 * 32 * 16 + 2 * 6 * 2 * 128 * 32 * 16
     assert bench.tc_issued_flops(1, 30, "tc_bf16") == 3 * tiles1 * per_tile1

@@ -171,8 +171,8 @@ def test_filter_validation_without_device_work(fbf):
     # empty image: a no-op, no launch
     assert L.fbf_filter(C.byref(p), nul, 0, 0, 4, 4, nul, 16, nul) == fbf.FBF_OK
     assert L.fbf_filter(C.byref(p), nul, 0, 4, 0, 4, nul, 16, nul) == fbf.FBF_OK
-    big = fbf.make_params(c, 11.0)  # W = 33 > FBF_WMAX
-    assert fbf.fbf_resolve_window(big) == 33
+    big = fbf.make_params(c, 16.2)  # W = 49 > FBF_WMAX = 48
+    assert fbf.fbf_resolve_window(big) == 49
     assert L.fbf_filter(C.byref(big), dummy, 0, 4, 4, 4, dummy, 16, nul) == fbf.FBF_ERR_RANGE
     neg = fbf.make_params(c, -1.0)
     assert L.fbf_filter(C.byref(neg), dummy, 0, 4, 4, 4, dummy, 16, nul) == fbf.FBF_ERR_INVALID_ARGUMENT

@@ -102,7 +102,7 @@ def test_ragged_and_tiny_images(fbf, shape, border, form):
 
 
 @pytest.mark.parametrize("form", FORMS)
-@pytest.mark.parametrize("W", [0, 1, 2, 5, 8, 15, 16, 17, 23, 30, 31, 32])
+@pytest.mark.parametrize("W", [0, 1, 2, 5, 8, 15, 16, 17, 23, 30, 31, 32, 33, 36, 40, 45, 48])
 def test_every_window_tail(fbf, W, form):
     """All tap-count residues mod 8 and both tile configurations (box and Gaussian)."""
     img = make_image(96, 150, seed=W)
@@ -116,17 +116,16 @@ def test_every_window_tail(fbf, W, form):
 
 def _tc_tile_rows(form, W):
     """Output rows of one tensor-core tile: 128 - 2W in the second layout (the
-    single form up to W = 48, split FP16 up to 24, BF16 up to 16); in the first
-    layout min(BY, 128 - 2W) with BY = 112 computed rows for W <= 16, 96 for
-    W <= 26 and 64 above."""
-    second = W <= {"tc_fp16_single": 48, "tc_fp16": 24, "tc_bf16": 16}[form]
-    if second:
+    single form at every W, the split forms beyond W = 32); in the first layout
+    min(BY, 128 - 2W) with BY = 112 computed rows for W <= 16, 96 for W <= 26
+    and 64 above."""
+    if form == "tc_fp16_single" or W > 32:
         return 128 - 2 * W
     return min(112, 128 - 2 * W) if W <= 16 else (128 - 2 * W if W <= 26 else 64)
 
 
 @pytest.mark.parametrize("form", ["tc_fp16", "tc_bf16", "tc_fp16_single"])
-@pytest.mark.parametrize("W", [1, 8, 9, 12, 15, 16, 17, 20, 24, 25, 26, 27, 30, 32])
+@pytest.mark.parametrize("W", [1, 8, 9, 12, 15, 16, 17, 20, 24, 25, 26, 27, 30, 32, 33, 45, 48])
 def test_tensor_core_tile_row_edges(fbf, W, form):
     """Heights at and across the tensor-core tiles' row count (both layouts),
     under both borders.  The single FP16 form is held to 0.25 gray here: on
@@ -208,7 +207,7 @@ def _sample_points(H, W, n, seed):
 
 
 @pytest.mark.parametrize("form", FORMS)
-@pytest.mark.parametrize("sigma_s", [3.0, 5.0, 10.0])
+@pytest.mark.parametrize("sigma_s", [3.0, 5.0, 10.0, 12.0])
 @pytest.mark.parametrize("sigma_r", [20.0, 40.0])
 def test_full_size_2048_sampled(fbf, sigma_s, sigma_r, form):
     """2048x2048, eps = 1e-3, the benchmark's launch configuration: sampled pixels
@@ -224,6 +223,21 @@ def test_full_size_2048_sampled(fbf, sigma_s, sigma_r, form):
     _check(got[ys, xs], ref, TOL[form])
     assert np.all(np.isfinite(got))
     assert got.min() >= -1.0 and got.max() <= 256.0
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("W", [33, 36, 45])
+def test_windows_beyond_32(fbf, W, form):
+    """Windows wider than 32 (sigma_s = 11 .. 15; Table 1 of Sec. V runs sigma_s up
+    to 12): every form against Algorithm 1 in FP64, both borders, Gaussian and
+    box kernels."""
+    img = make_image(300, 260, seed=W + 5)
+    c = fbf.fbf_fit_coeffs("gaussian", 25.0, 255.0, 1e-3)
+    for border in ("reflect", "truncate"):
+        got = _gpu(fbf, img, c, W / 3.0, W=W, border=border, form=form)
+        _check(got, _oracle_full(img, c, W / 3.0, W, "gaussian", border), TOL[form])
+    got = _gpu(fbf, img, c, 1.0, W=W, spatial="box", form=form)
+    _check(got, _oracle_full(img, c, 1.0, W, "box", "reflect"), 0.25 if form == "tc_fp16_single" else TOL[form])
 
 
 @pytest.mark.parametrize("sigma_r", [5.0, 10.0])
@@ -288,28 +302,30 @@ def test_auto_form_picks_the_documented_kernel(fbf, spatial, W, expect):
     _check(auto, _oracle_full(img, c, max(W, 1) / 3.0, W, spatial, "reflect"), TOL[expect])
 
 
-@pytest.mark.parametrize("form", ["tc_fp16_single", "tc_fp16", "tc_bf16"])
+@pytest.mark.parametrize("form,W", [("tc_fp16_single", 9), ("tc_fp16_single", 36), ("tc_fp16", 36),
+                                    ("tc_bf16", 36)])
 @pytest.mark.parametrize("pad", [0, 3])
-def test_bounded_wait_gives_up_then_the_next_call_is_correct(fbf, form, pad):
-    """With the poll limit set to 0 every bounded wait of the tensor-core kernel
-    gives up at once (the TMA box wait when the image is TMA-aligned, pad = 0;
-    the first MMA wait when rows are loaded directly, pad = 3): the kernel drains
-    its copies and MMAs in flight, sets the device error word and returns; the
-    context stays usable and the next call, at the default limit, is exact."""
+def test_bounded_wait_gives_up_then_the_next_call_is_correct(fbf, form, W, pad):
+    """With the poll limit set to 0 every bounded wait of the second tensor-core
+    layout gives up at once (the TMA box wait when the image is TMA-aligned,
+    pad = 0; the first MMA wait when rows are loaded directly, pad = 3): the
+    kernel drains its copies and MMAs in flight, sets the device error word and
+    returns; the context stays usable and the next call, at the default limit,
+    is exact.  (The split forms run the second layout beyond W = 32.)"""
     import ctypes as C
 
     img = make_image(150, 144, seed=31)  # 144-byte rows: TMA-aligned unless padded
     c = fbf.fbf_fit_coeffs("gaussian", 30.0, 255.0, 1e-3)
-    ref = _oracle_full(img, c, 3.0, 9, "gaussian", "reflect")
+    ref = _oracle_full(img, c, W / 3.0, W, "gaussian", "reflect")
     try:
         assert fbf.fbf_device_error() == 0
         fbf.fbf_set_wait_limit(0)
-        _gpu(fbf, img, c, 3.0, pad=pad, form=form)
+        _gpu(fbf, img, c, W / 3.0, W=W, pad=pad, form=form)
         v = C.c_uint(0)
         assert fbf.lib.fbf_device_error(C.byref(v)) == fbf.FBF_ERR_TIMEOUT
         assert v.value != 0
         assert fbf.fbf_device_error() == 0  # read and cleared
     finally:
         fbf.fbf_set_wait_limit(-1)
-    _check(_gpu(fbf, img, c, 3.0, pad=pad, form=form), ref, TOL[form])
+    _check(_gpu(fbf, img, c, W / 3.0, W=W, pad=pad, form=form), ref, TOL[form])
     assert fbf.fbf_device_error() == 0

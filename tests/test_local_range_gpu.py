@@ -78,7 +78,7 @@ def test_errors_and_empty(fbf):
     x = torch.zeros((4, 4), dtype=torch.uint8, device="cuda")
     p = C.c_void_p(x.data_ptr())
     o = C.c_void_p(out.data_ptr())
-    assert fbf.lib.fbf_local_range(p, fbf.FBF_U8, 4, 4, 4, 33, o, None) == fbf.FBF_ERR_RANGE
+    assert fbf.lib.fbf_local_range(p, fbf.FBF_U8, 4, 4, 4, 49, o, None) == fbf.FBF_ERR_RANGE
     assert fbf.lib.fbf_local_range(p, fbf.FBF_F32, 4, 4, 16, 3, o, None) == fbf.FBF_ERR_UNSUPPORTED
     assert fbf.lib.fbf_local_range(p, fbf.FBF_U8, 4, 4, 3, 3, o, None) == fbf.FBF_ERR_INVALID_ARGUMENT
     assert fbf.lib.fbf_local_range(p, fbf.FBF_U8, 4, 4, 4, 3, None, None) == fbf.FBF_ERR_INVALID_ARGUMENT
