@@ -554,13 +554,33 @@ def run_differentiation(fbf, torch, dev, stream, steps, with_oracle):
                 xi = xs[i].detach().requires_grad_(True)
                 (Fn.apply(xi, p) * gs[i]).sum().backward()
 
+    gbuf = torch.empty_like(xs)
+
+    def backward_only():  # fbf_filter_backward of the stack: forward pass for (a, b), adjoint, fold
+        fbf.fbf_filter_backward(p, xs, gs, grad=gbuf, stream=stream)
+
     ms_each = _timed_steps(torch, dev, stream, step_each, steps)
     ms = _timed_steps(torch, dev, stream, step, steps)
+    ms_bwd = _timed_steps(torch, dev, stream, backward_only, steps)
+    # Method's work of the gradient: the forward FIR over C = 4(K-1) + 2 channels
+    # (for a = g/Q, b = g fhat/Q) and the adjoint over 2C channels (the forward
+    # channels recomputed and the four adjoint ones per harmonic), 2 passes of
+    # 2W + 1 taps each: 3 x 2 x 2 (2W + 1) C flops per pixel.
+    Wd_ = 12
+    bwd_flops = 3.0 * algorithmic_flops_per_pixel(c.K, Wd_) * n * S * S
+    fp32_peak = fbf.fbf_measure_fp32_peak(dev.index if dev.index is not None else 0)
+    bwd_tf = bwd_flops / (ms_bwd * 1e-3) / 1e12
     res = {"workload": "16 x 512x512 f32 synthetic (seeds 1400+i, u8/255, T=1), sigma_s=4 (W=12), "
                        "sigma_r=0.1, levels=256, eps=1e-3, K=%d; forward + adjoint of the (16, 512, 512) stack "
                        "via torch.autograd" % c.K,
            "ms": round(ms, 3), "mpix_s": round(n * S * S / ms / 1e3, 1),
-           "single_image_calls": {"ms": round(ms_each, 3), "mpix_s": round(n * S * S / ms_each / 1e3, 1)}}
+           "single_image_calls": {"ms": round(ms_each, 3), "mpix_s": round(n * S * S / ms_each / 1e3, 1)},
+           "backward_only": {"ms": round(ms_bwd, 3), "mpix_s": round(n * S * S / ms_bwd / 1e3, 1),
+                             "roofline": {"bound": "alu", "achieved": round(bwd_tf, 3), "peak": round(fp32_peak, 3),
+                                          "unit": "TFLOP/s", "frac": round(bwd_tf / fp32_peak, 4),
+                                          "peak_source": "FP32 FMA probe (fbf_measure_fp32_peak) (of measured)",
+                                          "work": "3 x 2 x 2 (2W+1) C flops per pixel: forward for (a, b) + "
+                                                  "adjoint over 2C channels"}}}
     if with_oracle:
         import oracle as O
 

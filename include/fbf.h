@@ -167,7 +167,7 @@ fbf_status fbf_fit_coeffs_samples(const double *phi, int L, double T, double eps
  *              in_pitch bytes (>= Wd * element size)
  *   dtype      FBF_U8: values 0..255, coeffs->T must be an integer >= 1
  *              (the phase n*omega*f is reduced exactly in integers);
- *              FBF_F32: any finite values, any T > 0; FP32 form only, W <= 16
+ *              FBF_F32: any finite values, any T > 0; FP32 form only, W <= 32
  *   d_out      device FP32 output, H x Wd, row pitch out_pitch bytes; must not
  *              overlap d_in
  *   stream     CUDA stream (0 = legacy default stream)
@@ -269,7 +269,7 @@ fbf_status fbf_plan_schedule(const fbf_plan *plan, fbf_schedule *schedule, doubl
  *   d_gin      FP32 output dL/df, same shape and pitch
  * Allocates its scratch (8 bytes per pixel, plus (H+2W)(Wd+2W) floats under
  * REFLECT) stream-ordered with cudaMallocAsync / cudaFreeAsync on `stream`.
- * W <= 16.  Returns FBF_ERR_UNSUPPORTED for the tensor-core forms.
+ * W <= 32.  Returns FBF_ERR_UNSUPPORTED for the tensor-core forms.
  */
 fbf_status fbf_filter_backward(const fbf_params *p, const float *d_in, const float *d_gout,
                                const float *d_out_fwd, float *d_gin, int H, int Wd, size_t pitch,

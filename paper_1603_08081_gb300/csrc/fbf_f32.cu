@@ -36,9 +36,8 @@ namespace fbf {
 namespace {
 
 constexpr int kBX = 32;       // output tile columns
-constexpr int kWcapF = 16;    // compiled window limit of the FP32-input kernels
+constexpr int kWcapF = 32;    // window limit of the FP32-input kernels
 constexpr int kNTf = 256;
-constexpr int kHXA = kBX + 2 * kWcapF + kRun;  // halo columns incl. the FIR over-read
 constexpr int kPR = kBX + 1;  // row buffer pitch (odd, in 16-byte units)
 
 enum { kModeForward = 0, kModeAdjoint = 1 };
@@ -53,17 +52,21 @@ struct F32Args {
   size_t gext_pitch;  // bytes
 };
 
-// Output tiles of kBX x BY pixels, BY = 64 (fewer halo rows per output) or 32
-// (twice the tiles, for grids too small to fill the GPU with 64-row tiles).
-// The 32-row tiles also stage the adjoint's (a, b) halo (zero outside the
-// image); the 64-row tiles have no room for it and read (a, b) from L2.
-template <int BY>
+// Output tiles of kBX x BY pixels for windows up to WCAP.  WCAP = 16: BY = 64
+// (fewer halo rows per output) or 32 (twice the tiles, for grids too small to
+// fill the GPU with 64-row tiles); the 32-row tiles also stage the adjoint's
+// (a, b) halo (zero outside the image), the 64-row tiles read it from L2.
+// WCAP = 32 (windows 17..32): BY = 32 with neither f nor (a, b) staged -- the
+// channel tile and the row buffer take the shared memory -- both read from L2.
+template <int BY, int WCAP>
 struct F32Smem {
-  static constexpr int kHYP = BY + 2 * kWcapF;  // padded halo rows
-  static constexpr bool kStageAB = BY == 32;
+  static constexpr int kHYP = (BY + 2 * WCAP + 31) / 32 * 32;  // padded halo rows (row-pass groups of 32)
+  static constexpr int kHXA = kBX + 2 * WCAP + kRun;           // halo columns incl. the FIR over-read
+  static constexpr bool kStageF = WCAP <= 16;
+  static constexpr bool kStageAB = BY == 32 && WCAP <= 16;
   ulonglong2 chan[kHXA * kHYP];        // transposed channel tile, 4 channels per pixel
   ulonglong2 rowbuf[(kHYP + 1) * kPR];  // row-pass output
-  float fT[kHXA * kHYP];               // halo tile of f (forward border semantics), NaN = absent
+  float fT[kStageF ? kHXA * kHYP : 1];  // halo tile of f (forward border semantics), NaN = absent
   float2 abT[kStageAB ? kHXA * kHYP : 1];  // adjoint (a, b) halo, 32-row tiles only
 };
 
@@ -78,15 +81,17 @@ __device__ __forceinline__ float ldf(const float *base, size_t pitch, int y, int
 
 // MODE forward: out = fhat (nullable), ab = (g/Q, g fhat/Q) (nullable).
 // MODE adjoint: gext = per-position gradient on the grid described by F32Args.
-template <int MODE, int kBY>
+template <int MODE, int kBY, int WCAP>
 __global__ void __launch_bounds__(kNTf, 1) fbf_f32_kernel(const __grid_constant__ FilterArgs a,
                                                           const __grid_constant__ F32Args x) {
-  constexpr int kHYP = F32Smem<kBY>::kHYP;
+  using Smem = F32Smem<kBY, WCAP>;
+  constexpr int kHYP = Smem::kHYP, kHXA = Smem::kHXA;
+  constexpr bool kStageF = Smem::kStageF;
   constexpr int NW = kNTf / 32, NXR = kBX / kRun, NYR = kBY / kRun;
   constexpr int UPW = NYR / NW;  // column units per warp (1 column group of 32)
   static_assert(NYR % NW == 0 || NW % NYR == 0, "units");
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  F32Smem<kBY> &S = *reinterpret_cast<F32Smem<kBY> *>(smem_raw);
+  Smem &S = *reinterpret_cast<Smem *>(smem_raw);
 
   const int W = a.W, taps = 2 * W + 1;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -98,25 +103,37 @@ __global__ void __launch_bounds__(kNTf, 1) fbf_f32_kernel(const __grid_constant_
   const bool reflect = a.border == FBF_BORDER_REFLECT;
   const float invT = 1.0f / a.T;
 
-  // Stage f (forward border semantics) and, with 32-row tiles, the adjoint's
-  // (a, b) (zero outside the image).
-  constexpr bool kStageAB = MODE == kModeAdjoint && F32Smem<kBY>::kStageAB;
-  for (int e = tid; e < kHXA * kHYP; e += kNTf) {
-    const int ex = e / kHYP, ey = e - ex * kHYP;
-    float fv = __int_as_float(0x7fc00000);  // absent
-    float2 abv = make_float2(0.f, 0.f);
+  // f at halo position (ex, ey) with the forward border semantics; NaN = absent.
+  auto f_at = [&](int ex, int ey) -> float {
+    float fv = __int_as_float(0x7fc00000);
     if (ey < HY && ex < HX) {
-      int iy = py0 - W + ey, ix = px0 - W + ex;
-      const bool inside = iy >= 0 && iy < H && ix >= 0 && ix < Wd;
-      if (kStageAB && inside) abv = x.ab[(size_t)iy * Wd + ix];
-      if (reflect) {
+      const int iy = py0 - W + ey, ix = px0 - W + ex;
+      if (reflect)
         fv = ldf(static_cast<const float *>(a.in), a.in_pitch, reflect_index(iy, H), reflect_index(ix, Wd));
-      } else if (inside) {
+      else if (iy >= 0 && iy < H && ix >= 0 && ix < Wd)
         fv = ldf(static_cast<const float *>(a.in), a.in_pitch, iy, ix);
-      }
     }
-    S.fT[ex * kHYP + ey] = fv;
-    if constexpr (kStageAB) S.abT[ex * kHYP + ey] = abv;
+    return fv;
+  };
+  auto fT_at = [&](int e) -> float {  // staged tile, or L2 (wide windows)
+    if constexpr (kStageF) return S.fT[e];
+    const int ex = e / kHYP;
+    return f_at(ex, e - ex * kHYP);
+  };
+
+  // Stage f and, with 32-row tiles, the adjoint's (a, b) (zero outside the image).
+  constexpr bool kStageAB = MODE == kModeAdjoint && Smem::kStageAB;
+  if constexpr (kStageF) {
+    for (int e = tid; e < kHXA * kHYP; e += kNTf) {
+      const int ex = e / kHYP, ey = e - ex * kHYP;
+      float2 abv = make_float2(0.f, 0.f);
+      if (kStageAB && ey < HY && ex < HX) {
+        const int iy = py0 - W + ey, ix = px0 - W + ex;
+        if (iy >= 0 && iy < H && ix >= 0 && ix < Wd) abv = x.ab[(size_t)iy * Wd + ix];
+      }
+      S.fT[e] = f_at(ex, ey);
+      if constexpr (kStageAB) S.abT[e] = abv;
+    }
   }
   __syncthreads();
 
@@ -165,7 +182,7 @@ __global__ void __launch_bounds__(kNTf, 1) fbf_f32_kernel(const __grid_constant_
     const float nw = (float)n * 3.14159265358979323846f * invT;  // n * omega
     // ---- forward channels (cos, sin, f cos, f sin)(n w f) of every halo pixel.
     for (int e = tid; e < kHXA * kHYP; e += kNTf) {
-      const float fv = S.fT[e];
+      const float fv = fT_at(e);
       float sn = 0.f, cs = 0.f, fval = 0.f;
       if (fv == fv) {  // present
         sincospif((float)n * fv * invT, &sn, &cs);
@@ -226,7 +243,7 @@ __global__ void __launch_bounds__(kNTf, 1) fbf_f32_kernel(const __grid_constant_
         if (yr >= NYR) continue;
 #pragma unroll
         for (int o = 0; o < kRun; ++o) {
-          const float fm = S.fT[(lane + W) * kHYP + yr * kRun + o + W];
+          const float fm = fT_at((lane + W) * kHYP + yr * kRun + o + W);
           float sn = 0.f, cs = 0.f;
           if (fm == fm) sincospif((float)n * fm * invT, &sn, &cs);
           const float Ar = lo_f(adj[q][o].a), Ai = hi_f(adj[q][o].a);
@@ -301,13 +318,13 @@ __global__ void fbf_fold_kernel(const float *__restrict__ gext, size_t gext_pitc
   }
 }
 
-template <int MODE, int BY>
+template <int MODE, int BY, int WCAP>
 fbf_status launch_f32_by(const FilterArgs &a0, const F32Args &x, int grid_h, int grid_w, cudaStream_t s) {
   FilterArgs a = a0;
   a.tiles_x = (grid_w + kBX - 1) / kBX;
   a.ntiles = a.tiles_x * ((grid_h + BY - 1) / BY);
-  auto kern = fbf_f32_kernel<MODE, BY>;
-  const size_t smem = sizeof(F32Smem<BY>);
+  auto kern = fbf_f32_kernel<MODE, BY, WCAP>;
+  const size_t smem = sizeof(F32Smem<BY, WCAP>);
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return FBF_ERR_CUDA;
   kern<<<a.ntiles, kNTf, smem, s>>>(a, x);
@@ -322,9 +339,10 @@ fbf_status launch_f32(const FilterArgs &a, const F32Args &x, int grid_h, int gri
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return FBF_ERR_CUDA;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (a.W > 16) return launch_f32_by<MODE, 32, 32>(a, x, grid_h, grid_w, s);
   const long long tiles64 = (long long)((grid_w + kBX - 1) / kBX) * ((grid_h + 63) / 64);
-  if (tiles64 >= 2LL * sms) return launch_f32_by<MODE, 64>(a, x, grid_h, grid_w, s);
-  return launch_f32_by<MODE, 32>(a, x, grid_h, grid_w, s);
+  if (tiles64 >= 2LL * sms) return launch_f32_by<MODE, 64, 16>(a, x, grid_h, grid_w, s);
+  return launch_f32_by<MODE, 32, 16>(a, x, grid_h, grid_w, s);
 }
 
 }  // namespace

@@ -361,7 +361,7 @@ fbf_status launch_cfg(const FilterArgs &a0, cudaStream_t s) {
 // Tile shapes: 64 x 96 outputs with two table buffers for W <= 16 (<= 227 KB
 // of shared memory), 32 x 192 with one buffer for 17 <= W <= 32 (<= 222 KB),
 // and for 33 <= W <= 48 32 x 128 with one buffer and a run-time tap count
-// (launch_wide, 213 KB).
+// (213 KB; fbf_fp32_w33_48.cu).
 // Both keep the padded halo rows of the row pass at <= 1.33x the output rows
 // and split the row and column units evenly over 8 warps.  The tap count is a
 // template parameter (one instantiation per W), so both FIR loops unroll
@@ -372,12 +372,6 @@ fbf_status launch_w(const FilterArgs &a, cudaStream_t s) {
     return launch_cfg<64, 96, 256, 2, 16, 2 * Wv + 1>(a, s);
   else
     return launch_cfg<32, 192, 256, 1, 32, 2 * Wv + 1>(a, s);
-}
-
-// Windows 33..48: one instantiation with run-time taps (FIR or box sums).
-inline fbf_status launch_wide(const FilterArgs &a, cudaStream_t s) {
-  if (a.box) return launch_cfg<32, 128, 256, 1, 48, 0, 1>(a, s);
-  return launch_cfg<32, 128, 256, 1, 48, 0, 0>(a, s);
 }
 
 #define FBF_K1_CASE(Wv) \

@@ -3,9 +3,11 @@
 
 namespace fbf {
 
+// One instantiation with run-time taps for the FIR, one for the box sums.
 fbf_status launch_fp32_u8_w33_48(const FilterArgs &a, cudaStream_t s) {
   if (a.W < 33 || a.W > 48) return FBF_ERR_RANGE;
-  return launch_wide(a, s);
+  if (a.box) return launch_cfg<32, 128, 256, 1, 48, 0, 1>(a, s);
+  return launch_cfg<32, 128, 256, 1, 48, 0, 0>(a, s);
 }
 
 }  // namespace fbf

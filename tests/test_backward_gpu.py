@@ -47,7 +47,7 @@ def _cuda(a):
 
 @pytest.mark.parametrize("border", ["reflect", "truncate"])
 @pytest.mark.parametrize("shape,sigma_s", [((64, 64), 4.0), ((37, 53), 2.0), ((5, 7), 3.0), ((100, 33), 5.0),
-                                           ((1, 40), 1.0)])
+                                           ((1, 40), 1.0), ((70, 90), 7.0), ((45, 61), 10.6), ((9, 6), 6.0)])
 def test_float_forward_matches_oracle(fbf, border, shape, sigma_s):
     import torch
 
@@ -76,9 +76,11 @@ def test_float_forward_arbitrary_T(fbf):
 
 @pytest.mark.parametrize("border", ["reflect", "truncate"])
 @pytest.mark.parametrize("shape,sigma_s,W", [((24, 30), 1.0, 3), ((17, 13), 2.0, 6), ((40, 36), 4.0, 12),
-                                             ((6, 9), 2.0, 6), ((9, 4), 1.0, 16)])
+                                             ((6, 9), 2.0, 6), ((9, 4), 1.0, 16), ((30, 41), 6.7, 20),
+                                             ((36, 44), 10.0, 32), ((7, 5), 3.0, 20), ((50, 3), 8.0, 24)])
 def test_backward_matches_oracle_gradient(fbf, border, shape, sigma_s, W):
-    """Full FP64 gradient of sum(g * fhat), eq. (9), incl. windows wider than the image."""
+    """Full FP64 gradient of sum(g * fhat), eq. (9), incl. windows wider than the
+    image, for both kernel tile sets (W <= 16 and 17 <= W <= 32)."""
     import torch
 
     img = make_image_f32(*shape, seed=1401)
@@ -154,7 +156,7 @@ def test_backward_rejects_tensor_core_forms_and_big_windows(fbf):
     st = fbf.lib.fbf_filter_backward(C.byref(p), C.c_void_p(x.data_ptr()), C.c_void_p(x.data_ptr()), None,
                                      C.c_void_p(x.data_ptr()), 8, 8, 32, None)
     assert st == fbf.FBF_ERR_UNSUPPORTED
-    p = fbf.make_params(c, 6.0)  # W = 18 > 16
+    p = fbf.make_params(c, 11.0)  # W = 33 > 32, the adjoint's window limit
     st = fbf.lib.fbf_filter_backward(C.byref(p), C.c_void_p(x.data_ptr()), C.c_void_p(x.data_ptr()), None,
                                      C.c_void_p(x.data_ptr()), 8, 8, 32, None)
     assert st == fbf.FBF_ERR_RANGE
