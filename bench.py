@@ -377,6 +377,14 @@ def run_batched(fbf, torch, dev, stream, imgs, specs_raw, steps):
         ms = timed(lambda: fbf.fbf_filter_batched(plan, stream))
         res["plan_" + f] = {"ms": round(ms, 3), "mpix_s": round(total_px / ms / 1e3, 1), "graph_launches": 1,
                             "schedule": kind, "autotune_ms": round(tuned_ms, 3)}
+    # every candidate schedule of the single FP16 form, captured on its own
+    cand = {}
+    for k in ("persistent_tc", "per_image_form", "per_image_form_streams"):
+        with torch.cuda.stream(stream):
+            p1 = fbf.fbf_plan_create(xs, ys, specs, "tc_fp16_single", "reflect", schedule=k)
+        cand[k] = round(timed(lambda: fbf.fbf_filter_batched(p1, stream)), 3)
+        p1.destroy()
+    res["plan_tc_fp16_single"]["candidates_ms"] = cand
     for f in FORMS_ALL + ["auto"]:
         ms = timed(separate(f))
         res["separate_" + f] = {"ms": round(ms, 3), "mpix_s": round(total_px / ms / 1e3, 1), "launches": len(imgs)}

@@ -207,7 +207,8 @@ typedef enum {
   FBF_SCHEDULE_PER_IMAGE_FP32 = 2,  /* one single-image FP32 launch per image         */
   FBF_SCHEDULE_PER_IMAGE_FORM = 3,  /* one launch per image in the plan's form        */
   FBF_SCHEDULE_PER_IMAGE_FP32_STREAMS = 4, /* PER_IMAGE_FP32 on 4 concurrent branches */
-  FBF_SCHEDULE_PER_IMAGE_FORM_STREAMS = 5  /* PER_IMAGE_FORM on 4 concurrent branches */
+  FBF_SCHEDULE_PER_IMAGE_FORM_STREAMS = 5, /* PER_IMAGE_FORM on 4 concurrent branches */
+  FBF_SCHEDULE_PERSISTENT_TC = 6           /* one persistent tensor-core launch       */
 } fbf_schedule;
 
 /*
@@ -221,9 +222,15 @@ typedef enum {
  * spread over four concurrent graph branches (largest images first, each to
  * the least loaded branch), so that small images and the last wave of one
  * image's tiles share the GPU with other images (PERSISTENT needs every
- * W <= 32).  form FP32: PERSISTENT,
- * PERSISTENT_WIDE and both PER_IMAGE_FP32 schedules; AUTO: all six (per image
- * as fbf_filter's AUTO); a tensor-core form: both PER_IMAGE_FORM schedules.
+ * W <= 32), and PERSISTENT_TC: one launch of the tensor-core kernel with one
+ * CTA per SM taking (image, tile) items of all images -- sorted by estimated
+ * cost, most expensive first, CTA b taking items b, b + #SMs, ... -- and
+ * rebuilding the image's Toeplitz matrices whenever its next item belongs to
+ * another image (tiles 32 x (128 - 2W), every W <= FBF_WMAX, T <= 255).
+ * form FP32: PERSISTENT, PERSISTENT_WIDE and both PER_IMAGE_FP32 schedules;
+ * AUTO: those and both PER_IMAGE_FORM schedules (per image as fbf_filter's
+ * AUTO); TC_FP16_SINGLE: PERSISTENT_TC and both PER_IMAGE_FORM schedules; the
+ * split tensor-core forms: both PER_IMAGE_FORM schedules.
  * The concurrent schedules need images whose outputs overlap no other
  * image's output or input.
  * With more than one candidate the plan autotunes: it replays every

@@ -16,7 +16,10 @@
 //   PER_IMAGE_FP32   one launch per image of the single-image FP32 kernel
 //                    (compile-time tap counts, running sums for box windows);
 //   PER_IMAGE_FORM   one launch per image in the plan's form (AUTO: the
-//                    per-image choice of fbf_filter; the tensor-core forms).
+//                    per-image choice of fbf_filter; the tensor-core forms);
+//   PERSISTENT_TC    one launch of the second tensor-core layout (single FP16
+//                    form) over cost-sorted (image, tile) items of every
+//                    image, CTA b taking items b, b + #SMs, ... (fbf_tc2_batched.cu).
 //
 // Autotuning: when more than one candidate applies (forms AUTO and FP32), the
 // plan replays every candidate's graph on its own images (writing the
@@ -105,6 +108,7 @@ struct Persistent {
 struct Candidate {
   fbf_schedule kind = FBF_SCHEDULE_PERSISTENT;
   Persistent tables;
+  Tc2BatchTables tc2;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   double ms = 0.0;
@@ -114,6 +118,7 @@ struct Candidate {
     exec = nullptr;
     graph = nullptr;
     tables.release();
+    tc2.release();
   }
 };
 
@@ -192,6 +197,24 @@ fbf_status capture_persistent(int device, int border, Candidate *c, cudaStream_t
   cudaMemsetAsync(c->tables.d_counter, 0, sizeof(int), cs);
   if (c->tables.n_items > 0) kern<<<grid, kBNT, smem, cs>>>(args);
   if (cudaStreamEndCapture(cs, &c->graph) != cudaSuccess || !c->graph) return FBF_ERR_CUDA;
+  return cudaGraphInstantiate(&c->exec, c->graph, 0) == cudaSuccess ? FBF_OK : FBF_ERR_CUDA;
+}
+
+// Capture of the persistent tensor-core schedule: one launch over the batch's
+// tables (run once before the capture for the kernel's one-time host set-up).
+fbf_status capture_persistent_tc(const std::vector<FilterArgs> &args, int mode, Candidate *c, cudaStream_t cs) {
+  fbf_status st = c->tc2.build(args.data(), (int)args.size());
+  if (st != FBF_OK) return st;
+  st = launch_tc2_batch(c->tc2, mode, cs);
+  if (st != FBF_OK) return st;
+  if (cudaStreamSynchronize(cs) != cudaSuccess) return FBF_ERR_CUDA;
+  if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return FBF_ERR_CUDA;
+  st = launch_tc2_batch(c->tc2, mode, cs);
+  cudaGraph_t g = nullptr;
+  const bool ended = cudaStreamEndCapture(cs, &g) == cudaSuccess;
+  c->graph = g;
+  if (st != FBF_OK) return st;
+  if (!ended || !g) return FBF_ERR_CUDA;
   return cudaGraphInstantiate(&c->exec, c->graph, 0) == cudaSuccess ? FBF_OK : FBF_ERR_CUDA;
 }
 
@@ -340,6 +363,9 @@ static fbf_status plan_create(const fbf_image_desc *descs, int n, fbf_form form,
   // Candidate schedules of this form.
   std::vector<fbf_schedule> kinds;
   if (tc) {
+    bool t_ok = true;  // the persistent tensor-core kernel's 2T-phase table holds 2T <= 510
+    for (const FilterArgs &a : args) t_ok = t_ok && a.twoT >= 2 && a.twoT <= 510;
+    if (form == FBF_FORM_TC_FP16_SINGLE && t_ok) kinds.push_back(FBF_SCHEDULE_PERSISTENT_TC);
     kinds.push_back(FBF_SCHEDULE_PER_IMAGE_FORM);
     kinds.push_back(FBF_SCHEDULE_PER_IMAGE_FORM_STREAMS);
   } else {
@@ -373,6 +399,8 @@ static fbf_status plan_create(const fbf_image_desc *descs, int n, fbf_form form,
     } else if (k == FBF_SCHEDULE_PERSISTENT_WIDE) {
       st = build_persistent<64, 96>(args, &c.tables);
       if (st == FBF_OK) st = capture_persistent<64, 96, 1, 16>(p->device, (int)border, &c, cs);
+    } else if (k == FBF_SCHEDULE_PERSISTENT_TC) {
+      st = capture_persistent_tc(args, 2, &c, cs);
     } else {
       const bool fp32 = k == FBF_SCHEDULE_PER_IMAGE_FP32 || k == FBF_SCHEDULE_PER_IMAGE_FP32_STREAMS;
       const bool streams = k == FBF_SCHEDULE_PER_IMAGE_FP32_STREAMS || k == FBF_SCHEDULE_PER_IMAGE_FORM_STREAMS;
@@ -408,7 +436,7 @@ extern "C" fbf_status fbf_plan_create(const fbf_image_desc *descs, int n, fbf_fo
 extern "C" fbf_status fbf_plan_create_schedule(const fbf_image_desc *descs, int n, fbf_form form,
                                                fbf_border border, fbf_schedule schedule, fbf_plan **out) {
   if (out) *out = nullptr;
-  if ((int)schedule < 0 || (int)schedule > (int)FBF_SCHEDULE_PER_IMAGE_FORM_STREAMS) return FBF_ERR_INVALID_ARGUMENT;
+  if ((int)schedule < 0 || (int)schedule > (int)FBF_SCHEDULE_PERSISTENT_TC) return FBF_ERR_INVALID_ARGUMENT;
   return plan_create(descs, n, form, border, (int)schedule, out);
 }
 

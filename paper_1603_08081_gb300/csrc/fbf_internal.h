@@ -6,6 +6,7 @@
 #include <cstdint>
 
 #include <cuda.h>
+#include <vector_types.h>
 
 #include "fbf.h"
 
@@ -71,6 +72,37 @@ fbf_status launch_tc2_u8(const FilterArgs &a, int mode, cudaStream_t s);
 fbf_status launch_tc2_single(const FilterArgs &a, cudaStream_t s);
 fbf_status launch_tc2_fp16(const FilterArgs &a, cudaStream_t s);
 fbf_status launch_tc2_bf16(const FilterArgs &a, cudaStream_t s);
+
+// Work of one persistent launch of the second tensor-core layout over a batch
+// of images, each with its own window, coefficients and TMA map: a list of
+// (image, tile) items (sorted by the host, most expensive first) of which CTA
+// b takes items b, b + gridDim.x, ...; when a CTA moves to another image it
+// rebuilds the image's row Toeplitz blocks, column Toeplitz matrix and (if T
+// changed) 2T-phase table before the tile's first MMA.  (A single image takes
+// its arguments and TMA map from the kernel parameters instead.)
+struct Tc2Batch {
+  const FilterArgs *imgs;   // per image: arguments with tiles_x / ntiles of the 32 x (128 - 2W) tiling
+  const CUtensorMap *maps;  // per image: TMA map of 144 x 128 boxes (64-byte aligned)
+  const int *map_ok;        // per image: 1 when its map is valid, 0 for plain loads
+  const int2 *items;        // (image, tile index within the image)
+  int nitems;
+};
+
+// Device tables of a batch (one allocation): per-image arguments with the
+// 32 x (128 - 2W) tiling, TMA maps, and the items sorted by estimated cost
+// (harmonics x row chunks per tile), most expensive first, each image's tiles
+// in order.  build() skips empty images; FBF_ERR_RANGE when an image's W or T
+// lies outside the layout (W <= FBF_WMAX, 2T <= 510).
+struct Tc2BatchTables {
+  Tc2Batch b{};
+  void *mem = nullptr;
+  int wmax = 0;
+  fbf_status build(const FilterArgs *args, int n);
+  void release();
+};
+// One persistent launch over a batch; mode as for launch_tc_u8.
+// FBF_ERR_UNSUPPORTED outside the instantiations (today: the single FP16 form).
+fbf_status launch_tc2_batch(const Tc2BatchTables &t, int mode, cudaStream_t s);
 
 // Host helpers shared by the launchers (fbf_host.cu, fbf_api.cu).
 // 2-D u8 TMA map of an image with a box of bw x bh bytes, cached per (device,

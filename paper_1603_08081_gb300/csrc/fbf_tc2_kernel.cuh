@@ -76,7 +76,8 @@ using namespace tc;
 constexpr int kNC = 512;           // compute threads per CTA (four groups of four warps)
 constexpr int kNT = kNC + 128;     // + one warpgroup of MMA / TMA issuers
 constexpr int kRegCompute = 112;   // registers per thread after setmaxnreg: compute warpgroups
-constexpr int kRegIssue = 24;      //   and the issuing warpgroup (4 x 112 + 24 <= 5 x 96 per SM sub-partition)
+constexpr int kRegIssue = 24;      //   and the issuing warpgroup (4 x 112 + 24 <= 5 x 96 per SM sub-partition);
+constexpr int kRegIssueBatch = 32; //   32 in batched launches (4 x 112 + 32 = 5 x 96)
 constexpr int kLanes = 128;        // TMEM lanes = ext rows per tile
 constexpr int kBX = 32;            // output columns per tile
 constexpr int kTrigEntries = 510;  // 2T <= 510 (T <= 255)
@@ -207,10 +208,10 @@ __device__ __forceinline__ float from16(unsigned short x) {
 // (split forms, with SHARED): A1 holds one data part at a time -- the row MMAs
 // of a harmonic run in two rounds, hi part then lo part, with the lo part
 // modulated into A1 between them -- so that wide windows fit the TMEM.
-template <int BF, int NSPLIT, int KXC, int SHARED, int SEQ = 0>
-__global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constant__ FilterArgs a,
-                                                             const __grid_constant__ CUtensorMap tmap,
-                                                             const Tc2Extra x) {
+// BATCH: the work source (a1 / map1 for one image, bt for a batch).
+template <int BF, int NSPLIT, int KXC, int SHARED, int SEQ, bool BATCH>
+__device__ __forceinline__ void tc2_body(const FilterArgs *a1, const CUtensorMap *map1, const Tc2Batch &bt,
+                                         const Tc2Extra &x) {
   constexpr int kParts = NSPLIT > 1 ? 2 : 1;   // data parts (hi, lo)
   constexpr int kA1Parts = SEQ ? 1 : kParts;   // data parts held in A1 at a time
   constexpr int kCopies = trig_copies(NSPLIT);
@@ -240,12 +241,7 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constan
   const bool col_issuer = lane == 0 && iw == 0, row_issuer = lane == 0 && (iw == 1 || iw == 2),
              tma_issuer = lane == 0 && iw == 3;
   const int r = 32 * q + lane;            // ext row = TMEM lane of this thread
-  const int W = a.W, Wp = wpad(W), KX = kx_of(W), kcr = KX / 16;
-  const int H = a.H, Wd = a.Wd, BYv = kLanes - 2 * W;
-  const int twoT = a.twoT;
-  const float c0 = 0.5f * a.T;  // intensity centre
-  const bool reflect = a.border == FBF_BORDER_REFLECT;
-  const int nunits = KX / 8, demod_u = Wp / 8 + h;
+  const int nitems = BATCH ? bt.nitems : a1->ntiles;
 
   unsigned char *trig = smem + Ly.trig;         // [zero entry][entry m = 0 .. 2T-1], 16 copies of float2
   unsigned char *B2 = smem + Ly.b2;
@@ -258,6 +254,33 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constan
   uint32_t *tmem_base_s = reinterpret_cast<uint32_t *>(smem + Ly.bar + 32);
   // byte offset of entry 0 of the trig table, this lane's copy folded in
   const int tb = (int)Ly.trig + kCopies * 8;
+  const int bv = tid & 255, bhalf = tid >> 8;  // channel-table entry built by this thread
+
+  // ---- the image of the current tile and what follows from it (one image:
+  // set once; batch: when a CTA's item moves to another image)
+  const FilterArgs *A = a1;
+  int W = 0, Wp = 0, KX = 0, kcr = 0, H = 0, Wd = 0, BYv = 0, twoT = 2, nunits = 0, demod_u = 0, lim = 0,
+      bstep = 0;
+  float c0 = 0.f;  // intensity centre T / 2
+  bool reflect = false;
+  auto set_image = [&](const FilterArgs *p) {
+    A = p;
+    W = p->W;
+    Wp = wpad(W);
+    KX = kx_of(W);
+    kcr = KX / 16;
+    H = p->H;
+    Wd = p->Wd;
+    BYv = kLanes - 2 * W;
+    twoT = p->twoT;
+    c0 = 0.5f * p->T;
+    reflect = p->border == FBF_BORDER_REFLECT;
+    nunits = KX / 8;
+    demod_u = Wp / 8 + h;
+    lim = twoT * kCopies * 8;  // offset of entry 2T
+    bstep = (bv % twoT) * (kCopies * 8);
+  };
+  set_image(BATCH ? bt.imgs + (nitems > 0 && (int)blockIdx.x < nitems ? bt.items[blockIdx.x].x : 0) : a1);
 
   // ---- unit assignment: the demodulation unit, then halo unit j of group h is
   // the (h + 4 j)-th of the units left and right of the four demodulation units.
@@ -266,6 +289,63 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constan
     if (k < left) return k;
     const int u = k - left + Wp / 8 + 4;
     return u < nunits ? u : -1;
+  };
+
+  // ---- per-image tables (threads t0, t0 + stride, ...).  trig: entry m (cos,
+  // sin)(pi m / T) in 16 copies; the zero entry (index -1) holds the channels of
+  // pixels outside the image (TRUNCATE).
+  auto setup_trig = [&](int t0, int stride) {
+    for (int m = t0 - 1; m < twoT; m += stride) {
+      float sn = 0.f, cs = 0.f;
+      if (m >= 0) sincospif((float)m / A->T, &sn, &cs);
+      unsigned char *ent = trig + kCopies * 8 + m * kCopies * 8;
+#pragma unroll
+      for (int k = 0; k < kCopies; ++k)  // rotated so that a warp's stores spread over the banks
+        *reinterpret_cast<float2 *>(ent + ((k + lane) & (kCopies - 1)) * 8) = make_float2(cs, sn);
+    }
+  };
+  // Row Toeplitz blocks (shared memory, K-major, 1 KB each): chunk i, output x,
+  // K index k = ext column 16 i + k: tap 16 i + k - Wp - x + W.
+  auto setup_row_toeplitz = [&](int t0, int stride) {
+    for (int e = t0; e < kcr * kWParts * 512; e += stride) {
+      const int blk = e >> 9, el = e & 511, n = el >> 4, k = el & 15;
+      const int i = blk / kWParts, bp = blk % kWParts;
+      const int t = 16 * i + k - Wp - n + W;
+      const float wv = (t >= 0 && t <= 2 * W) ? A->w[t] : 0.f;
+      const unsigned short hi = to16<BF>(wv);
+      const unsigned short v = bp == 0 ? hi : to16<BF>(wv - from16<BF>(hi));
+      const int off = (n & 7) * 16 + (n >> 3) * 256 + (k & 7) * 2 + (k >> 3) * 128;
+      *reinterpret_cast<unsigned short *>(BR + (size_t)blk * 1024 + off) = v;
+    }
+  };
+  // Column Toeplitz matrix in TMEM (compute threads): lane m (output ext row),
+  // K = input ext row 16 i + k: w[16 i + k - m + W] inside the band; group h
+  // writes chunks 2h, 2h+1.
+  constexpr uint32_t tmem = 0;
+  const uint32_t lane_base = (uint32_t)(32 * q) << 16;
+  auto setup_col_toeplitz = [&]() {
+    const int m = r;
+#pragma unroll
+    for (int ii = 0; ii < 2; ++ii) {
+      const int i = 2 * h + ii;
+      uint32_t vh[8], vl[8] = {};
+#pragma unroll
+      for (int kk = 0; kk < 8; ++kk) {
+        float wv[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int t = 16 * i + 2 * kk + e - m + W;
+          wv[e] = (t >= 0 && t <= 2 * W) ? A->w[t] : 0.f;
+        }
+        if constexpr (kWParts == 2)
+          split2<BF>(wv[0], wv[1], vh[kk], vl[kk]);
+        else
+          vh[kk] = pack2<BF>(wv[0], wv[1]);
+      }
+      tmem_st_x8(tmem + lane_base + kT + (uint32_t)(8 * i), vh);
+      if constexpr (kWParts == 2) tmem_st_x8(tmem + lane_base + kT + 64 + (uint32_t)(8 * i), vl);
+    }
+    tmem_st_wait();
   };
 
   // ---- one-time setup -------------------------------------------------------
@@ -280,27 +360,9 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constan
     mbar_init(mbarD, 3);  // drain: one commit per MMA-issuing thread
     mbar_fence_init();
   }
-  // trig table: entry m (cos, sin)(pi m / T) in 16 copies; the zero entry
-  // (index -1) holds the channels of pixels outside the image (TRUNCATE).
-  for (int m = tid - 1; m < twoT; m += kNT) {
-    float sn = 0.f, cs = 0.f;
-    if (m >= 0) sincospif((float)m / a.T, &sn, &cs);
-    unsigned char *ent = trig + kCopies * 8 + m * kCopies * 8;
-#pragma unroll
-    for (int k = 0; k < kCopies; ++k)  // rotated so that a warp's stores spread over the banks
-      *reinterpret_cast<float2 *>(ent + ((k + lane) & (kCopies - 1)) * 8) = make_float2(cs, sn);
-  }
-  // Row Toeplitz blocks (shared memory, K-major, 1 KB each): chunk i, output x,
-  // K index k = ext column 16 i + k: tap 16 i + k - Wp - x + W.
-  for (int e = tid; e < kcr * kWParts * 512; e += kNT) {
-    const int blk = e >> 9, el = e & 511, n = el >> 4, k = el & 15;
-    const int i = blk / kWParts, bp = blk % kWParts;
-    const int t = 16 * i + k - Wp - n + W;
-    const float wv = (t >= 0 && t <= 2 * W) ? a.w[t] : 0.f;
-    const unsigned short hi = to16<BF>(wv);
-    const unsigned short v = bp == 0 ? hi : to16<BF>(wv - from16<BF>(hi));
-    const int off = (n & 7) * 16 + (n >> 3) * 256 + (k & 7) * 2 + (k >> 3) * 128;
-    *reinterpret_cast<unsigned short *>(BR + (size_t)blk * 1024 + off) = v;
+  if (!BATCH) {  // one image: its tables once, by every thread (batch: per image, below)
+    setup_trig(tid, kNT);
+    setup_row_toeplitz(tid, kNT);
   }
   // zero entries (v = 256) of both channel-table buffers: pixels outside the image
   if (tid < 2 * kEntry / 16)
@@ -313,55 +375,29 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constan
   // All 512 columns are allocated, so the allocation starts at lane 0, column 0:
   // the MMA operands below are compile-time TMEM addresses (issued from uniform
   // registers).  Anything else is refused as a failed launch.
-  constexpr uint32_t tmem = 0;
   const bool tmem_ok = *tmem_base_s == 0;
-  const uint32_t lane_base = (uint32_t)(32 * q) << 16;
-  // Column Toeplitz matrix in TMEM: lane m (output ext row), K = input ext row
-  // 16 i + k: w[16 i + k - m + W] inside the band; group h writes chunks 2h, 2h+1.
-  if (tmem_ok && compute) {
-    const int m = r;
-#pragma unroll
-    for (int ii = 0; ii < 2; ++ii) {
-      const int i = 2 * h + ii;
-      uint32_t vh[8], vl[8] = {};
-#pragma unroll
-      for (int kk = 0; kk < 8; ++kk) {
-        float wv[2];
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          const int t = 16 * i + 2 * kk + e - m + W;
-          wv[e] = (t >= 0 && t <= 2 * W) ? a.w[t] : 0.f;
-        }
-        if constexpr (kWParts == 2)
-          split2<BF>(wv[0], wv[1], vh[kk], vl[kk]);
-        else
-          vh[kk] = pack2<BF>(wv[0], wv[1]);
-      }
-      tmem_st_x8(tmem + lane_base + kT + (uint32_t)(8 * i), vh);
-      if constexpr (kWParts == 2) tmem_st_x8(tmem + lane_base + kT + 64 + (uint32_t)(8 * i), vl);
-    }
-    tmem_st_wait();
-  }
+  if (!BATCH && tmem_ok && compute) setup_col_toeplitz();
 
-  // ---- TMA box of a tile: columns from floor16(tx0 - Wp), rows from ty0 - W.
-  auto tile_org = [&](int t, int &ty0, int &tx0) {
-    const int ty = t / a.tiles_x;
-    ty0 = ty * BYv;
-    tx0 = (t - ty * a.tiles_x) * kBX;
-  };
-  auto box_x0 = [&](int tx0) -> int { return (tx0 - Wp) >= 0 ? ((tx0 - Wp) & ~15) : -((Wp - tx0 + 15) & ~15); };
-  auto issue_tma = [&](int t) {  // one thread
-    int ty0, tx0;
-    tile_org(t, ty0, tx0);
+  // ---- items: image and tile; the TMA box of a tile starts at column
+  // floor16(tx0 - Wp) and row ty0 - W.
+  auto item_image = [&](int it) -> int { return BATCH ? bt.items[it].x : 0; };
+  auto item_tile = [&](int it) -> int { return BATCH ? bt.items[it].y : it; };
+  auto item_tma = [&](int it) -> bool { return BATCH ? bt.map_ok[bt.items[it].x] != 0 : x.use_tma != 0; };
+  auto box_x0 = [](int tx0, int wp) -> int { return (tx0 - wp) >= 0 ? ((tx0 - wp) & ~15) : -((wp - tx0 + 15) & ~15); };
+  auto issue_tma = [&](int it) {  // one thread: the box of item it (any image)
+    const int img = item_image(it), t = item_tile(it);
+    const FilterArgs *p = BATCH ? bt.imgs + img : a1;
+    const int w = p->W, by = kLanes - 2 * w, ty = t / p->tiles_x;
+    const int tx0 = (t - ty * p->tiles_x) * kBX;
     mbar_arrive_expect_tx(mbarT, (uint32_t)(kBoxW * kLanes));
-    tma_load_2d(box, &tmap, box_x0(tx0), ty0 - W, mbarT);
+    tma_load_2d(box, BATCH ? static_cast<const void *>(bt.maps + img) : static_cast<const void *>(map1),
+                box_x0(tx0, wpad(w)), ty * by - w, mbarT);
   };
-  const bool use_tma = x.use_tma != 0;
   bool tma_pending = false;
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
-  if (use_tma && blockIdx.x < a.ntiles) {
+  if ((int)blockIdx.x < nitems && item_tma(blockIdx.x)) {
     if (tma_issuer) issue_tma(blockIdx.x);
     tma_pending = true;
   }
@@ -377,7 +413,6 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constan
   int mo[8];
   uint32_t vo[4];
   const int copy8 = (lane & (kCopies - 1)) * 8;
-  const int lim = twoT * kCopies * 8;  // offset of entry 2T
   auto wrap = [&](int m) -> int { return m >= lim ? m - lim : m; };
   unsigned char *t16 = smem + Ly.t16;
 
@@ -399,8 +434,6 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constan
   // ---- channel table of harmonic n into buffer b: thread t builds entry
   // v = t % 256 (half of its copies); bm is the byte offset of its phase
   // n v mod 2T in the 2T-phase table (advanced here, harmonics in order).
-  const int bv = tid & 255, bhalf = tid >> 8;
-  const int bstep = (bv % twoT) * (kCopies * 8);
   int bm = 0;
   auto build_table = [&](int n, int b) {
     const float2 cs = *reinterpret_cast<const float2 *>(trig + tb + bm + copy8);
@@ -409,7 +442,7 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constan
     // channels (rounding d_n-scaled values to FP16 once doubles its error: an
     // FP64 emulation of both on the 2048^2 image, sigma_s = 3, sigma_r = 40
     // gives 0.043 against 0.020 gray) and multiplies by d_n when demodulating
-    const float dn = kFold ? a.d[n] : 1.f, fv = (float)bv - c0;
+    const float dn = kFold ? A->d[n] : 1.f, fv = (float)bv - c0;
     const float dc = dn * cs.x, ds = dn * cs.y, dfc = dn * (fv * cs.x), dfs = dn * (fv * cs.y);
     unsigned char *ent = t16 + (size_t)b * kT16Bytes + bv * kEntry;
     if constexpr (kParts == 2) {
@@ -570,7 +603,7 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constan
     }
     tmem_ld_wait_dep(*reinterpret_cast<uint32_t(*)[16]>(&v[0]));
     tmem_ld_wait_dep(*reinterpret_cast<uint32_t(*)[16]>(&v[16]));
-    const float dn = kFold ? 1.f : a.d[n];
+    const float dn = kFold ? 1.f : A->d[n];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const float tc = dn * cs[j].x, ts = dn * cs[j].y;
@@ -598,9 +631,15 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constan
   // below, issuing at each point what the barrier made ready.
   bool ok = tmem_ok;
   if (!compute) {
-    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(kRegIssue));
-    for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
-      if (use_tma) {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(BATCH ? kRegIssueBatch : kRegIssue));
+    for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
+      int K = A->K;
+      if (BATCH) {  // this item's image: its harmonics and row chunks
+        const FilterArgs *p = bt.imgs + item_image(it);
+        K = p->K;
+        kcr = kx_of(p->W) / 16;
+      }
+      if (item_tma(it)) {
         if (mbar_wait_bounded(mbarT, phT, polls)) {
           phT ^= 1;
           tma_pending = false;
@@ -612,12 +651,13 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constan
           break;
         }
       }
-      if (!phase_sync()) {  // the compute warps have read the box
+      if (!phase_sync()) {  // the compute warps have read the box (and set up a new image)
         ok = false;
         break;
       }
-      if (use_tma && tile + (int)gridDim.x < a.ntiles) {
-        if (tma_issuer) issue_tma(tile + gridDim.x);
+      const int nx = it + (int)gridDim.x;
+      if (nx < nitems && item_tma(nx)) {
+        if (tma_issuer) issue_tma(nx);
         tma_pending = true;
       }
       if (!(ok = phase_sync())) break;  // table of harmonic 0
@@ -628,8 +668,8 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constan
         if (row_issuer) issue_row(1);
       }
       if (!(ok = phase_sync())) break;  // B2 <- harmonic 0
-      for (int n = 0; n < a.K; ++n) {
-        const bool more = n + 1 < a.K;
+      for (int n = 0; n < K; ++n) {
+        const bool more = n + 1 < K;
         if (col_issuer) issue_col();  // C(n)
         if (!(ok = phase_sync())) break;  // A1 <- harmonic n + 1 (SEQ: hi part)
         if (SHARED) {
@@ -648,11 +688,12 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constan
     finish(ok);
   } else {
     asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(kRegCompute));
-    for (int tile = blockIdx.x; tile < a.ntiles && ok; tile += gridDim.x) {
-      int ty0, tx0;
-      tile_org(tile, ty0, tx0);
-      const int iy = ty0 - W + r;  // image row of this thread's ext row
-      if (use_tma) {
+    int cur = -1;       // batch: image whose tables are set up
+    float cur_T = -1.f; // batch: T of the 2T-phase table
+    for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
+      const int t = item_tile(it);
+      const bool tma_here = item_tma(it);
+      if (tma_here) {
         if (mbar_wait_bounded(mbarT, phT, polls)) {
           phT ^= 1;
           tma_pending = false;
@@ -664,13 +705,31 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constan
           break;
         }
       }
+      if (BATCH) {
+        const int img = item_image(it);
+        if (img != cur) {  // another image: its tables (no MMA is in flight between tiles)
+          cur = img;
+          set_image(bt.imgs + img);
+          if (A->T != cur_T) {
+            setup_trig(tid, kNC);
+            cur_T = A->T;
+          }
+          setup_row_toeplitz(tid, kNC);
+          if (tmem_ok) setup_col_toeplitz();
+        }
+      }
+      const int ty = t / A->tiles_x;
+      const int ty0 = ty * BYv, tx0 = (t - ty * A->tiles_x) * kBX;
+      const int iy = ty0 - W + r;  // image row of this thread's ext row
       // ---- load the thread's pixels: REFLECT mirrors (repeatedly, for windows
       // wider than the image); TRUNCATE marks pixels outside the image, whose
       // channels are zero (the zero table entries, no phase step).
       {
-        const int bx0 = box_x0(tx0), by0 = ty0 - W;
+        const int bx0 = box_x0(tx0, Wp), by0 = ty0 - W;
         bool row_in = iy >= 0 && iy < H;
         const int sy = reflect ? reflect_index(iy, H) : iy;
+        const unsigned char *in = static_cast<const unsigned char *>(A->in);
+        const size_t in_pitch = A->in_pitch;
   #pragma unroll
         for (int uu = 0; uu < UPT; ++uu) {
           const int u = uu == 0 ? demod_u : halo_unit(uu - 1);
@@ -678,21 +737,21 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constan
   #pragma unroll
           for (int j = 0; j < 8; ++j) {
             const int ix = tx0 - Wp + 8 * (u < 0 ? 0 : u) + j;
-            bool in = row_in && ix >= 0 && ix < Wd;
+            bool in_img = row_in && ix >= 0 && ix < Wd;
             int sx = ix;
             if (reflect) {
               sx = reflect_index(ix, Wd);
-              in = true;
+              in_img = true;
             }
             int v = 0;
-            if (in && u >= 0) {
+            if (in_img && u >= 0) {
               const int by = (reflect ? sy : iy) - by0, bx = sx - bx0;
-              if (use_tma && by >= 0 && by < kLanes && bx >= 0 && bx < kBoxW)
+              if (tma_here && by >= 0 && by < kLanes && bx >= 0 && bx < kBoxW)
                 v = box[by * kBoxW + bx];
               else
-                v = __ldg(static_cast<const unsigned char *>(a.in) + (size_t)(reflect ? sy : iy) * a.in_pitch + sx);
+                v = __ldg(in + (size_t)(reflect ? sy : iy) * in_pitch + sx);
             }
-            const bool valid = in && u >= 0;
+            const bool valid = in_img && u >= 0;
             po[uu][j] = (valid ? v : kZeroV) * kEntry + copy_off;
             if (uu == 0) {
               mo[j] = valid ? copy8 : copy8 - kCopies * 8;  // entry m = 0, or the zero entry
@@ -706,14 +765,17 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constan
         }
       }
       // every thread has read the box: the next tile's copy may overwrite it
+      // (and a new image's row Toeplitz blocks are visible to the MMAs)
       fence_proxy_async_smem();
       if (!phase_sync()) {
         ok = false;
         break;
       }
-      if (use_tma && tile + (int)gridDim.x < a.ntiles) tma_pending = true;
+      const int nx = it + (int)gridDim.x;
+      if (nx < nitems && item_tma(nx)) tma_pending = true;
   #pragma unroll
       for (int j = 0; j < 8; ++j) P[j] = Q[j] = 0.f;
+      const int K = A->K;
 
       // ---- prologue: the tables of harmonics 0 and 1; harmonic 0 through the row
       // pass and the re-split.  The table of harmonic n is in buffer n % 2.
@@ -722,7 +784,7 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constan
       if (!(ok = phase_sync())) break;
       modulate(0, 0);
       if (!(ok = phase_sync())) break;
-      if (a.K > 1) build_table(1, 1);
+      if (K > 1) build_table(1, 1);
       wait_bar(mbarR, phR);
       if (SEQ) {  // the lo part through the same A1
         modulate(0, 1);
@@ -732,13 +794,13 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constan
       resplit();
       if (!(ok = phase_sync())) break;
 
-      for (int n = 0; n < a.K; ++n) {
-        const bool more = n + 1 < a.K;
+      for (int n = 0; n < K; ++n) {
+        const bool more = n + 1 < K;
         if (more) modulate((n + 1) & 1, 0);  // A1 <- harmonic n + 1 (while C(n): B2 -> D2 runs)
         if (!(ok = phase_sync())) break;
         // the table of n + 2 replaces that of n (read by the modulation of n, done)
         if (SHARED) {
-          if (n + 2 < a.K) build_table(n + 2, n & 1);
+          if (n + 2 < K) build_table(n + 2, n & 1);
           wait_bar(mbarC, phC);
           demod(n);
           if (!(ok = phase_sync())) break;
@@ -753,7 +815,7 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constan
           }
         } else {
           // R(n+1): A1 -> D1 runs meanwhile
-          if (n + 2 < a.K) build_table(n + 2, n & 1);
+          if (n + 2 < K) build_table(n + 2, n & 1);
           wait_bar(mbarC, phC);
           demod(n);
           if (more) {
@@ -767,7 +829,7 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constan
 
       // ---- fhat = P / Q + c0 for this thread's 8 pixels of output row iy
       if (r >= W && r < kLanes - W && iy < H) {
-        float *orow = reinterpret_cast<float *>(reinterpret_cast<char *>(a.out) + (size_t)iy * a.out_pitch);
+        float *orow = reinterpret_cast<float *>(reinterpret_cast<char *>(A->out) + (size_t)iy * A->out_pitch);
         const int x0 = tx0 + 8 * h;
   #pragma unroll
         for (int j = 0; j < 8; ++j)
@@ -776,6 +838,22 @@ __global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constan
     }
     finish(ok);
   }
+}
+
+// One image (the single-image entry points).
+template <int BF, int NSPLIT, int KXC, int SHARED, int SEQ = 0>
+__global__ void __launch_bounds__(kNT, 1) fbf_tc2_u8_kernel(const __grid_constant__ FilterArgs a,
+                                                             const __grid_constant__ CUtensorMap tmap,
+                                                             const Tc2Extra x) {
+  const Tc2Batch none{};
+  tc2_body<BF, NSPLIT, KXC, SHARED, SEQ, false>(&a, &tmap, none, x);
+}
+
+// A batch of images in one persistent launch (batched plans).
+template <int BF, int NSPLIT, int KXC, int SHARED, int SEQ = 0>
+__global__ void __launch_bounds__(kNT, 1) fbf_tc2_batched_kernel(const __grid_constant__ Tc2Batch b,
+                                                                  const Tc2Extra x) {
+  tc2_body<BF, NSPLIT, KXC, SHARED, SEQ, true>(nullptr, nullptr, b, x);
 }
 
 }  // namespace tc2
@@ -812,6 +890,31 @@ fbf_status launch_cfg(const FilterArgs &a0, cudaStream_t s) {
   Tc2Extra x{device_error_word(), wait_polls(), use_tma};
   if (!x.err) return FBF_ERR_CUDA;
   kern<<<grid, kNT, Ly.bytes, s>>>(a, map, x);
+  return cuda_status(cudaGetLastError());
+}
+
+// Host launcher of a batch (device tables prepared by the caller, every image
+// within the instantiation's window): one persistent CTA per SM, at most one
+// per item.
+template <int BF, int NSPLIT, int KXC, int SHARED, int SEQ = 0>
+fbf_status launch_batch_cfg(const Tc2Batch &b, cudaStream_t s) {
+  if (b.nitems <= 0) return FBF_OK;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return FBF_ERR_CUDA;
+  const int sms = sm_count(dev);
+  if (sms <= 0) return FBF_ERR_CUDA;
+  const int grid = b.nitems < sms ? b.nitems : sms;
+  constexpr Layout Ly = layout<NSPLIT, KXC>();
+  auto kern = fbf_tc2_batched_kernel<BF, NSPLIT, KXC, SHARED, SEQ>;
+  static FuncAttrOnce once;
+  if (!once.done(dev)) {
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Ly.bytes) != cudaSuccess)
+      return FBF_ERR_CUDA;
+    once.set(dev);
+  }
+  Tc2Extra x{device_error_word(), wait_polls(), 0};
+  if (!x.err) return FBF_ERR_CUDA;
+  kern<<<grid, kNT, Ly.bytes, s>>>(b, x);
   return cuda_status(cudaGetLastError());
 }
 

@@ -1,7 +1,8 @@
 """GPU parity of the batched plan (fbf_plan_create / fbf_filter_batched): every
 image of an uneven batch, each with its own window, range scale and order K,
 against the FP64 oracle and against the single-image filter, for the
-autotuned FP32 / AUTO plans and the per-image tensor-core plans."""
+autotuned FP32 / AUTO plans, the per-image tensor-core plans and the
+persistent tensor-core plan of the single FP16 form."""
 import numpy as np
 import pytest
 
@@ -136,7 +137,7 @@ FORM_SCHEDULES = {
     "fp32": ["persistent", "persistent_wide", "per_image_fp32", "per_image_fp32_streams"],
     "auto": ["persistent", "persistent_wide", "per_image_fp32", "per_image_fp32_streams", "per_image_form",
              "per_image_form_streams"],
-    "tc_fp16_single": ["per_image_form", "per_image_form_streams"],
+    "tc_fp16_single": ["per_image_form", "per_image_form_streams", "persistent_tc"],
 }
 
 
@@ -164,15 +165,16 @@ def test_every_schedule_explicitly(fbf, form, schedule):
         y.fill_(float("nan"))
     fbf.fbf_filter_batched(plan)
     torch.cuda.synchronize()
-    per_form = "fp32" if schedule.startswith("per_image_fp32") or schedule.startswith("persistent") else form
+    per_form = "fp32" if schedule in ("per_image_fp32", "per_image_fp32_streams", "persistent", "persistent_wide") \
+        else form
     for x, y, y0, sp in zip(xs, ys, first, specs):
         assert torch.equal(y, y0)
         c = fbf.fbf_fit_coeffs("gaussian", sp["sigma_r"], 255.0, sp.get("eps", 1e-3))
         p = fbf.make_params(c, sp["sigma_s"], 0, "gaussian", "reflect", per_form)
         single = fbf.fbf_filter(p, x)
         torch.cuda.synchronize()
-        if schedule.startswith("per_image"):
-            assert torch.equal(single, y)
+        if schedule.startswith("per_image") or schedule == "persistent_tc":
+            assert torch.equal(single, y)  # the same tile arithmetic as the single-image kernels
         else:
             assert torch.max(torch.abs(single - y)).item() <= 1e-4
     plan.destroy()
@@ -186,13 +188,16 @@ def test_schedule_not_of_the_form_is_rejected(fbf):
     x = torch.zeros((40, 40), dtype=torch.uint8, device="cuda")
     y = torch.zeros((40, 40), dtype=torch.float32, device="cuda")
     for form, schedule in (("tc_fp16", "persistent"), ("tc_fp16", "per_image_fp32_streams"),
-                           ("fp32", "per_image_form")):
+                           ("fp32", "per_image_form"), ("fp32", "persistent_tc"), ("tc_fp16", "persistent_tc"),
+                           ("auto", "persistent_tc")):
         with pytest.raises(fbf.FbfError) as e:
             fbf.fbf_plan_create([x], [y], [dict(sigma_s=2.0, sigma_r=30.0)], form, schedule=schedule)
         assert e.value.status == fbf.FBF_ERR_INVALID_ARGUMENT
     h = C.c_void_p()
     arr = (fbf.fbf_image_desc * 1)()
     assert fbf.lib.fbf_plan_create_schedule(arr, 0, fbf.FBF_FORM_FP32, 0, 6, C.byref(h)) == \
+        fbf.FBF_ERR_INVALID_ARGUMENT
+    assert fbf.lib.fbf_plan_create_schedule(arr, 0, fbf.FBF_FORM_TC_FP16_SINGLE, 0, 7, C.byref(h)) == \
         fbf.FBF_ERR_INVALID_ARGUMENT
     assert fbf.lib.fbf_plan_create_schedule(arr, 0, fbf.FBF_FORM_FP32, 0, -1, C.byref(h)) == \
         fbf.FBF_ERR_INVALID_ARGUMENT
@@ -210,7 +215,8 @@ def test_tensor_core_plan(fbf, form):
              dict(sigma_s=2.0, sigma_r=60.0, eps=1e-2), dict(sigma_s=10.0, sigma_r=25.0)]
     imgs = [make_image(h, w, seed=1500 + k) for k, (h, w) in enumerate(shapes)]
     plan, xs, ys = _run_plan(fbf, imgs, specs, form=form)
-    assert plan.schedule()[0] in ("per_image_form", "per_image_form_streams")
+    kinds = ("per_image_form", "per_image_form_streams") + (("persistent_tc",) if form == "tc_fp16_single" else ())
+    assert plan.schedule()[0] in kinds
     tol = 0.15 if form == "tc_fp16_single" else 0.02
     for im, x, y, sp in zip(imgs, xs, ys, specs):
         c = fbf.fbf_fit_coeffs("gaussian", sp["sigma_r"], 255.0, sp.get("eps", 1e-3))
@@ -222,4 +228,77 @@ def test_tensor_core_plan(fbf, form):
         ref = O.alg1(im, O.weights_1d(O.SPATIAL_GAUSSIAN, sp["sigma_s"], W), O.BORDER_REFLECT,
                      np.array(c.coefficients), 255.0)[0]
         assert np.abs(y.cpu().numpy() - ref).max() <= tol
+    plan.destroy()
+
+
+# Per window band of the persistent tensor-core kernel (its instantiation follows
+# the batch's largest W: 16, 32, 48), the (sigma_s, sigma_r) of eight images.
+PTC_SPECS = {
+    16: [(3.0, 30.0), (0.7, 15.0), (5.0, 50.0), (2.0, 60.0), (4.0, 15.0), (1.5, 20.0), (5.3, 40.0), (1.0, 35.0)],
+    32: [(3.0, 30.0), (10.0, 20.0), (6.0, 50.0), (2.0, 60.0), (8.3, 25.0), (1.5, 20.0), (10.6, 40.0), (7.0, 15.0)],
+    48: [(16.0, 30.0), (3.0, 20.0), (12.0, 50.0), (11.0, 60.0), (14.2, 25.0), (1.5, 20.0), (6.0, 40.0), (15.9, 15.0)],
+}
+
+
+@pytest.mark.parametrize("border", ["reflect", "truncate"])
+@pytest.mark.parametrize("band", [16, 32, 48])
+def test_persistent_tc_plan_matches_oracle(fbf, band, border):
+    """The persistent tensor-core schedule (one launch over cost-sorted (image,
+    tile) items of all images; Algorithm 1 per image with its own K from
+    Algorithm 2): ragged shapes down to 1 x 64 and 5 x 7, one image read through a
+    strided view whose pitch breaks TMA's 16-byte rule (plain loads), windows
+    of every band.  Every output equals the single-image filter of the same form
+    bit for bit and Algorithm 1 in FP64 within the form's tolerance; a second
+    replay gives the same outputs."""
+    import torch
+
+    shapes = [(300, 260), (70, 90), (33, 200), (256, 40), (1, 64), (5, 7), (130, 131), (129, 97)]
+    imgs = [make_image(h, w, seed=1700 + 10 * band + k) for k, (h, w) in enumerate(shapes)]
+    xs = [torch.from_numpy(im).cuda() for im in imgs]
+    big = torch.zeros((140, 141), dtype=torch.uint8, device="cuda")  # pitch 141: no TMA map
+    big[3:3 + 129, 5:5 + 97] = xs[7]
+    xs[7] = big[3:3 + 129, 5:5 + 97]
+    ys = [torch.full(im.shape, float("nan"), dtype=torch.float32, device="cuda") for im in imgs]
+    specs = [dict(sigma_s=ss, sigma_r=sr) for ss, sr in PTC_SPECS[band]]
+    assert max(int(np.ceil(3 * s["sigma_s"] - 1e-12)) for s in specs) > band - 16
+    plan = fbf.fbf_plan_create(xs, ys, specs, "tc_fp16_single", border, schedule="persistent_tc")
+    assert plan.schedule() == ("persistent_tc", 0.0)
+    fbf.fbf_filter_batched(plan)
+    torch.cuda.synchronize()
+    first = [y.clone() for y in ys]
+    for y in ys:
+        y.fill_(float("nan"))
+    fbf.fbf_filter_batched(plan)
+    torch.cuda.synchronize()
+    bd = O.BORDER_REFLECT if border == "reflect" else O.BORDER_TRUNCATE
+    for im, x, y, y0, sp in zip(imgs, xs, ys, first, specs):
+        assert torch.equal(y, y0)
+        c = fbf.fbf_fit_coeffs("gaussian", sp["sigma_r"], 255.0, 1e-3)
+        p = fbf.make_params(c, sp["sigma_s"], 0, "gaussian", border, "tc_fp16_single")
+        single = fbf.fbf_filter(p, x)
+        torch.cuda.synchronize()
+        assert torch.equal(single, y)
+        W = int(np.ceil(3 * sp["sigma_s"] - 1e-12))
+        ref = O.alg1(im, O.weights_1d(O.SPATIAL_GAUSSIAN, sp["sigma_s"], W), bd, np.array(c.coefficients), 255.0)[0]
+        assert np.abs(y.cpu().numpy() - ref).max() <= 0.15
+    plan.destroy()
+
+
+def test_persistent_tc_plan_is_autotuned_on_an_uneven_batch(fbf):
+    """Form TC_FP16_SINGLE on a 32-image uneven batch: the autotuner times the
+    persistent tensor-core launch against the per-image schedules; whichever it
+    keeps, every output equals the single-image filter."""
+    import torch
+
+    specs_raw = make_batch_specs(32, seed=1399, lo=64, hi=600)
+    imgs = [make_image(h, w, seed=s) for (h, w, _, _, s) in specs_raw]
+    specs = [dict(sigma_s=ss, sigma_r=sr) for (_, _, ss, sr, _) in specs_raw]
+    plan, xs, ys = _run_plan(fbf, imgs, specs, form="tc_fp16_single")
+    kind, ms = plan.schedule()
+    assert kind in ("persistent_tc", "per_image_form", "per_image_form_streams") and ms > 0
+    for x, y, sp in zip(xs, ys, specs):
+        c = fbf.fbf_fit_coeffs("gaussian", sp["sigma_r"], 255.0, 1e-3)
+        single = fbf.fbf_filter(fbf.make_params(c, sp["sigma_s"], 0, "gaussian", "reflect", "tc_fp16_single"), x)
+        torch.cuda.synchronize()
+        assert torch.equal(single, y)
     plan.destroy()
