@@ -351,11 +351,20 @@ class Plan:
             pass
 
 
-def fbf_plan_create(images, outs, specs, form="fp32", border="reflect", schedule=None):
+def fbf_plan_create(images, outs, specs, form="fp32", border="reflect", schedule=None, tune_cache=None):
     """images / outs: lists of uint8 / float32 CUDA tensors; specs: list of dicts
     with sigma_s, sigma_r and optionally W, spatial, range, T, eps, K_fixed, levels.
     schedule: None autotunes (fbf_plan_create); a name of SCHEDULES captures
-    that schedule only (fbf_plan_create_schedule)."""
+    that schedule only (fbf_plan_create_schedule).
+    tune_cache: path of a JSON autotuning cache (tune_cache.py), or None for
+    the FBF_TUNE_CACHE environment variable (unset: no cache).  With a cache
+    and schedule None, a request seen before on this GPU model captures the
+    recorded schedule without autotuning; otherwise the autotuned choice is
+    recorded."""
+    if schedule is None:
+        cache = tune_cache if tune_cache is not None else os.environ.get("FBF_TUNE_CACHE") or None
+        if cache:
+            return _plan_create_cached(images, outs, specs, form, border, cache)
     n = len(images)
     arr = (fbf_image_desc * max(n, 1))()
     for k, (x, y, sp) in enumerate(zip(images, outs, specs)):
@@ -380,6 +389,28 @@ def fbf_plan_create(images, outs, specs, form="fp32", border="reflect", schedule
     if st != FBF_OK:
         raise FbfError(st, "fbf_plan_create")
     return Plan(h, (list(images), list(outs)))
+
+
+def _plan_create_cached(images, outs, specs, form, border, cache):
+    import torch
+
+    from . import tune_cache as TC
+
+    dev = images[0].device if images else torch.device("cuda", torch.cuda.current_device())
+    gpu = torch.cuda.get_device_name(dev)
+    tma_ok = [x.data_ptr() % 16 == 0 and x.stride(0) % 16 == 0 for x in images]
+    sig = TC.signature(form, border, [tuple(x.shape) for x in images], tma_ok, specs)
+    hit = TC.lookup(cache, gpu, sig)
+    if hit is not None and hit["schedule"] in SCHEDULES:
+        try:
+            return fbf_plan_create(images, outs, specs, form, border, schedule=hit["schedule"])
+        except FbfError as e:  # no longer a candidate of the form: autotune again
+            if e.status != FBF_ERR_INVALID_ARGUMENT:
+                raise
+    plan = fbf_plan_create(images, outs, specs, form, border, tune_cache="")
+    kind, ms = plan.schedule()
+    TC.record(cache, gpu, sig, {"schedule": kind, "ms": round(ms, 4), "form": form, "n_images": len(images)})
+    return plan
 
 
 def fbf_filter_batched(plan: Plan, stream=None):

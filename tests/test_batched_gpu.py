@@ -302,3 +302,36 @@ def test_persistent_tc_plan_is_autotuned_on_an_uneven_batch(fbf):
         torch.cuda.synchronize()
         assert torch.equal(single, y)
     plan.destroy()
+
+
+def test_tuning_cache_reuses_the_autotuned_schedule(fbf, tmp_path):
+    """With a tuning cache the first plan autotunes and records its choice; a
+    second plan for the same request on this GPU captures that schedule without
+    replaying the candidates (autotune time 0) and gives the same outputs."""
+    import json
+
+    import torch
+
+    path = str(tmp_path / "tune.json")
+    specs_raw = make_batch_specs(12, seed=1399, lo=64, hi=400)
+    imgs = [make_image(h, w, seed=s) for (h, w, _, _, s) in specs_raw]
+    specs = [dict(sigma_s=ss, sigma_r=sr) for (_, _, ss, sr, _) in specs_raw]
+    xs = [torch.from_numpy(im).cuda() for im in imgs]
+    ys = [torch.empty(im.shape, dtype=torch.float32, device="cuda") for im in imgs]
+    p1 = fbf.fbf_plan_create(xs, ys, specs, "tc_fp16_single", "reflect", tune_cache=path)
+    kind, ms = p1.schedule()
+    assert ms > 0
+    entries = json.load(open(path))["entries"][torch.cuda.get_device_name()]
+    assert [e["schedule"] for e in entries.values()] == [kind]
+    fbf.fbf_filter_batched(p1)
+    torch.cuda.synchronize()
+    first = [y.clone() for y in ys]
+    p2 = fbf.fbf_plan_create(xs, ys, specs, "tc_fp16_single", "reflect", tune_cache=path)
+    assert p2.schedule() == (kind, 0.0)
+    for y in ys:
+        y.fill_(float("nan"))
+    fbf.fbf_filter_batched(p2)
+    torch.cuda.synchronize()
+    assert all(torch.equal(a, b) for a, b in zip(first, ys))
+    p1.destroy()
+    p2.destroy()
