@@ -2,6 +2,8 @@
 // the per-launch constants, and dispatch to the kernel forms.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -145,6 +147,16 @@ extern "C" fbf_status fbf_filter_stack(const fbf_params *p, const void *d_in, fb
   // image i starts i strides in: float images need strides that keep 4-byte alignment
   if (N > 1 && (out_image_stride % sizeof(float) != 0 || (dtype == FBF_F32 && in_image_stride % sizeof(float) != 0)))
     return FBF_ERR_INVALID_ARGUMENT;
+  if (dtype == FBF_F32 && (p->form == FBF_FORM_AUTO || p->form == FBF_FORM_FP32)) {
+    // float images: the whole stack in one launch (chunks of at most 65535 images)
+    if (a.W > f32_wmax()) return FBF_ERR_RANGE;
+    for (int i0 = 0; i0 < N && st == FBF_OK; i0 += 65535) {
+      a.in = static_cast<const char *>(d_in) + (size_t)i0 * in_image_stride;
+      a.out = reinterpret_cast<float *>(reinterpret_cast<char *>(d_out) + (size_t)i0 * out_image_stride);
+      st = launch_fp32_f32_stack(a, N - i0 < 65535 ? N - i0 : 65535, in_image_stride, out_image_stride, stream);
+    }
+    return st;
+  }
   for (int i = 0; i < N && st == FBF_OK; ++i) {
     a.in = static_cast<const char *>(d_in) + (size_t)i * in_image_stride;
     a.out = reinterpret_cast<float *>(reinterpret_cast<char *>(d_out) + (size_t)i * out_image_stride);
@@ -167,15 +179,20 @@ extern "C" fbf_status fbf_filter_backward_stack(const fbf_params *p, const float
   if (reinterpret_cast<uintptr_t>(d_gout) % sizeof(float) != 0) return FBF_ERR_INVALID_ARGUMENT;
   if (p->form != FBF_FORM_AUTO && p->form != FBF_FORM_FP32) return FBF_ERR_UNSUPPORTED;
   if (a.W > f32_wmax()) return FBF_ERR_RANGE;
-  const size_t bytes = backward_scratch_bytes(H, Wd, a.W, a.border);
+  // The stack in chunks whose scratch stays under kStackScratch bytes, each
+  // chunk one launch per pass.
+  constexpr size_t kStackScratch = (size_t)1 << 30;
+  const size_t per = backward_scratch_stride(H, Wd, a.W, a.border);
+  const int chunk = (int)std::max<size_t>(1, std::min<size_t>({(size_t)N, (size_t)65535, kStackScratch / per}));
   void *scratch = nullptr;
-  if (cudaMallocAsync(&scratch, bytes, stream) != cudaSuccess) return FBF_ERR_CUDA;
-  for (int i = 0; i < N && st == FBF_OK; ++i) {
-    const size_t off = (size_t)i * image_stride;
+  if (cudaMallocAsync(&scratch, per * (size_t)chunk, stream) != cudaSuccess) return FBF_ERR_CUDA;
+  for (int i0 = 0; i0 < N && st == FBF_OK; i0 += chunk) {
+    const size_t off = (size_t)i0 * image_stride;
     a.in = reinterpret_cast<const char *>(d_in) + off;
     a.out = reinterpret_cast<float *>(reinterpret_cast<char *>(d_gin) + off);
     const float *g = reinterpret_cast<const float *>(reinterpret_cast<const char *>(d_gout) + off);
-    st = launch_backward(a, g, pitch, a.out, pitch, scratch, stream);
+    st = launch_backward_stack(a, std::min(chunk, N - i0), image_stride, g, pitch, image_stride, a.out, pitch,
+                               image_stride, scratch, per, stream);
   }
   if (cudaFreeAsync(scratch, stream) != cudaSuccess && st == FBF_OK) st = FBF_ERR_CUDA;
   return st;

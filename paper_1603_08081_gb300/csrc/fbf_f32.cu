@@ -50,6 +50,9 @@ struct F32Args {
   int ext_off;        // adjoint: W under REFLECT (grid origin at -W), 0 under TRUNCATE
   int ext_h, ext_w;   // adjoint: grid size
   size_t gext_pitch;  // bytes
+  // a stack of equal-size images (blockIdx.y = image): byte strides between
+  // images of in, out, g and gext, element stride of ab (all 0 for one image)
+  size_t in_istride, out_istride, g_istride, gext_istride, ab_istride;
 };
 
 // Output tiles of kBX x BY pixels for windows up to WCAP.  WCAP = 16: BY = 64
@@ -97,6 +100,14 @@ __global__ void __launch_bounds__(kNTf, 1) fbf_f32_kernel(const __grid_constant_
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int H = a.H, Wd = a.Wd;
   const int tile_y = blockIdx.x / a.tiles_x, tile_x = blockIdx.x - tile_y * a.tiles_x;
+  // this block's image of the stack
+  const size_t img = blockIdx.y;
+  const float *fin = reinterpret_cast<const float *>(static_cast<const char *>(a.in) + img * x.in_istride);
+  float *fout = a.out ? reinterpret_cast<float *>(reinterpret_cast<char *>(a.out) + img * x.out_istride) : nullptr;
+  const float *gup = x.g ? reinterpret_cast<const float *>(reinterpret_cast<const char *>(x.g) + img * x.g_istride)
+                         : nullptr;
+  float2 *abp = x.ab ? x.ab + img * x.ab_istride : nullptr;
+  float *gext = x.gext ? reinterpret_cast<float *>(reinterpret_cast<char *>(x.gext) + img * x.gext_istride) : nullptr;
   const int off = MODE == kModeAdjoint ? x.ext_off : 0;
   const int py0 = tile_y * kBY - off, px0 = tile_x * kBX - off;  // image coords of output (0, 0)
   const int HY = kBY + 2 * W, HX = kBX + 2 * W;
@@ -109,9 +120,9 @@ __global__ void __launch_bounds__(kNTf, 1) fbf_f32_kernel(const __grid_constant_
     if (ey < HY && ex < HX) {
       const int iy = py0 - W + ey, ix = px0 - W + ex;
       if (reflect)
-        fv = ldf(static_cast<const float *>(a.in), a.in_pitch, reflect_index(iy, H), reflect_index(ix, Wd));
+        fv = ldf(fin, a.in_pitch, reflect_index(iy, H), reflect_index(ix, Wd));
       else if (iy >= 0 && iy < H && ix >= 0 && ix < Wd)
-        fv = ldf(static_cast<const float *>(a.in), a.in_pitch, iy, ix);
+        fv = ldf(fin, a.in_pitch, iy, ix);
     }
     return fv;
   };
@@ -129,7 +140,7 @@ __global__ void __launch_bounds__(kNTf, 1) fbf_f32_kernel(const __grid_constant_
       float2 abv = make_float2(0.f, 0.f);
       if (kStageAB && ey < HY && ex < HX) {
         const int iy = py0 - W + ey, ix = px0 - W + ex;
-        if (iy >= 0 && iy < H && ix >= 0 && ix < Wd) abv = x.ab[(size_t)iy * Wd + ix];
+        if (iy >= 0 && iy < H && ix >= 0 && ix < Wd) abv = abp[(size_t)iy * Wd + ix];
       }
       S.fT[e] = f_at(ex, ey);
       if constexpr (kStageAB) S.abT[e] = abv;
@@ -213,7 +224,7 @@ __global__ void __launch_bounds__(kNTf, 1) fbf_f32_kernel(const __grid_constant_
           if constexpr (kStageAB)
             abv = S.abT[(lane + W) * kHYP + yr * kRun + o + W];
           else
-            abv = ab_at(x.ab, H, Wd, py0 + yr * kRun + o, px0 + lane);
+            abv = ab_at(abp, H, Wd, py0 + yr * kRun + o, px0 + lane);
           const float Vr = abv.x * Fr - abv.y * Gr, Vi = abv.x * Fi - abv.y * Gi;
           acc[q][o][1] = fmaf(dn * nw, cs * Vi - sn * Vr, acc[q][o][1]);
         }
@@ -229,7 +240,7 @@ __global__ void __launch_bounds__(kNTf, 1) fbf_f32_kernel(const __grid_constant_
         if constexpr (kStageAB)
           abv = S.abT[e];
         else
-          abv = ab_at(x.ab, H, Wd, py0 - W + ey, px0 - W + ex);
+          abv = ab_at(abp, H, Wd, py0 - W + ey, px0 - W + ex);
         const u64 c = S.chan[e].x;
         const float cs = lo_f(c), sn = hi_f(c);
         S.chan[e] = make_ulonglong2(pack_f(abv.x * cs, -abv.x * sn), pack_f(abv.y * cs, -abv.y * sn));
@@ -271,12 +282,12 @@ __global__ void __launch_bounds__(kNTf, 1) fbf_f32_kernel(const __grid_constant_
         if (iy < H && ix < Wd) {
           const float P = acc[q][o][0], Q = acc[q][o][1];
           const float fh = P / Q;
-          if (a.out)
-            *reinterpret_cast<float *>(reinterpret_cast<char *>(a.out) + (size_t)iy * a.out_pitch +
+          if (fout)
+            *reinterpret_cast<float *>(reinterpret_cast<char *>(fout) + (size_t)iy * a.out_pitch +
                                        (size_t)ix * sizeof(float)) = fh;
-          if (x.ab) {
-            const float gv = ldf(x.g, x.g_pitch, iy, ix);
-            x.ab[(size_t)iy * Wd + ix] = make_float2(gv / Q, gv * fh / Q);
+          if (abp) {
+            const float gv = ldf(gup, x.g_pitch, iy, ix);
+            abp[(size_t)iy * Wd + ix] = make_float2(gv / Q, gv * fh / Q);
           }
         }
       } else {
@@ -285,7 +296,7 @@ __global__ void __launch_bounds__(kNTf, 1) fbf_f32_kernel(const __grid_constant_
           const int iy = gy - off, ix = gx - off;
           const bool inside = iy >= 0 && iy < H && ix >= 0 && ix < Wd;
           const float v = acc[q][o][0] + (inside ? acc[q][o][1] : 0.f);
-          *reinterpret_cast<float *>(reinterpret_cast<char *>(x.gext) + (size_t)gy * x.gext_pitch +
+          *reinterpret_cast<float *>(reinterpret_cast<char *>(gext) + (size_t)gy * x.gext_pitch +
                                      (size_t)gx * sizeof(float)) = v;
         }
       }
@@ -294,10 +305,12 @@ __global__ void __launch_bounds__(kNTf, 1) fbf_f32_kernel(const __grid_constant_
 }
 
 // grad(m) = sum over extended positions p with reflect(p) = m of gext(p).
-__global__ void fbf_fold_kernel(const float *__restrict__ gext, size_t gext_pitch, int W, int H, int Wd,
-                                float *grad, size_t grad_pitch) {
+__global__ void fbf_fold_kernel(const float *__restrict__ gext0, size_t gext_pitch, size_t gext_istride, int W, int H,
+                                int Wd, float *grad0, size_t grad_pitch, size_t grad_istride) {
   const int ix = blockIdx.x * blockDim.x + threadIdx.x;
   if (ix >= Wd) return;
+  const float *gext = reinterpret_cast<const float *>(reinterpret_cast<const char *>(gext0) + blockIdx.z * gext_istride);
+  float *grad = reinterpret_cast<float *>(reinterpret_cast<char *>(grad0) + blockIdx.z * grad_istride);
   for (int iy = blockIdx.y; iy < H; iy += gridDim.y) {
   float s = 0.f;
   // Preimages of m in [-W, N + W): p = m + 2kN and p = -1 - m + 2kN.
@@ -319,7 +332,7 @@ __global__ void fbf_fold_kernel(const float *__restrict__ gext, size_t gext_pitc
 }
 
 template <int MODE, int BY, int WCAP>
-fbf_status launch_f32_by(const FilterArgs &a0, const F32Args &x, int grid_h, int grid_w, cudaStream_t s) {
+fbf_status launch_f32_by(const FilterArgs &a0, const F32Args &x, int grid_h, int grid_w, int nimg, cudaStream_t s) {
   FilterArgs a = a0;
   a.tiles_x = (grid_w + kBX - 1) / kBX;
   a.ntiles = a.tiles_x * ((grid_h + BY - 1) / BY);
@@ -327,32 +340,37 @@ fbf_status launch_f32_by(const FilterArgs &a0, const F32Args &x, int grid_h, int
   const size_t smem = sizeof(F32Smem<BY, WCAP>);
   if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
     return FBF_ERR_CUDA;
-  kern<<<a.ntiles, kNTf, smem, s>>>(a, x);
+  kern<<<dim3(a.ntiles, nimg), kNTf, smem, s>>>(a, x);
   return cuda_status(cudaGetLastError());
 }
 
-// 64-row tiles when they give at least two tiles per SM, else 32-row tiles
-// (2048^2: forward 1.65 -> 1.34 ms with 64 rows; a 512^2 image has only 128
-// such tiles for 152 SMs).
+// 64-row tiles when they give at least two tiles per SM (over all images of
+// the stack), else 32-row tiles (2048^2: forward 1.65 -> 1.34 ms with 64 rows;
+// one 512^2 image has only 128 such tiles for 152 SMs).
 template <int MODE>
-fbf_status launch_f32(const FilterArgs &a, const F32Args &x, int grid_h, int grid_w, cudaStream_t s) {
+fbf_status launch_f32(const FilterArgs &a, const F32Args &x, int grid_h, int grid_w, int nimg, cudaStream_t s) {
   int dev = 0, sms = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return FBF_ERR_CUDA;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (a.W > 16) return launch_f32_by<MODE, 32, 32>(a, x, grid_h, grid_w, s);
-  const long long tiles64 = (long long)((grid_w + kBX - 1) / kBX) * ((grid_h + 63) / 64);
-  if (tiles64 >= 2LL * sms) return launch_f32_by<MODE, 64, 16>(a, x, grid_h, grid_w, s);
-  return launch_f32_by<MODE, 32, 16>(a, x, grid_h, grid_w, s);
+  if (nimg < 1 || nimg > 65535) return FBF_ERR_INVALID_ARGUMENT;
+  if (a.W > 16) return launch_f32_by<MODE, 32, 32>(a, x, grid_h, grid_w, nimg, s);
+  const long long tiles64 = (long long)((grid_w + kBX - 1) / kBX) * ((grid_h + 63) / 64) * nimg;
+  if (tiles64 >= 2LL * sms) return launch_f32_by<MODE, 64, 16>(a, x, grid_h, grid_w, nimg, s);
+  return launch_f32_by<MODE, 32, 16>(a, x, grid_h, grid_w, nimg, s);
 }
 
 }  // namespace
 
 int f32_wmax() { return kWcapF; }
 
-fbf_status launch_fp32_f32(const FilterArgs &a, cudaStream_t s) {
+fbf_status launch_fp32_f32(const FilterArgs &a, cudaStream_t s) { return launch_fp32_f32_stack(a, 1, 0, 0, s); }
+
+fbf_status launch_fp32_f32_stack(const FilterArgs &a, int n, size_t in_istride, size_t out_istride, cudaStream_t s) {
   if (a.W > kWcapF) return FBF_ERR_RANGE;
   F32Args x{};
-  return launch_f32<kModeForward>(a, x, a.H, a.Wd, s);
+  x.in_istride = in_istride;
+  x.out_istride = out_istride;
+  return launch_f32<kModeForward>(a, x, a.H, a.Wd, n, s);
 }
 
 size_t backward_scratch_bytes(int H, int Wd, int W, int border) {
@@ -361,9 +379,20 @@ size_t backward_scratch_bytes(int H, int Wd, int W, int border) {
   return ((ab + 255) & ~(size_t)255) + ge;
 }
 
+size_t backward_scratch_stride(int H, int Wd, int W, int border) {
+  return (backward_scratch_bytes(H, Wd, W, border) + 255) & ~(size_t)255;
+}
+
 fbf_status launch_backward(const FilterArgs &a, const float *g, size_t g_pitch, float *gin, size_t gin_pitch,
                            void *scratch, cudaStream_t s) {
+  return launch_backward_stack(a, 1, 0, g, g_pitch, 0, gin, gin_pitch, 0, scratch, 0, s);
+}
+
+fbf_status launch_backward_stack(const FilterArgs &a, int n, size_t in_istride, const float *g, size_t g_pitch,
+                                 size_t g_istride, float *gin, size_t gin_pitch, size_t gin_istride, void *scratch,
+                                 size_t scratch_istride, cudaStream_t s) {
   if (a.W > kWcapF) return FBF_ERR_RANGE;
+  if (n < 1 || n > 65535 || scratch_istride % 256 != 0) return FBF_ERR_INVALID_ARGUMENT;
   const int H = a.H, Wd = a.Wd, W = a.W;
   float2 *ab = static_cast<float2 *>(scratch);
   const size_t ab_bytes = (((size_t)H * Wd * sizeof(float2)) + 255) & ~(size_t)255;
@@ -372,31 +401,39 @@ fbf_status launch_backward(const FilterArgs &a, const float *g, size_t g_pitch, 
   x1.g = g;
   x1.g_pitch = g_pitch;
   x1.ab = ab;
+  x1.in_istride = in_istride;
+  x1.g_istride = g_istride;
+  x1.ab_istride = scratch_istride / sizeof(float2);
   FilterArgs af = a;
   af.out = nullptr;
-  fbf_status st = launch_f32<kModeForward>(af, x1, H, Wd, s);
+  fbf_status st = launch_f32<kModeForward>(af, x1, H, Wd, n, s);
   if (st != FBF_OK) return st;
   // Pass 2: adjoint on the extended grid (REFLECT) or the image (TRUNCATE).
   F32Args x2{};
   x2.ab = ab;
+  x2.in_istride = in_istride;
+  x2.ab_istride = scratch_istride / sizeof(float2);
   if (a.border == FBF_BORDER_REFLECT) {
     x2.ext_off = W;
     x2.ext_h = H + 2 * W;
     x2.ext_w = Wd + 2 * W;
     x2.gext = reinterpret_cast<float *>(static_cast<char *>(scratch) + ab_bytes);
     x2.gext_pitch = (size_t)x2.ext_w * sizeof(float);
+    x2.gext_istride = scratch_istride;
   } else {
     x2.ext_off = 0;
     x2.ext_h = H;
     x2.ext_w = Wd;
     x2.gext = gin;
     x2.gext_pitch = gin_pitch;
+    x2.gext_istride = gin_istride;
   }
-  st = launch_f32<kModeAdjoint>(a, x2, x2.ext_h, x2.ext_w, s);
+  st = launch_f32<kModeAdjoint>(a, x2, x2.ext_h, x2.ext_w, n, s);
   if (st != FBF_OK || a.border != FBF_BORDER_REFLECT) return st;
   // Pass 3: fold the extended grid back onto the image.
-  dim3 grid((Wd + 127) / 128, H < 65535 ? H : 65535);
-  fbf_fold_kernel<<<grid, 128, 0, s>>>(x2.gext, x2.gext_pitch, W, H, Wd, gin, gin_pitch);
+  dim3 grid((Wd + 127) / 128, H < 65535 ? H : 65535, n);
+  fbf_fold_kernel<<<grid, 128, 0, s>>>(x2.gext, x2.gext_pitch, x2.gext_istride, W, H, Wd, gin, gin_pitch,
+                                       gin_istride);
   return cuda_status(cudaGetLastError());
 }
 

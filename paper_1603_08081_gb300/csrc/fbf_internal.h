@@ -60,9 +60,20 @@ fbf_status tc_read_clear_error(unsigned int *code);
 // FP32-input forward and the adjoint (fbf_f32.cu); W <= f32_wmax().
 int f32_wmax();
 fbf_status launch_fp32_f32(const FilterArgs &a, cudaStream_t s);
+// n equal-size images, image i at byte offset i * stride of in / out: one launch.
+fbf_status launch_fp32_f32_stack(const FilterArgs &a, int n, size_t in_istride, size_t out_istride, cudaStream_t s);
 size_t backward_scratch_bytes(int H, int Wd, int W, int border);
+// Scratch per image of a stacked backward (backward_scratch_bytes rounded to 256).
+size_t backward_scratch_stride(int H, int Wd, int W, int border);
 fbf_status launch_backward(const FilterArgs &a, const float *g, size_t g_pitch, float *gin, size_t gin_pitch,
                            void *scratch, cudaStream_t s);
+// The backward of n equal-size images in one launch per pass: image i's input,
+// upstream gradient and gradient at byte offsets i * in_istride, i * g_istride,
+// i * gin_istride, its scratch at i * scratch_istride (a multiple of 256, at
+// least backward_scratch_stride).
+fbf_status launch_backward_stack(const FilterArgs &a, int n, size_t in_istride, const float *g, size_t g_pitch,
+                                 size_t g_istride, float *gin, size_t gin_pitch, size_t gin_istride, void *scratch,
+                                 size_t scratch_istride, cudaStream_t s);
 
 inline fbf_status cuda_status(cudaError_t e) { return e == cudaSuccess ? FBF_OK : FBF_ERR_CUDA; }
 

@@ -455,15 +455,17 @@ __device__ __forceinline__ void tc2_body(const FilterArgs *a1, const CUtensorMap
       for (int k = 0; k < kCp / 2; ++k)
         *reinterpret_cast<uint4 *>(ent + ((lane + bhalf * (kCp / 2) + k) & (kCp - 1)) * 16) = e;
     } else {
-      const uint2 e = make_uint2(pack2<BF>(dc, ds), pack2<BF>(dfc, dfs));
+      // 16-byte stores of two copies each
+      const uint32_t e0 = pack2<BF>(dc, ds), e1 = pack2<BF>(dfc, dfs);
+      const uint4 e = make_uint4(e0, e1, e0, e1);
 #pragma unroll
-      for (int k = 0; k < kCp / 2; ++k)
-        *reinterpret_cast<uint2 *>(ent + ((lane + bhalf * (kCp / 2) + k) & (kCp - 1)) * 8) = e;
+      for (int k = 0; k < kCp / 4; ++k)
+        *reinterpret_cast<uint4 *>(ent + ((lane + bhalf * (kCp / 4) + k) & (kCp / 2 - 1)) * 16) = e;
     }
   };
 
   // ---- modulate with the table in buffer b: per unit, one gather per pixel,
-  // neighbouring columns paired by byte permutes, two-column TMEM stores.  SEQ:
+  // neighbouring columns paired by byte permutes, four-column TMEM stores.  SEQ:
   // only data part `part` (0 = hi, 1 = lo), into the one set of A1 regions.
   auto modulate = [&](int b, int part) {
     const unsigned char *tb16 = t16 + (size_t)b * kT16Bytes;
@@ -508,8 +510,7 @@ __device__ __forceinline__ void tc2_body(const FilterArgs *a1, const CUtensorMap
 #pragma unroll
         for (int p = 0; p < kA1Parts; ++p) {
           const uint32_t ta = tmem + lane_base + kA1 + (uint32_t)((c * kA1Parts + p) * kA1Stride + 4 * u);
-          tmem_st_x2(ta, ch[c][p][0], ch[c][p][1]);
-          tmem_st_x2(ta + 2, ch[c][p][2], ch[c][p][3]);
+          tmem_st_x4(ta, ch[c][p][0], ch[c][p][1], ch[c][p][2], ch[c][p][3]);
         }
     }
     tmem_st_wait();

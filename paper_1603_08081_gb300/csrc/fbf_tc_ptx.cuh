@@ -195,6 +195,10 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *m, uint32_t parity, 
 
 // ---- TMA ------------------------------------------------------------------
 
+// One arrival (release semantics at CTA scope).
+__device__ __forceinline__ void mbar_arrive(uint64_t *m) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(m)) : "memory");
+}
 // Expect `bytes` of asynchronous transactions on `m` (and arrive once).
 __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *m, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(m)), "r"(bytes) : "memory");
