@@ -6,11 +6,12 @@ sigma_s in {3, 5, 10} x sigma_r in {20, 40}, Gaussian spatial and range kernels,
 coefficients fitted to eps = 1e-3 (K = 17 for sigma_r = 20, K = 9 for 40),
 REFLECT border.  The coefficient fit is host work done once and reported apart.
 
-Forms: fp32 (fused FP32 FMA kernel), tc_fp16, tc_bf16 and tc_fp16_single
-(tensor-core kernels: split FP16 data, split BF16 data and weights, FP16
-rounded once); all are timed (interleaved step by step) and the headline
-`form` is the fastest whose output stays within 0.5 gray of the FP64 oracle on
-the CPU-baseline slab.
+Forms: fp32 (fused FP32 FMA kernel), tc_fp16, tc_bf16, tc_fp16_single and
+tc_bf16_single (tensor-core kernels: split FP16 data, split BF16 data and
+weights, FP16 rounded once, BF16 rounded once); all are timed (interleaved
+step by step) and the headline `form` is the fastest whose output stays within
+0.5 gray of the FP64 oracle on the CPU-baseline slab (of forms within 1% of
+that speed, the most accurate).
 
 Printed: ONE JSON line (rank 0).  `value` is whole-job Mpixel/s with inputs
 resident in HBM; `e2e` is the same metric through the public Python API with
@@ -24,7 +25,8 @@ channel per pass) against the measured bf16 peak, `pipe_frac` the dense MMA
 flops the kernel issues (band padding and split products included), and
 `padding_ratio` their quotient.  `value_bf16` and `value_fp32` repeat the two
 forms the metric names beside the headline, each with its own roofline
-fraction; `cfg0` times the plain 256x256 configuration (K = 10) per form with
+fraction (`value_bf16`: the faster BF16 tensor-core form within 0.5 gray;
+`value_bf16_split` the three-product BF16 form); `cfg0` times the plain 256x256 configuration (K = 10) per form with
 its errors and the host time per call.  `cpu_baseline` times the FP64 oracle (Algorithm 1 form) on a
 bounded row slab of the same workload and reports its agreement with the GPU
 output on that slab (the max-error condition of the metric).
@@ -212,25 +214,25 @@ def cpu_baseline(img, slab_rows: int):
 
 # ------------------------------------------------------------------ main ---
 
-FORMS_ALL = ["fp32", "tc_fp16", "tc_bf16", "tc_fp16_single"]
-FORM_DTYPE = {"fp32": "f32", "tc_fp16": "f16", "tc_bf16": "bf16", "tc_fp16_single": "f16"}
+FORMS_ALL = ["fp32", "tc_fp16", "tc_bf16", "tc_fp16_single", "tc_bf16_single"]
+FORM_DTYPE = {"fp32": "f32", "tc_fp16": "f16", "tc_bf16": "bf16", "tc_fp16_single": "f16", "tc_bf16_single": "bf16"}
 FORM_KERNEL = {"fp32": "fbf_fp32_u8_kernel", "tc_fp16": "fbf_tc_u8_kernel<0,2,..>",
                "tc_bf16": "fbf_tc_u8_kernel<1,3,..>", "tc_fp16_single": "fbf_tc_u8_kernel<0,1,..>"}
 FORM_KERNEL2 = {"tc_fp16": "fbf_tc2_u8_kernel<0,2,..>", "tc_bf16": "fbf_tc2_u8_kernel<1,3,..>",
-                "tc_fp16_single": "fbf_tc2_u8_kernel<0,1,..>"}
+                "tc_fp16_single": "fbf_tc2_u8_kernel<0,1,..>", "tc_bf16_single": "fbf_tc2_u8_kernel<1,1,..>"}
 
 
 def form_kernel(form: str, W: int) -> str:
     if form != "fp32" and tc_layout(form, W) == "tc2":
         return FORM_KERNEL2[form]
     return FORM_KERNEL[form]
-TC_NSPLIT = {"tc_fp16": 2, "tc_bf16": 3, "tc_fp16_single": 1}
+TC_NSPLIT = {"tc_fp16": 2, "tc_bf16": 3, "tc_fp16_single": 1, "tc_bf16_single": 1}
 
 
 def tc_layout(form: str, W: int) -> str:
     """Which tensor-core layout runs the form at this window (T <= 255): the
-    second for the single form, and for the split forms beyond W = 32."""
-    return "tc2" if form == "tc_fp16_single" or W > 32 else "tc1"
+    second for the single forms, and for the split forms beyond W = 32."""
+    return "tc2" if form in ("tc_fp16_single", "tc_bf16_single") or W > 32 else "tc1"
 
 
 def tc_issued_flops(K: int, W: int, form: str) -> float:
@@ -755,7 +757,12 @@ def run_ours(args):
         for c in acc_ctx:
             del c["direct"]
     ok_forms = [f for f in forms if errs.get(f, 0.0) <= 0.5]
-    head = max(ok_forms or forms, key=lambda f: per_form[f]["value"])
+    fastest = max(per_form[f]["value"] for f in (ok_forms or forms))
+    # the fastest form within 0.5 gray; of forms within 1% of it, the most accurate
+    head = min((f for f in (ok_forms or forms) if per_form[f]["value"] >= 0.99 * fastest),
+               key=lambda f: (errs.get(f, 0.0), -per_form[f]["value"]))
+    bf16_ok = [f for f in ("tc_bf16_single", "tc_bf16") if f in per_form and errs.get(f, 0.0) <= 0.5]
+    bf16_best = max(bf16_ok, key=lambda f: per_form[f]["value"]) if bf16_ok else "tc_bf16"
 
     # End to end through the public API (headline form): pinned host image in,
     # every output back, every step.  Steps are pipelined as a stream of images
@@ -839,7 +846,7 @@ def run_ours(args):
         if f not in per_form:
             return None
         r = per_form[f]["roofline"]
-        return {"value": round(per_form[f]["value"], 1), "unit": "Mpixel/s",
+        return {"form": f, "value": round(per_form[f]["value"], 1), "unit": "Mpixel/s",
                 "max_err_vs_oracle": per_form[f].get("max_err_vs_oracle"),
                 "frac": r["frac"], "bound": r["bound"], "peak": r["peak"], "achieved": r["achieved"],
                 "launch": r["launch"]}
@@ -857,7 +864,8 @@ def run_ours(args):
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": hf["roofline"],
         # the two forms the metric names, side by side with the headline
-        "value_bf16": form_line("tc_bf16"),
+        "value_bf16": form_line(bf16_best),
+        "value_bf16_split": form_line("tc_bf16"),
         "value_fp32": form_line("fp32"),
         "forms": {f: {"value": round(per_form[f]["value"], 1), "ms_per_step": round(per_form[f]["ms_per_step"], 4),
                       "max_err_vs_oracle": per_form[f].get("max_err_vs_oracle"),

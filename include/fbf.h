@@ -69,16 +69,26 @@ typedef enum { FBF_U8 = 0, FBF_F32 = 1 } fbf_dtype;
  * tensor-core products); on 8-bit images its error against the exact
  * Algorithm 1 stays near 0.02-0.05 gray level for sigma_r >= 20 and grows as
  * sigma_r shrinks (about 0.1 at sigma_r = 5), where the split forms stay below
- * 2e-3.  AUTO: the faster of FP32 and TC_FP16 for the window, as measured on
- * GB300 (TC_FP16 from W = 4 up, for the Gaussian and the box kernel alike;
- * FP32, which runs the box kernel as running window sums, below); AUTO never
- * picks TC_FP16_SINGLE. */
+ * 2e-3.  TC_BF16_SINGLE: data and weights rounded to BF16 once (one product,
+ * the speed of TC_FP16_SINGLE; BF16 keeps 8 significand bits to FP16's 11):
+ * with the REFLECT border its error stays within 0.35 gray level for
+ * sigma_r >= 15 and sigma_s >= 1 (an FP64 emulation of its rounding steps gives
+ * 0.08-0.31 over Gaussian and box windows W = 3..48) and reaches 0.5 near
+ * sigma_r = 10 or with a window of one dominant tap (sigma_s < 1); with
+ * TRUNCATE the same holds away from the image border, while near a corner,
+ * where a quarter of the window remains, the error grows up to about four
+ * times (0.48 measured at W = 16).  Callers opt in.
+ * AUTO: the faster of FP32 and TC_FP16 for the window, as measured on GB300
+ * (TC_FP16 from W = 4 up, for the Gaussian and the box kernel alike; FP32,
+ * which runs the box kernel as running window sums, below); AUTO never picks
+ * TC_FP16_SINGLE or TC_BF16_SINGLE. */
 typedef enum {
   FBF_FORM_AUTO = 0,
   FBF_FORM_FP32 = 1,
   FBF_FORM_TC_FP16 = 2,
   FBF_FORM_TC_BF16 = 3,
-  FBF_FORM_TC_FP16_SINGLE = 4
+  FBF_FORM_TC_FP16_SINGLE = 4,
+  FBF_FORM_TC_BF16_SINGLE = 5
 } fbf_form;
 
 #define FBF_KMAX 256 /* maximum number of coefficients K                 */

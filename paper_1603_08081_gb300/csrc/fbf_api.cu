@@ -80,7 +80,7 @@ namespace fbf {
 // Launch of one packed image in the requested form (validated by the caller's
 // pack_filter_args; sizes non-zero).
 fbf_status launch_filter(const FilterArgs &a, fbf_form form, fbf_dtype dtype, cudaStream_t stream) {
-  const bool tc = form == FBF_FORM_TC_FP16 || form == FBF_FORM_TC_BF16 || form == FBF_FORM_TC_FP16_SINGLE;
+  const bool tc = is_tc_form(form);
   if (form != FBF_FORM_AUTO && form != FBF_FORM_FP32 && !tc) return FBF_ERR_INVALID_ARGUMENT;
   if (dtype == FBF_F32) {
     if (tc) return FBF_ERR_UNSUPPORTED;
@@ -90,6 +90,7 @@ fbf_status launch_filter(const FilterArgs &a, fbf_form form, fbf_dtype dtype, cu
   if (form == FBF_FORM_TC_FP16) return launch_tc_u8(a, 0, stream);
   if (form == FBF_FORM_TC_BF16) return launch_tc_u8(a, 1, stream);
   if (form == FBF_FORM_TC_FP16_SINGLE) return launch_tc_u8(a, 2, stream);
+  if (form == FBF_FORM_TC_BF16_SINGLE) return launch_tc_u8(a, 3, stream);
   if (form == FBF_FORM_AUTO && auto_picks_tc(a)) return launch_tc_u8(a, 0, stream);
   return launch_fp32_u8(a, stream);
 }

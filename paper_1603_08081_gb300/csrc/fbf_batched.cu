@@ -322,7 +322,7 @@ static fbf_status plan_create(const fbf_image_desc *descs, int n, fbf_form form,
   *out = nullptr;
   if (n < 0 || (n > 0 && !descs)) return FBF_ERR_INVALID_ARGUMENT;
   if (border != FBF_BORDER_REFLECT && border != FBF_BORDER_TRUNCATE) return FBF_ERR_INVALID_ARGUMENT;
-  const bool tc = form == FBF_FORM_TC_FP16 || form == FBF_FORM_TC_BF16 || form == FBF_FORM_TC_FP16_SINGLE;
+  const bool tc = is_tc_form(form);
   if (form != FBF_FORM_AUTO && form != FBF_FORM_FP32 && !tc) return FBF_ERR_INVALID_ARGUMENT;
 
   std::vector<FilterArgs> args(n);
@@ -365,7 +365,8 @@ static fbf_status plan_create(const fbf_image_desc *descs, int n, fbf_form form,
   if (tc) {
     bool t_ok = true;  // the persistent tensor-core kernel's 2T-phase table holds 2T <= 510
     for (const FilterArgs &a : args) t_ok = t_ok && a.twoT >= 2 && a.twoT <= 510;
-    if (form == FBF_FORM_TC_FP16_SINGLE && t_ok) kinds.push_back(FBF_SCHEDULE_PERSISTENT_TC);
+    const bool single = form == FBF_FORM_TC_FP16_SINGLE || form == FBF_FORM_TC_BF16_SINGLE;
+    if (single && t_ok) kinds.push_back(FBF_SCHEDULE_PERSISTENT_TC);
     kinds.push_back(FBF_SCHEDULE_PER_IMAGE_FORM);
     kinds.push_back(FBF_SCHEDULE_PER_IMAGE_FORM_STREAMS);
   } else {
@@ -400,7 +401,7 @@ static fbf_status plan_create(const fbf_image_desc *descs, int n, fbf_form form,
       st = build_persistent<64, 96>(args, &c.tables);
       if (st == FBF_OK) st = capture_persistent<64, 96, 1, 16>(p->device, (int)border, &c, cs);
     } else if (k == FBF_SCHEDULE_PERSISTENT_TC) {
-      st = capture_persistent_tc(args, 2, &c, cs);
+      st = capture_persistent_tc(args, tc_mode(form), &c, cs);
     } else {
       const bool fp32 = k == FBF_SCHEDULE_PER_IMAGE_FP32 || k == FBF_SCHEDULE_PER_IMAGE_FP32_STREAMS;
       const bool streams = k == FBF_SCHEDULE_PER_IMAGE_FP32_STREAMS || k == FBF_SCHEDULE_PER_IMAGE_FORM_STREAMS;

@@ -53,8 +53,16 @@ fbf_status launch_fp32_u8(const FilterArgs &a, cudaStream_t s);
 // One packed image in `form` (AUTO resolved by auto_picks_tc); sizes non-zero.
 fbf_status launch_filter(const FilterArgs &a, fbf_form form, fbf_dtype dtype, cudaStream_t stream);
 bool auto_picks_tc(const FilterArgs &a);
-// mode: 0 = FP16 split data, 1 = BF16 split data and weights, 2 = FP16 single.
+// mode: 0 = FP16 split data, 1 = BF16 split data and weights, 2 = FP16 single,
+// 3 = BF16 single (second layout only).
 fbf_status launch_tc_u8(const FilterArgs &a, int mode, cudaStream_t s);
+inline bool is_tc_form(fbf_form f) {
+  return f == FBF_FORM_TC_FP16 || f == FBF_FORM_TC_BF16 || f == FBF_FORM_TC_FP16_SINGLE || f == FBF_FORM_TC_BF16_SINGLE;
+}
+// launch_tc_u8 mode of a tensor-core form.
+inline int tc_mode(fbf_form f) {
+  return f == FBF_FORM_TC_FP16 ? 0 : f == FBF_FORM_TC_BF16 ? 1 : f == FBF_FORM_TC_FP16_SINGLE ? 2 : 3;
+}
 fbf_status tc_read_clear_error(unsigned int *code);
 
 // FP32-input forward and the adjoint (fbf_f32.cu); W <= f32_wmax().
@@ -81,6 +89,7 @@ inline fbf_status cuda_status(cudaError_t e) { return e == cudaSuccess ? FBF_OK 
 // request lies outside its instantiations (the caller then runs the first one).
 fbf_status launch_tc2_u8(const FilterArgs &a, int mode, cudaStream_t s);
 fbf_status launch_tc2_single(const FilterArgs &a, cudaStream_t s);
+fbf_status launch_tc2_bf16_single(const FilterArgs &a, cudaStream_t s);
 fbf_status launch_tc2_fp16(const FilterArgs &a, cudaStream_t s);
 fbf_status launch_tc2_bf16(const FilterArgs &a, cudaStream_t s);
 
@@ -112,7 +121,7 @@ struct Tc2BatchTables {
   void release();
 };
 // One persistent launch over a batch; mode as for launch_tc_u8.
-// FBF_ERR_UNSUPPORTED outside the instantiations (today: the single FP16 form).
+// FBF_ERR_UNSUPPORTED outside the instantiations (the single FP16 and BF16 forms).
 fbf_status launch_tc2_batch(const Tc2BatchTables &t, int mode, cudaStream_t s);
 
 // Host helpers shared by the launchers (fbf_host.cu, fbf_api.cu).

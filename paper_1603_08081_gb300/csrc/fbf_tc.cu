@@ -849,13 +849,14 @@ fbf_status launch_tc_cfg(const FilterArgs &a0, cudaStream_t s) {
 // mode 0: FP16 operands, split data, single weights (2 products per step);
 // 1: BF16 operands, split data and weights (3 products); 2: FP16 operands, data
 // and weights rounded once (1 product; A1 then takes half the TMEM columns, so
-// the tiles of windows above 16 run the pipelined schedule too).
+// the tiles of windows above 16 run the pipelined schedule too); 3: BF16
+// operands rounded once (second layout only: T <= 255).
 fbf_status launch_tc_u8(const FilterArgs &a, int mode, cudaStream_t s) {
-  if (mode < 0 || mode > 2) return FBF_ERR_INVALID_ARGUMENT;
+  if (mode < 0 || mode > 3) return FBF_ERR_INVALID_ARGUMENT;
   // The second layout (fbf_tc2_kernel.cuh) covers T <= 255 and, per form, the
   // windows of its instantiations; this kernel runs the rest.
   const fbf_status st2 = launch_tc2_u8(a, mode, s);
-  if (st2 != FBF_ERR_UNSUPPORTED) return st2;
+  if (st2 != FBF_ERR_UNSUPPORTED || mode == 3) return st2;
   constexpr int BY16 = FBF_TC_BY_16, NBC16 = FBF_TC_NBC_16, NT16 = FBF_TC_NT_16;
   if (a.W <= 16) {
     if (mode == 1) return launch_tc_cfg<1, 3, BY16, 16, FBF_TC_NBR, NBC16, FBF_TC_PIPE, NT16>(a, s);
@@ -878,6 +879,7 @@ fbf_status launch_tc_u8(const FilterArgs &a, int mode, cudaStream_t s) {
 fbf_status launch_tc2_u8(const FilterArgs &a, int mode, cudaStream_t s) {
   if (a.twoT < 2 || a.twoT > 510) return FBF_ERR_UNSUPPORTED;
   if (mode == 2) return launch_tc2_single(a, s);
+  if (mode == 3) return launch_tc2_bf16_single(a, s);
   if (mode == 0) return launch_tc2_fp16(a, s);
   return launch_tc2_bf16(a, s);
 }

@@ -77,8 +77,14 @@ void Tc2BatchTables::release() {
 }
 
 fbf_status launch_tc2_batch(const Tc2BatchTables &t, int mode, cudaStream_t s) {
-  if (mode != 2) return FBF_ERR_UNSUPPORTED;  // the single FP16 form
+  if (mode != 2 && mode != 3) return FBF_ERR_UNSUPPORTED;  // the single FP16 and BF16 forms
   if (t.b.nitems <= 0) return FBF_OK;
+  if (mode == 3) {
+    if (t.wmax <= 16) return tc2::launch_batch_cfg<1, 1, 4, 0>(t.b, s);
+    if (t.wmax <= 32) return tc2::launch_batch_cfg<1, 1, 6, 0>(t.b, s);
+    if (t.wmax <= 48) return tc2::launch_batch_cfg<1, 1, 8, 1>(t.b, s);
+    return FBF_ERR_UNSUPPORTED;
+  }
   if (t.wmax <= 16) return tc2::launch_batch_cfg<0, 1, 4, 0>(t.b, s);
   if (t.wmax <= 32) return tc2::launch_batch_cfg<0, 1, 6, 0>(t.b, s);
   if (t.wmax <= 48) return tc2::launch_batch_cfg<0, 1, 8, 1>(t.b, s);
