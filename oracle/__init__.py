@@ -71,6 +71,14 @@ def _load():
             lib.orc_set_threads.restype = None
             lib.orc_local_range.argtypes = [dp, i, i, i, i]
             lib.orc_local_range.restype = d
+            lib.orc_rec_kernel.argtypes = [d, C.c_long]
+            lib.orc_rec_kernel.restype = d
+            lib.orc_rec_coeffs.argtypes = [d, dp, dp, dp]
+            lib.orc_rec_coeffs.restype = None
+            lib.orc_rec_filter_line.argtypes = [dp, C.c_long, d, dp]
+            lib.orc_rec_filter_line.restype = None
+            lib.orc_alg1_rec.argtypes = [dp, i, i, d, i, dp, i, d, dp, dp, dp]
+            lib.orc_alg1_rec.restype = i
             _lib = lib
     return _lib
 
@@ -259,3 +267,39 @@ def local_range(f, W: int, border: int = 0) -> float:
 def bound12(T: float, eps: float, w0: float) -> float:
     """Right-hand side of the accuracy bound, eq. (12): 2 T eps / (w(0) - eps)."""
     return 2.0 * T * eps / (w0 - eps)
+
+
+def rec_kernel(sigma_s: float, k: int) -> float:
+    """Deriche's approximation g(k) of exp(-k^2 / (2 sigma_s^2)), unscaled (the
+    recursive Gaussian that Sec. II cites; see the C source)."""
+    return float(_load().orc_rec_kernel(float(sigma_s), int(k)))
+
+
+def rec_coeffs(sigma_s: float):
+    """(causal numerator n[0..3], denominator d[0..4] with d[0] = 1, anticausal
+    numerator m[0..4] with m[0] = 0) of the recursive Gaussian, unit gain."""
+    nc, dd, na = np.zeros(4), np.zeros(5), np.zeros(5)
+    _load().orc_rec_coeffs(float(sigma_s), _dp(nc), _dp(dd), _dp(na))
+    return nc, dd, na
+
+
+def rec_filter_line(x, sigma_s: float) -> np.ndarray:
+    """One line through the causal + anticausal recursions (zero outside)."""
+    x = np.ascontiguousarray(x, np.float64)
+    y = np.empty_like(x)
+    _load().orc_rec_filter_line(_dp(x), len(x), float(sigma_s), _dp(y))
+    return y
+
+
+def alg1_rec(f, sigma_s: float, border: int, d, T: float):
+    """Algorithm 1 with the recursive Gaussian as the convolution (whole image).
+    Returns (out, P, Q)."""
+    f = _img(f)
+    H, Wd = f.shape
+    d = np.ascontiguousarray(d, np.float64)
+    out, P, Q = (np.empty((H, Wd), np.float64) for _ in range(3))
+    st = _load().orc_alg1_rec(_dp(f), H, Wd, float(sigma_s), int(border), _dp(d), len(d), float(T),
+                              _dp(out), _dp(P), _dp(Q))
+    if st != 0:
+        raise ValueError("oracle alg1_rec: bad arguments")
+    return out, P, Q

@@ -21,6 +21,10 @@
  *   orc_grad_at        the same derivative at sampled pixels only
  *   orc_local_range    the dynamic range T of the image over the window Omega,
  *                      the definition that opens Sec. III
+ *   orc_rec_kernel,    the recursive Gaussian that Sec. II cites for constant-
+ *   orc_rec_coeffs,    time filtering (Deriche): its kernel, its recursion
+ *   orc_rec_filter_line  coefficients and one line through it
+ *   orc_alg1_rec       Algorithm 1 with that recursive filter as the convolution
  *
  * The fit uses Householder QR, deliberately not the modified Gram-Schmidt
  * recursion of Algorithm 2, so the two are independent: the least-squares
@@ -570,4 +574,184 @@ double orc_local_range(const double *f, int H, int Wd, int W, int border) {
     }
   }
   return T;
+}
+
+/*
+ * Recursive Gaussian (the constant-time Gaussian filtering that Sec. II cites,
+ * after eq. (5): R. Deriche, "Recursively implementing the Gaussian and its
+ * derivatives", 1993).  Deriche approximates exp(-x^2 / (2 s^2)), x >= 0, by
+ * two damped sinusoids,
+ *   g(x) = (a1 cos(w1 x/s) + b1 sin(w1 x/s)) exp(-l1 x/s)
+ *        + (a2 cos(w2 x/s) + b2 sin(w2 x/s)) exp(-l2 x/s),
+ * with his published constants (a1, b1, w1, l1) = (1.680, 3.735, 0.6318, 1.783)
+ * and (a2, b2, w2, l2) = (-0.6803, -0.2598, 1.997, 1.723), and g(-x) = g(x).
+ * The samples g(k), k >= 0, are the impulse response of a causal recursion
+ * whose transfer function is the sum of the z-transforms of the two terms
+ * (each a first-degree numerator over a second-degree denominator); the
+ * samples g(k), k <= -1, that of the mirrored anticausal recursion.  The sum of
+ * the two is scaled to unit gain.
+ *
+ * Readings taken here (the paper prints no formula for the recursive filter):
+ *   * Deriche's fourth-order approximation with the constants above;
+ *   * the 1-D kernel is scaled so that sum_k g(k) = 1 (the FIR kernel's Sec. IV
+ *     normalisation; the scale cancels in P / Q anyway);
+ *   * borders: TRUNCATE is zero outside the image (the infinite-support kernel
+ *     restricted to the image); REFLECT extends each line by E = ceil(8 s)
+ *     half-sample-symmetric samples on each side (repeated for E longer than
+ *     the line) and is zero beyond them;
+ *   * the 2-D filter is the rows' recursion followed by the columns'.
+ */
+static const double orc_der_a[2] = {1.680, -0.6803}, orc_der_b[2] = {3.735, -0.2598};
+static const double orc_der_w[2] = {0.6318, 1.997}, orc_der_l[2] = {1.783, 1.723};
+
+/* g(k) of the approximation above, unscaled. */
+double orc_rec_kernel(double s, long k) {
+  double x = fabs((double)k) / s, g = 0.0;
+  for (int i = 0; i < 2; ++i)
+    g += (orc_der_a[i] * cos(orc_der_w[i] * x) + orc_der_b[i] * sin(orc_der_w[i] * x)) * exp(-orc_der_l[i] * x);
+  return g;
+}
+
+/* Recursion coefficients for scale s: causal numerator nc[0..3], common
+ * denominator 1 + dd[1] z^-1 + ... + dd[4] z^-4, anticausal numerator
+ * na[1..4] (na[0] = 0), all scaled to unit total gain.  Term i contributes
+ *   sum_{k>=0} (a cos(wk) + b sin(wk)) e^{-lk} z^-k
+ *     = (a + e^{-l}(b sin w - a cos w) z^-1) / (1 - 2 e^{-l} cos w z^-1 + e^{-2l} z^-2)
+ * (w, l already divided by s). */
+void orc_rec_coeffs(double s, double nc[4], double dd[5], double na[5]) {
+  double num[2][2], den[2][3];
+  for (int i = 0; i < 2; ++i) {
+    const double w = orc_der_w[i] / s, l = orc_der_l[i] / s, e = exp(-l);
+    num[i][0] = orc_der_a[i];
+    num[i][1] = e * (orc_der_b[i] * sin(w) - orc_der_a[i] * cos(w));
+    den[i][0] = 1.0;
+    den[i][1] = -2.0 * e * cos(w);
+    den[i][2] = e * e;
+  }
+  for (int k = 0; k < 5; ++k) dd[k] = 0.0;
+  for (int p = 0; p < 3; ++p)
+    for (int q = 0; q < 3; ++q) dd[p + q] += den[0][p] * den[1][q];
+  for (int k = 0; k < 4; ++k) nc[k] = 0.0;
+  for (int p = 0; p < 2; ++p)
+    for (int q = 0; q < 3; ++q) nc[p + q] += num[0][p] * den[1][q] + num[1][p] * den[0][q];
+  /* anticausal: sum_{k>=1} g(k) z^k = N(1/z)/D(1/z) - g(0) */
+  na[0] = 0.0;
+  for (int k = 1; k < 4; ++k) na[k] = nc[k] - nc[0] * dd[k];
+  na[4] = -nc[0] * dd[4];
+  /* unit gain: (N(1) + Na(1)) / D(1) */
+  double sn = 0.0, sa = 0.0, sd = 0.0;
+  for (int k = 0; k < 4; ++k) sn += nc[k];
+  for (int k = 1; k < 5; ++k) sa += na[k];
+  for (int k = 0; k < 5; ++k) sd += dd[k];
+  const double gain = (sn + sa) / sd;
+  for (int k = 0; k < 4; ++k) nc[k] /= gain;
+  for (int k = 1; k < 5; ++k) na[k] /= gain;
+}
+
+/* One line x[0..L) through both recursions (zero before 0 and after L - 1):
+ * y = causal + anticausal.  Complex samples, real coefficients. */
+static void orc_rec_line(const double complex *x, long L, const double nc[4], const double dd[5],
+                         const double na[5], double complex *y, double complex *tmp) {
+  for (long i = 0; i < L; ++i) {
+    double complex acc = 0.0;
+    for (int k = 0; k < 4; ++k)
+      if (i - k >= 0) acc += nc[k] * x[i - k];
+    for (int k = 1; k < 5; ++k)
+      if (i - k >= 0) acc -= dd[k] * tmp[i - k];
+    tmp[i] = acc;
+  }
+  for (long i = L - 1; i >= 0; --i) {
+    double complex acc = 0.0;
+    for (int k = 1; k < 5; ++k)
+      if (i + k < L) acc += na[k] * x[i + k] - dd[k] * y[i + k];
+    y[i] = acc;
+  }
+  for (long i = 0; i < L; ++i) y[i] += tmp[i];
+}
+
+/* 1-D recursive filter of a real line (exported for the tests' impulse
+ * responses): x[0..L) -> y[0..L), zero outside. */
+void orc_rec_filter_line(const double *x, long L, double s, double *y) {
+  double nc[4], dd[5], na[5];
+  orc_rec_coeffs(s, nc, dd, na);
+  double complex *xc = malloc(sizeof(double complex) * L), *yc = malloc(sizeof(double complex) * L),
+                 *tc = malloc(sizeof(double complex) * L);
+  for (long i = 0; i < L; ++i) xc[i] = x[i];
+  orc_rec_line(xc, L, nc, dd, na, yc, tc);
+  for (long i = 0; i < L; ++i) y[i] = creal(yc[i]);
+  free(xc);
+  free(yc);
+  free(tc);
+}
+
+/* Separable recursive filter of an H x Wd complex image in place: each row,
+ * then each column, extended per the border reading above. */
+static void orc_rec2(double complex *X, int H, int Wd, double s, int border) {
+  double nc[4], dd[5], na[5];
+  orc_rec_coeffs(s, nc, dd, na);
+  const long E = border == ORC_BORDER_REFLECT ? (long)ceil(8.0 * s) : 0;
+  for (int pass = 0; pass < 2; ++pass) {
+    const long n = pass == 0 ? Wd : H, lines = pass == 0 ? H : Wd, L = n + 2 * E;
+#pragma omp parallel
+    {
+      double complex *xe = malloc(sizeof(double complex) * L), *ye = malloc(sizeof(double complex) * L),
+                     *te = malloc(sizeof(double complex) * L);
+#pragma omp for schedule(static)
+      for (long ln = 0; ln < lines; ++ln) {
+        for (long i = 0; i < L; ++i) {
+          const long j = border == ORC_BORDER_REFLECT ? orc_reflect(i - E, n) : i;
+          xe[i] = pass == 0 ? X[ln * Wd + j] : X[j * Wd + ln];
+        }
+        orc_rec_line(xe, L, nc, dd, na, ye, te);
+        for (long i = 0; i < n; ++i) {
+          if (pass == 0)
+            X[ln * Wd + i] = ye[i + E];
+          else
+            X[i * Wd + ln] = ye[i + E];
+        }
+      }
+      free(xe);
+      free(ye);
+      free(te);
+    }
+  }
+}
+
+/* Algorithm 1 with the recursive Gaussian in place of the FIR convolution
+ * (the constant-time variant of Sec. II): the same modulation, demodulation
+ * and c_{+-n} = d_n / 2 as orc_alg1, each channel filtered by orc_rec2.  Whole
+ * image; out, P, Q are H x Wd. */
+int orc_alg1_rec(const double *f, int H, int Wd, double sigma_s, int border, const double *d, int K,
+                 double T, double *out, double *P, double *Q) {
+  if (H < 1 || Wd < 1 || K < 1 || !(T > 0.0) || !(sigma_s > 0.0)) return -1;
+  const size_t np = (size_t)H * Wd;
+  double complex *G = malloc(sizeof(double complex) * np), *F = malloc(sizeof(double complex) * np);
+  double complex *Pc = calloc(np, sizeof(double complex)), *Qc = calloc(np, sizeof(double complex));
+  const double omega = M_PI / T;
+  const int N = K - 1;
+  for (int n = -N; n <= N; ++n) {
+    const int an = n < 0 ? -n : n;
+    const double cn = n == 0 ? d[0] : 0.5 * d[an];
+    for (size_t p = 0; p < np; ++p) {
+      G[p] = cexp(I * ((double)n * omega * f[p]));
+      F[p] = G[p] * f[p];
+    }
+    orc_rec2(F, H, Wd, sigma_s, border);
+    orc_rec2(G, H, Wd, sigma_s, border);
+    for (size_t p = 0; p < np; ++p) {
+      const double complex Hc = cn * conj(cexp(I * ((double)n * omega * f[p])));
+      Pc[p] += Hc * F[p];
+      Qc[p] += Hc * G[p];
+    }
+  }
+  for (size_t p = 0; p < np; ++p) {
+    out[p] = creal(Pc[p]) / creal(Qc[p]);
+    if (P) P[p] = creal(Pc[p]);
+    if (Q) Q[p] = creal(Qc[p]);
+  }
+  free(G);
+  free(F);
+  free(Pc);
+  free(Qc);
+  return 0;
 }
