@@ -493,6 +493,51 @@ def run_wide(fbf, torch, dev, stream, forms, steps, flush, with_oracle, slab_row
     return res
 
 
+def run_recursive(fbf, torch, dev, stream, steps, flush, with_oracle):
+    """The recursive Gaussian (the constant-time filtering Sec. II cites; Table 1
+    of Sec. V shows a run time flat in sigma_s): the 2048x2048 image (seed 1100),
+    sigma_r = 20 (K = 17), REFLECT, sigma_s from 3 to 32, FP32 recursive form
+    beside the FIR forms where their windows exist (W <= 48).  Errors: the
+    recursive form against the oracle's FP64 recursive mode on a 256 x 256 crop,
+    and its difference from the truncated-FIR FP32 output on the whole image."""
+    from paper_1603_08081_gb300.synth import make_image
+
+    img = make_image(H, W_IMG, SEED)
+    x = torch.from_numpy(img).to(dev)
+    y = torch.empty((H, W_IMG), dtype=torch.float32, device=dev)
+    y2 = torch.empty_like(y)
+    c = fbf.fbf_fit_coeffs("gaussian", 20.0, T, EPS)
+    crop = np.ascontiguousarray(img[:256, :256])
+    xc = torch.from_numpy(crop).to(dev)
+    res = {"workload": "2048x2048 u8 synthetic (seed 1100), sigma_r=20 (K=%d), eps=1e-3, reflect; "
+                       "recursive Gaussian (FP32) vs FIR forms" % c.K, "runs": []}
+    for ss in (3.0, 5.0, 10.0, 12.0, 16.0, 32.0):
+        p = fbf.make_params(c, ss, 0, "gaussian_recursive", "reflect", "fp32")
+        ms = _timed_steps(torch, dev, stream, lambda: fbf.fbf_filter(p, x, out=y, stream=stream), steps, flush)
+        row = {"sigma_s": ss, "form": "fp32_recursive", "ms": round(ms, 4), "mpix_s": round(H * W_IMG / ms / 1e3, 1)}
+        W = int(math.ceil(3 * ss - 1e-12))
+        if W <= 48:
+            for f in ("fp32", "tc_fp16_single"):
+                pf = fbf.make_params(c, ss, 0, "gaussian", "reflect", f)
+                msf = _timed_steps(torch, dev, stream, lambda: fbf.fbf_filter(pf, x, out=y2, stream=stream), steps,
+                                   flush)
+                row["fir_" + f + "_ms"] = round(msf, 4)
+            torch.cuda.synchronize(dev)
+            pf = fbf.make_params(c, ss, 0, "gaussian", "reflect", "fp32")
+            fbf.fbf_filter(pf, x, out=y2, stream=stream)
+            torch.cuda.synchronize(dev)
+            row["max_diff_vs_fir_fp32"] = round(float(torch.max(torch.abs(y - y2)).item()), 4)
+        if with_oracle:
+            import oracle as O
+
+            pc = fbf.fbf_filter(p, xc)
+            torch.cuda.synchronize(dev)
+            ref = O.alg1_rec(crop.astype(np.float64), ss, O.BORDER_REFLECT, np.array(c.coefficients), T)[0]
+            row["max_err_vs_oracle_crop256"] = round(float(np.max(np.abs(pc.cpu().numpy() - ref))), 6)
+        res["runs"].append(row)
+    return res
+
+
 def run_exponential(fbf, torch, dev, stream, steps, flush, with_oracle, slab_rows=32):
     """4096x4096 u8 image (seed 1200), exponential range kernel sigma_r = 20 with
     a fixed K = 40 (the eps = 1e-3 fit needs K = 255, timed once as a stress
@@ -827,6 +872,8 @@ def run_ours(args):
 
         extras["wide_window_2048"] = run_wide(fbf, torch, dev, stream, forms, ex_steps, flush_l2,
                                               not args.no_cpu_baseline)
+        extras["recursive_2048"] = run_recursive(fbf, torch, dev, stream, ex_steps, flush_l2,
+                                                 not args.no_cpu_baseline)
         extras["exponential_4096"] = run_exponential(fbf, torch, dev, stream, ex_steps, flush_l2,
                                                      not args.no_cpu_baseline)
         extras["differentiation"] = run_differentiation(fbf, torch, dev, stream, ex_steps,

@@ -19,7 +19,11 @@
  *   - Images are single channel, row-major, with a row pitch in BYTES.
  *   - Device pointers are plain CUDA device pointers; every device call is
  *     asynchronous on the given stream, never synchronises, and (unless stated)
- *     allocates nothing.  The caller owns every buffer.
+ *     allocates nothing.  The caller owns every buffer.  Calls that need
+ *     scratch take it stream-ordered from a memory pool the library creates
+ *     per device on first use; the pool keeps the memory it has reserved, so
+ *     the next call re-uses it (the memory stays reserved while the process
+ *     runs).
  *   - Errors are returned as fbf_status; nothing is thrown across the ABI.
  *     A fault inside a kernel surfaces at the caller's next synchronisation.
  */
@@ -50,7 +54,20 @@ typedef enum { FBF_RANGE_GAUSSIAN = 0, FBF_RANGE_EXPONENTIAL = 1 } fbf_range_ker
 
 /* Spatial kernel w on Omega = [-W, W]^2 (Sec. I).  Gaussian: eq. (2),
  * separable; box: uniform.  Weights are normalised to sum 1 (Sec. IV). */
-typedef enum { FBF_SPATIAL_GAUSSIAN = 0, FBF_SPATIAL_BOX = 1 } fbf_spatial_kernel;
+typedef enum {
+  FBF_SPATIAL_GAUSSIAN = 0,
+  FBF_SPATIAL_BOX = 1,
+  /* The recursive Gaussian (the constant-time Gaussian filtering that Sec. II
+   * cites after eq. (5): Deriche's fourth-order approximation, two damped
+   * sinusoids per direction realised as causal + anticausal recursions, unit
+   * gain).  Its cost per pixel does not depend on sigma_s: there is no window
+   * (W is not used).  TRUNCATE: zero outside the image; REFLECT: each line
+   * extended by ceil(8 sigma_s) mirrored samples.  0.5 <= sigma_s <= 256; the
+   * FP32 form (AUTO selects it) on uint8 images; fbf_filter then takes 40
+   * bytes per pixel and harmonic of scratch (at most 4 GiB, harmonics in
+   * chunks beyond that) stream-ordered from the library's pool. */
+  FBF_SPATIAL_GAUSSIAN_RECURSIVE = 2
+} fbf_spatial_kernel;
 
 /* Border rule (the paper leaves it open).  REFLECT: half-sample symmetric
  * extension (index -1 -> 0, -2 -> 1, ...; repeated for windows wider than the
@@ -285,7 +302,7 @@ fbf_status fbf_plan_schedule(const fbf_plan *plan, fbf_schedule *schedule, doubl
  *   d_out_fwd  ignored (may be NULL): Q is needed, so the forward is recomputed
  *   d_gin      FP32 output dL/df, same shape and pitch
  * Allocates its scratch (8 bytes per pixel, plus (H+2W)(Wd+2W) floats under
- * REFLECT) stream-ordered with cudaMallocAsync / cudaFreeAsync on `stream`.
+ * REFLECT) stream-ordered from the library's pool on `stream`.
  * W <= 32.  Returns FBF_ERR_UNSUPPORTED for the tensor-core forms.
  */
 fbf_status fbf_filter_backward(const fbf_params *p, const float *d_in, const float *d_gout,

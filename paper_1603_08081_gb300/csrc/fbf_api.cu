@@ -21,12 +21,15 @@ fbf_status pack_filter_args(const fbf_params *p, const void *d_in, fbf_dtype dty
   if (!p || !p->coeffs || !a) return FBF_ERR_INVALID_ARGUMENT;
   if (H < 0 || Wd < 0) return FBF_ERR_INVALID_ARGUMENT;
   if (dtype != FBF_U8 && dtype != FBF_F32) return FBF_ERR_INVALID_ARGUMENT;
-  if (p->spatial != FBF_SPATIAL_GAUSSIAN && p->spatial != FBF_SPATIAL_BOX) return FBF_ERR_INVALID_ARGUMENT;
+  const bool rec = p->spatial == FBF_SPATIAL_GAUSSIAN_RECURSIVE;
+  if (p->spatial != FBF_SPATIAL_GAUSSIAN && p->spatial != FBF_SPATIAL_BOX && !rec) return FBF_ERR_INVALID_ARGUMENT;
   if (p->border != FBF_BORDER_REFLECT && p->border != FBF_BORDER_TRUNCATE) return FBF_ERR_INVALID_ARGUMENT;
   if (p->spatial == FBF_SPATIAL_GAUSSIAN && !(p->sigma_s > 0.0 && std::isfinite(p->sigma_s)))
     return FBF_ERR_INVALID_ARGUMENT;
   if (p->spatial == FBF_SPATIAL_BOX && p->W <= 0) return FBF_ERR_INVALID_ARGUMENT;
-  const int W = resolve_window(p->spatial, p->sigma_s, p->W);
+  if (rec && !(p->sigma_s > 0.0 && std::isfinite(p->sigma_s))) return FBF_ERR_INVALID_ARGUMENT;
+  if (rec && !(p->sigma_s >= 0.5 && p->sigma_s <= 256.0)) return FBF_ERR_RANGE;
+  const int W = rec ? 0 : resolve_window(p->spatial, p->sigma_s, p->W);
   if (W < 0) return FBF_ERR_INVALID_ARGUMENT;
   if (W > FBF_WMAX) return FBF_ERR_RANGE;
   const fbf_coeffs *c = p->coeffs;
@@ -61,7 +64,9 @@ fbf_status pack_filter_args(const fbf_params *p, const void *d_in, fbf_dtype dty
   a->twoT = dtype == FBF_U8 ? 2 * (int)c->T : 0;
   a->border = (int)p->border;
   a->box = p->spatial == FBF_SPATIAL_BOX ? 1 : 0;
-  spatial_weights(p->spatial, p->sigma_s, W, a->w);
+  spatial_weights(rec ? FBF_SPATIAL_BOX : p->spatial, p->sigma_s, W, a->w);
+  a->rec = rec ? 1 : 0;
+  if (rec) recursive_coeffs(p->sigma_s, a);
   for (int j = 0; j < 2 * W + 1; ++j) {
     unsigned int b;
     std::memcpy(&b, &a->w[j], sizeof(b));
@@ -82,6 +87,10 @@ namespace fbf {
 fbf_status launch_filter(const FilterArgs &a, fbf_form form, fbf_dtype dtype, cudaStream_t stream) {
   const bool tc = is_tc_form(form);
   if (form != FBF_FORM_AUTO && form != FBF_FORM_FP32 && !tc) return FBF_ERR_INVALID_ARGUMENT;
+  if (a.rec) {  // the recursive Gaussian: FP32 form, uint8 input
+    if (tc || dtype != FBF_U8) return FBF_ERR_UNSUPPORTED;
+    return launch_rec_u8(a, stream);
+  }
   if (dtype == FBF_F32) {
     if (tc) return FBF_ERR_UNSUPPORTED;
     if (a.W > f32_wmax()) return FBF_ERR_RANGE;
@@ -129,9 +138,9 @@ extern "C" fbf_status fbf_filter_backward(const fbf_params *p, const float *d_in
   if (a.W > f32_wmax()) return FBF_ERR_RANGE;
   const size_t bytes = backward_scratch_bytes(H, Wd, a.W, a.border);
   void *scratch = nullptr;
-  if (cudaMallocAsync(&scratch, bytes, stream) != cudaSuccess) return FBF_ERR_CUDA;
+  if (scratch_alloc(&scratch, bytes, stream) != FBF_OK) return FBF_ERR_CUDA;
   st = launch_backward(a, d_gout, pitch, d_gin, pitch, scratch, stream);
-  if (cudaFreeAsync(scratch, stream) != cudaSuccess && st == FBF_OK) st = FBF_ERR_CUDA;
+  if (scratch_free(scratch, stream) != FBF_OK && st == FBF_OK) st = FBF_ERR_CUDA;
   return st;
 }
 
@@ -148,7 +157,7 @@ extern "C" fbf_status fbf_filter_stack(const fbf_params *p, const void *d_in, fb
   // image i starts i strides in: float images need strides that keep 4-byte alignment
   if (N > 1 && (out_image_stride % sizeof(float) != 0 || (dtype == FBF_F32 && in_image_stride % sizeof(float) != 0)))
     return FBF_ERR_INVALID_ARGUMENT;
-  if (dtype == FBF_F32 && (p->form == FBF_FORM_AUTO || p->form == FBF_FORM_FP32)) {
+  if (dtype == FBF_F32 && (p->form == FBF_FORM_AUTO || p->form == FBF_FORM_FP32) && !a.rec) {
     // float images: the whole stack in one launch (chunks of at most 65535 images)
     if (a.W > f32_wmax()) return FBF_ERR_RANGE;
     for (int i0 = 0; i0 < N && st == FBF_OK; i0 += 65535) {
@@ -186,7 +195,7 @@ extern "C" fbf_status fbf_filter_backward_stack(const fbf_params *p, const float
   const size_t per = backward_scratch_stride(H, Wd, a.W, a.border);
   const int chunk = (int)std::max<size_t>(1, std::min<size_t>({(size_t)N, (size_t)65535, kStackScratch / per}));
   void *scratch = nullptr;
-  if (cudaMallocAsync(&scratch, per * (size_t)chunk, stream) != cudaSuccess) return FBF_ERR_CUDA;
+  if (scratch_alloc(&scratch, per * (size_t)chunk, stream) != FBF_OK) return FBF_ERR_CUDA;
   for (int i0 = 0; i0 < N && st == FBF_OK; i0 += chunk) {
     const size_t off = (size_t)i0 * image_stride;
     a.in = reinterpret_cast<const char *>(d_in) + off;
@@ -195,7 +204,7 @@ extern "C" fbf_status fbf_filter_backward_stack(const fbf_params *p, const float
     st = launch_backward_stack(a, std::min(chunk, N - i0), image_stride, g, pitch, image_stride, a.out, pitch,
                                image_stride, scratch, per, stream);
   }
-  if (cudaFreeAsync(scratch, stream) != cudaSuccess && st == FBF_OK) st = FBF_ERR_CUDA;
+  if (scratch_free(scratch, stream) != FBF_OK && st == FBF_OK) st = FBF_ERR_CUDA;
   return st;
 }
 

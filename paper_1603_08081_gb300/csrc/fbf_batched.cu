@@ -329,6 +329,7 @@ static fbf_status plan_create(const fbf_image_desc *descs, int n, fbf_form form,
   int wmax = 0;
   for (int i = 0; i < n; ++i) {
     const fbf_image_desc &d = descs[i];
+    if (d.spatial == FBF_SPATIAL_GAUSSIAN_RECURSIVE) return FBF_ERR_UNSUPPORTED;  // single-image calls only
     fbf_coeffs c;
     fbf_status st = fbf_fit_coeffs(d.range, d.sigma_r, d.T, d.eps, d.K_fixed, d.levels, &c);
     if (st != FBF_OK) return st;

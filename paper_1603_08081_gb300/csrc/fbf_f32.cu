@@ -391,6 +391,7 @@ fbf_status launch_backward(const FilterArgs &a, const float *g, size_t g_pitch, 
 fbf_status launch_backward_stack(const FilterArgs &a, int n, size_t in_istride, const float *g, size_t g_pitch,
                                  size_t g_istride, float *gin, size_t gin_pitch, size_t gin_istride, void *scratch,
                                  size_t scratch_istride, cudaStream_t s) {
+  if (a.rec) return FBF_ERR_UNSUPPORTED;  // the adjoint has the FIR kernels only
   if (a.W > kWcapF) return FBF_ERR_RANGE;
   if (n < 1 || n > 65535 || scratch_istride % 256 != 0) return FBF_ERR_INVALID_ARGUMENT;
   const int H = a.H, Wd = a.Wd, W = a.W;

@@ -24,6 +24,38 @@ int resolve_window(fbf_spatial_kernel spatial, double sigma_s, int W) {
   return (int)w;
 }
 
+// Recursive Gaussian (the constant-time Gaussian filtering cited in Sec. II,
+// after eq. (5): Deriche 1993).  Deriche writes exp(-x^2 / (2 s^2)), x >= 0, as
+// two damped sinusoids (a_i cos(w_i x/s) + b_i sin(w_i x/s)) exp(-l_i x/s) with
+// the published constants below.  Each term, sampled at k >= 0, is the impulse
+// response of a second-order section: its z-transform is
+//   (a + e^{-l}(b sin w - a cos w) z^-1) / (1 - 2 e^{-l} cos w z^-1 + e^{-2l} z^-2)
+// (w, l divided by s); its mirror k <= -1 is the anticausal section with
+// numerator N(1/z) - a D(1/z) on z, z^2.  The two sections run in parallel and
+// their sum is scaled to unit gain.
+void recursive_coeffs(double sigma_s, FilterArgs *a) {
+  static const double ka[2] = {1.680, -0.6803}, kb[2] = {3.735, -0.2598};
+  static const double kw[2] = {0.6318, 1.997}, kl[2] = {1.783, 1.723};
+  double n[2][2], m[2][2], p[2][2], gain = 0.0;
+  for (int i = 0; i < 2; ++i) {
+    const double w = kw[i] / sigma_s, e = std::exp(-kl[i] / sigma_s);
+    n[i][0] = ka[i];
+    n[i][1] = e * (kb[i] * std::sin(w) - ka[i] * std::cos(w));
+    p[i][0] = -2.0 * e * std::cos(w);
+    p[i][1] = e * e;
+    m[i][0] = n[i][1] - n[i][0] * p[i][0];
+    m[i][1] = -n[i][0] * p[i][1];
+    gain += (n[i][0] + n[i][1] + m[i][0] + m[i][1]) / (1.0 + p[i][0] + p[i][1]);
+  }
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) {
+      a->rn[i][j] = (float)(n[i][j] / gain);
+      a->rm[i][j] = (float)(m[i][j] / gain);
+      a->rp[i][j] = (float)p[i][j];
+    }
+  a->rE = (int)std::ceil(8.0 * sigma_s);
+}
+
 // Normalised 1-D weights w1[j + W], j = -W..W, sum 1; the 2-D kernel of eq. (2)
 // is w1(j_y) w1(j_x) and sums to 1 (Sec. IV assumes unit sum).
 void spatial_weights(fbf_spatial_kernel spatial, double sigma_s, int W, float *w1) {

@@ -1,6 +1,7 @@
 // Host-side state shared by the launchers: the TMA tensor maps of input images
 // (encoded once per pointer, shape and pitch), the multiprocessor count per
-// device, and the poll limit of the kernels' bounded waits.
+// device, the poll limit of the kernels' bounded waits, and the stream-ordered
+// memory pool of the calls that need scratch.
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
@@ -43,6 +44,8 @@ int g_map_next = 0;
 
 constexpr int kMaxDev = 64;
 std::atomic<int> g_sms[kMaxDev];
+std::mutex g_pool_mu;
+cudaMemPool_t g_pools[kMaxDev] = {};
 
 // Default poll limit of the tensor-core kernels' bounded waits (about a second
 // of polling on GB300), or the limit set by fbf_set_wait_limit.
@@ -95,6 +98,40 @@ int sm_count(int dev) {
     g_sms[dev].store(v, std::memory_order_relaxed);
   }
   return v;
+}
+
+// The library's own stream-ordered pool per device, created on first use,
+// keeping the memory it has reserved (release threshold: unlimited) so that a
+// call's scratch is re-used by the next call instead of being mapped again.
+static cudaMemPool_t scratch_pool(int dev) {
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  if (!g_pools[dev]) {
+    cudaMemPoolProps props = {};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.handleTypes = cudaMemHandleTypeNone;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t pool = nullptr;
+    if (cudaMemPoolCreate(&pool, &props) != cudaSuccess) return nullptr;
+    unsigned long long keep = ~0ull;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pools[dev] = pool;
+  }
+  return g_pools[dev];
+}
+
+fbf_status scratch_alloc(void **p, size_t bytes, cudaStream_t s) {
+  *p = nullptr;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return FBF_ERR_CUDA;
+  cudaMemPool_t pool = scratch_pool(dev);
+  if (!pool) return FBF_ERR_CUDA;
+  return cudaMallocFromPoolAsync(p, bytes, pool, s) == cudaSuccess ? FBF_OK : FBF_ERR_CUDA;
+}
+
+fbf_status scratch_free(void *p, cudaStream_t s) {
+  if (!p) return FBF_OK;
+  return cudaFreeAsync(p, s) == cudaSuccess ? FBF_OK : FBF_ERR_CUDA;
 }
 
 unsigned int wait_polls() {

@@ -18,8 +18,14 @@ namespace fbf {
 
 constexpr int TAPS_MAX = 2 * FBF_WMAX + 1;
 
+struct FilterArgs;
+
 // Host helpers (fbf_fit.cpp).
 int resolve_window(fbf_spatial_kernel spatial, double sigma_s, int W);
+// Recursive Gaussian of scale sigma_s into a->rn / rm / rp / rE (unit gain).
+void recursive_coeffs(double sigma_s, FilterArgs *a);
+// Recursive-Gaussian filter of one u8 image (FP32; scratch stream-ordered).
+fbf_status launch_rec_u8(const FilterArgs &a, cudaStream_t s);
 void spatial_weights(fbf_spatial_kernel spatial, double sigma_s, int W, float *w1);
 
 // Everything one filter launch needs, passed by value as a __grid_constant__
@@ -42,6 +48,12 @@ struct FilterArgs {
   float w[TAPS_MAX];  // normalised 1-D spatial taps w1[j + W]
   float d[FBF_KMAX];  // cosine coefficients, eq. (6)
   unsigned long long w2[TAPS_MAX];  // each tap duplicated into both halves of an f32x2 pair
+  // Recursive Gaussian (spatial FBF_SPATIAL_GAUSSIAN_RECURSIVE, rec = 1): two
+  // second-order sections per direction, section i: causal numerator rn[i][0..1],
+  // anticausal numerator rm[i][0..1] (on x[k+1], x[k+2]), denominator
+  // 1 + rp[i][0] z^-1 + rp[i][1] z^-2; REFLECT extension rE samples per side.
+  int rec, rE;
+  float rn[2][2], rm[2][2], rp[2][2];
 };
 
 // Common host-side validation + argument packing for the single-image forms.
@@ -131,6 +143,10 @@ bool cached_box_map(const void *ptr, int Wd, int H, size_t pitch, int bw, int bh
 int sm_count(int dev);                // multiprocessor count, cached per device
 unsigned int *device_error_word();    // device address of the library's error word (current device)
 unsigned int wait_polls();            // poll limit of the kernels' bounded waits
+// Stream-ordered scratch from the library's pool on the current device (kept
+// reserved between calls); free it on the same stream.
+fbf_status scratch_alloc(void **p, size_t bytes, cudaStream_t s);
+fbf_status scratch_free(void *p, cudaStream_t s);
 // cudaFuncSetAttribute once per kernel and device (a bit per device ordinal < 64).
 struct FuncAttrOnce {
   unsigned long long mask = 0;

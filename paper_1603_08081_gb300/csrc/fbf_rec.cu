@@ -1,0 +1,356 @@
+// Algorithm 1 with the recursive Gaussian (the constant-time Gaussian filtering
+// that Sec. II cites after eq. (5): Deriche's fourth-order approximation) for
+// uint8 images, FP32.  The cost per pixel and harmonic does not depend on
+// sigma_s: each 1-D pass is a causal and an anticausal recursion of two
+// second-order sections per channel (coefficients from recursive_coeffs).
+//
+// Per chunk of harmonics (all of them when the scratch fits 4 GiB), three
+// kernels, one thread per image line and harmonic:
+//   rec_v    thread (column x, harmonic n): modulates f(y, x) on the fly into
+//            the four real channels (cos, sin, (f - T/2) cos, (f - T/2) sin)(n w f)
+//            (exact integer phase n f mod 2T, a 256-entry table per block), runs
+//            the causal recursion down the column and the anticausal one up
+//            it, and writes their sum to vt[n][c][x][y] -- transposed, through a
+//            32 x 32 shared-memory tile per channel (the causal half waits in
+//            the s2 planes in natural layout), so that every global access of
+//            both passes is coalesced;
+//   rec_h    thread (row y, harmonic n): the same recursions along x on vt
+//            (consecutive threads read consecutive y: coalesced), the causal
+//            result kept in s2 (same layout), then demodulation:
+//            (P_n, Q_n) = d_n ((cos, sin) . (Fr, Fi), (cos, sin) . (Gr, Gi));
+//   rec_out  sums (P_n, Q_n) over the chunk (and the chunks before it) and, on
+//            the last chunk, writes fhat = P / Q + T/2 through a tile transpose.
+// Borders: TRUNCATE is zero outside the image; REFLECT extends every line by E
+// mirrored samples on each side (half-sample symmetric, repeated), zero beyond.
+// Scratch: 40 bytes per pixel and harmonic of the chunk, plus 8 per pixel,
+// allocated and freed stream-ordered from the library's pool.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "fbf_common.cuh"
+#include "fbf_internal.h"
+
+namespace fbf {
+namespace {
+
+constexpr int kChunk = 16;  // vertical pass: steps whose loads are issued together
+constexpr int kChunkA = 8;  // its anticausal half (four more loads per step)
+constexpr int kChunkH = 8;  // horizontal pass: the same
+
+struct RecArgs {
+  const unsigned char *in;
+  size_t in_pitch;
+  float *out;
+  size_t out_pitch;
+  int H, Wd, twoT, border, E;
+  int n0, nh, first, last;  // harmonics n0 .. n0 + nh - 1; first / last chunk
+  float T, c0;
+  float rn[2][2], rm[2][2], rp[2][2];
+  float *vt;    // [nh][4][Wd][H] vertical pass, transposed
+  float *s2;    // [nh][4] planes: causal half of the vertical pass ([y][x]), then of the horizontal one ([x][y])
+  float2 *pq;   // [nh][Wd][H]    (P_n, Q_n)
+  float2 *acc;  // [Wd][H]        (P, Q) of the chunks so far
+  float d[FBF_KMAX];
+};
+
+// (cos, sin)(pi m / T), m = n v mod 2T, for v = 0..255 (exact integer phase).
+__device__ __forceinline__ void build_tab(float2 *tab, int n, const RecArgs &r) {
+  for (int v = threadIdx.x + threadIdx.y * blockDim.x; v < 256; v += blockDim.x * blockDim.y) {
+    const int m = (int)(((long long)n * v) % r.twoT);
+    float sn, cs;
+    sincospif((float)m / r.T, &sn, &cs);
+    tab[v] = make_float2(cs, sn);
+  }
+  __syncthreads();
+}
+
+// One step of the causal recursion (both sections, four channels): input c,
+// state x1 (previous input), y1, y2 (previous outputs per section); returns
+// the sum of the sections in yo.
+struct Causal {
+  float x1[4] = {}, y1[2][4] = {}, y2[2][4] = {};
+  __device__ __forceinline__ void step(const RecArgs &r, const float (&c)[4], float (&yo)[4]) {
+#pragma unroll
+    for (int ch = 0; ch < 4; ++ch) {
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const float yn = fmaf(-r.rp[i][0], y1[i][ch],
+                              fmaf(r.rn[i][0], c[ch], fmaf(r.rn[i][1], x1[ch], -r.rp[i][1] * y2[i][ch])));
+        y2[i][ch] = y1[i][ch];
+        y1[i][ch] = yn;
+      }
+      yo[ch] = y1[0][ch] + y1[1][ch];
+      x1[ch] = c[ch];
+    }
+  }
+};
+// The anticausal recursion, run backwards: the output at k uses the inputs at
+// k + 1, k + 2 (x1, x2) and the outputs at k + 1, k + 2; then takes input c.
+struct Anticausal {
+  float x1[4] = {}, x2[4] = {}, z1[2][4] = {}, z2[2][4] = {};
+  __device__ __forceinline__ void step(const RecArgs &r, const float (&c)[4], float (&yo)[4]) {
+#pragma unroll
+    for (int ch = 0; ch < 4; ++ch) {
+#pragma unroll
+      for (int i = 0; i < 2; ++i) {
+        const float zn = fmaf(-r.rp[i][0], z1[i][ch],
+                              fmaf(r.rm[i][0], x1[ch], fmaf(r.rm[i][1], x2[ch], -r.rp[i][1] * z2[i][ch])));
+        z2[i][ch] = z1[i][ch];
+        z1[i][ch] = zn;
+      }
+      yo[ch] = z1[0][ch] + z1[1][ch];
+      x2[ch] = x1[ch];
+      x1[ch] = c[ch];
+    }
+  }
+};
+
+__global__ void __launch_bounds__(32) fbf_rec_v_kernel(const __grid_constant__ RecArgs r) {
+  __shared__ float2 tab[256];
+  __shared__ float tile[4][32][33];  // [channel][column in block][row in group]
+  const int lane = threadIdx.x, x0 = blockIdx.x * 32, x = x0 + lane, nl = blockIdx.y;
+  build_tab(tab, r.n0 + nl, r);
+  const int H = r.H, Wd = r.Wd;
+  const bool reflect = r.border == FBF_BORDER_REFLECT;
+  const int E = reflect ? r.E : 0;
+  const int xs = x < Wd ? x : Wd - 1;  // lanes past the image compute on a clamped column, store nothing
+  float *vt = r.vt + (size_t)nl * 4 * Wd * H;
+  // pixel of extended row ye, or -1 outside a TRUNCATE image
+  auto load = [&](int ye) -> int {
+    if (!reflect && (ye < 0 || ye >= H)) return -1;
+    const int sy = reflect ? reflect_index(ye, H) : ye;
+    return __ldg(r.in + (size_t)sy * r.in_pitch + xs);
+  };
+  auto chan = [&](int v, float (&c)[4]) {
+    if (v < 0) {
+      c[0] = c[1] = c[2] = c[3] = 0.f;
+      return;
+    }
+    const float2 cs = tab[v];
+    const float fv = (float)v - r.c0;
+    c[0] = cs.x;
+    c[1] = cs.y;
+    c[2] = fv * cs.x;
+    c[3] = fv * cs.y;
+  };
+  // the tile of rows [base, last] to / from vt: lane = row offset (coalesced)
+  auto flush = [&](int base, int lastrow) {
+    __syncwarp();
+    const int y = base + lane;
+    for (int ch = 0; ch < 4; ++ch)
+      for (int xl = 0; xl < 32 && x0 + xl < Wd; ++xl)
+        if (y <= lastrow) vt[((size_t)ch * Wd + x0 + xl) * H + y] = tile[ch][xl][lane];
+    __syncwarp();
+  };
+  // The loads of a chunk of steps are issued together, then the recursion runs
+  // over them: one load latency per chunk instead of one per step.  The causal
+  // half goes to s2 in natural layout ([c][y][x], coalesced over the lanes);
+  // the anticausal pass reads it back with its own loads and writes the sum
+  // to vt through the transposing tile.
+  float *sh = r.s2 + (size_t)nl * 4 * Wd * H;
+  const size_t plane = (size_t)Wd * H;
+  const bool xin = x < Wd;
+  Causal cz;
+  for (int y0 = -E; y0 < H + E; y0 += kChunk) {
+    int vv[kChunk];
+#pragma unroll
+    for (int j = 0; j < kChunk; ++j) vv[j] = y0 + j < H + E ? load(y0 + j) : -1;
+#pragma unroll
+    for (int j = 0; j < kChunk; ++j) {
+      const int ye = y0 + j;
+      if (ye >= H + E) break;
+      float c[4], yo[4];
+      chan(vv[j], c);
+      cz.step(r, c, yo);
+      if (xin && ye >= 0 && ye < H) {
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) sh[(size_t)ch * plane + (size_t)ye * Wd + x] = yo[ch];
+      }
+    }
+  }
+  Anticausal az;
+  for (int y0 = H + E - 1; y0 >= -E; y0 -= kChunkA) {
+    int vv[kChunkA];
+    float sv[kChunkA][4];
+#pragma unroll
+    for (int j = 0; j < kChunkA; ++j) {
+      const int ye = y0 - j;
+      vv[j] = ye >= -E ? load(ye) : -1;
+      const bool out = xin && ye >= 0 && ye < H;
+#pragma unroll
+      for (int ch = 0; ch < 4; ++ch) sv[j][ch] = out ? sh[(size_t)ch * plane + (size_t)ye * Wd + x] : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < kChunkA; ++j) {
+      const int ye = y0 - j;
+      if (ye < -E) break;
+      float c[4], yo[4];
+      chan(vv[j], c);
+      az.step(r, c, yo);
+      if (ye >= 0 && ye < H) {
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) tile[ch][lane][ye & 31] = yo[ch] + sv[j][ch];
+        if ((ye & 31) == 0) flush(ye, ye + 31 < H - 1 ? ye + 31 : H - 1);
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(32) fbf_rec_h_kernel(const __grid_constant__ RecArgs r) {
+  __shared__ float2 tab[256];
+  const int lane = threadIdx.x, y = blockIdx.x * 32 + lane, nl = blockIdx.y, n = r.n0 + nl;
+  build_tab(tab, n, r);
+  const int H = r.H, Wd = r.Wd;
+  const bool reflect = r.border == FBF_BORDER_REFLECT;
+  const int E = reflect ? r.E : 0;
+  const bool yin = y < H;
+  const size_t plane = (size_t)Wd * H;
+  const float *vt = r.vt + (size_t)nl * 4 * plane;
+  float *s2 = r.s2 + (size_t)nl * 4 * plane;
+  float2 *pq = r.pq + (size_t)nl * plane;
+  const float dn = r.d[n];
+  auto chan = [&](int xe, float (&c)[4]) {
+    const bool in_img = xe >= 0 && xe < Wd;
+    if (!yin || (!reflect && !in_img) || xe < -E || xe >= Wd + E) {
+      c[0] = c[1] = c[2] = c[3] = 0.f;
+      return;
+    }
+    const int sx = reflect ? reflect_index(xe, Wd) : xe;
+#pragma unroll
+    for (int ch = 0; ch < 4; ++ch) c[ch] = vt[(size_t)ch * plane + (size_t)sx * H + y];
+  };
+  // kChunkH steps' loads are issued together (see rec_v)
+  Causal cz;
+  for (int x0 = -E; x0 < Wd + E; x0 += kChunkH) {
+    float cc[kChunkH][4];
+#pragma unroll
+    for (int j = 0; j < kChunkH; ++j) chan(x0 + j, cc[j]);
+#pragma unroll
+    for (int j = 0; j < kChunkH; ++j) {
+      const int xe = x0 + j;
+      if (xe >= Wd + E) break;
+      float yo[4];
+      cz.step(r, cc[j], yo);
+      if (yin && xe >= 0 && xe < Wd) {
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) s2[(size_t)ch * plane + (size_t)xe * H + y] = yo[ch];
+      }
+    }
+  }
+  Anticausal az;
+  const unsigned char *row = r.in + (size_t)(yin ? y : 0) * r.in_pitch;
+  for (int x0 = Wd + E - 1; x0 >= -E; x0 -= kChunkH) {
+    float cc[kChunkH][4], sv[kChunkH][4];
+    int fv[kChunkH];
+#pragma unroll
+    for (int j = 0; j < kChunkH; ++j) {
+      const int xe = x0 - j;
+      chan(xe, cc[j]);
+      const bool out = yin && xe >= 0 && xe < Wd;
+#pragma unroll
+      for (int ch = 0; ch < 4; ++ch) sv[j][ch] = out ? s2[(size_t)ch * plane + (size_t)xe * H + y] : 0.f;
+      fv[j] = out ? __ldg(row + xe) : 0;
+    }
+#pragma unroll
+    for (int j = 0; j < kChunkH; ++j) {
+      const int xe = x0 - j;
+      if (xe < -E) break;
+      float yo[4];
+      az.step(r, cc[j], yo);
+      if (yin && xe >= 0 && xe < Wd) {
+        float v[4];
+#pragma unroll
+        for (int ch = 0; ch < 4; ++ch) v[ch] = yo[ch] + sv[j][ch];
+        // demodulate: Re[e^{-i n w f} (filtered channel)] for the G and F pairs
+        const float2 cs = tab[fv[j]];
+        pq[(size_t)xe * H + y] = make_float2(dn * fmaf(cs.x, v[2], cs.y * v[3]), dn * fmaf(cs.x, v[0], cs.y * v[1]));
+      }
+    }
+  }
+}
+
+// (P, Q) summed over the chunk's harmonics (and the earlier chunks' acc); the
+// last chunk writes fhat = P / Q + T/2.  Block 32 x 32: threadIdx.x = row offset
+// (coalesced reads of the transposed planes), tile transpose for the output.
+__global__ void __launch_bounds__(1024) fbf_rec_out_kernel(const __grid_constant__ RecArgs r) {
+  __shared__ float t[32][33];
+  const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+  const int ty = threadIdx.y, tx = threadIdx.x;
+  const int x = x0 + ty, y = y0 + tx;
+  const int H = r.H, Wd = r.Wd;
+  const bool in = x < Wd && y < H;
+  float2 a = make_float2(0.f, 0.f);
+  if (in) {
+    const size_t o = (size_t)x * H + y, plane = (size_t)Wd * H;
+    if (!r.first) a = r.acc[o];
+    for (int nl = 0; nl < r.nh; ++nl) {
+      const float2 v = r.pq[(size_t)nl * plane + o];
+      a.x += v.x;
+      a.y += v.y;
+    }
+    if (!r.last) r.acc[o] = a;
+  }
+  if (!r.last) return;  // uniform over the grid
+  t[ty][tx] = in ? a.x / a.y + r.c0 : 0.f;
+  __syncthreads();
+  const int ox = x0 + tx, oy = y0 + ty;  // write out[oy][ox] = t[tx][ty]: coalesced over tx
+  if (ox < Wd && oy < H)
+    *reinterpret_cast<float *>(reinterpret_cast<char *>(r.out) + (size_t)oy * r.out_pitch + (size_t)ox * sizeof(float)) =
+        t[tx][ty];
+}
+
+}  // namespace
+
+fbf_status launch_rec_u8(const FilterArgs &a, cudaStream_t s) {
+  if (!a.rec || a.twoT < 2) return FBF_ERR_INVALID_ARGUMENT;
+  const int H = a.H, Wd = a.Wd, K = a.K;
+  if (H <= 0 || Wd <= 0) return FBF_OK;
+  const size_t px = (size_t)H * Wd;
+  const size_t per_h = px * (4 * sizeof(float) * 2 + sizeof(float2));  // vt, s2, pq
+  constexpr size_t kBudget = (size_t)4 << 30;
+  const int nh = (int)std::max<size_t>(1, std::min<size_t>((size_t)K, kBudget / per_h));
+  const size_t vt_b = (size_t)nh * 4 * px * sizeof(float), pq_b = (size_t)nh * px * sizeof(float2);
+  const size_t acc_b = K > nh ? px * sizeof(float2) : 0;
+  char *scratch = nullptr;
+  if (scratch_alloc(reinterpret_cast<void **>(&scratch), 2 * vt_b + pq_b + acc_b + 256, s) != FBF_OK)
+    return FBF_ERR_CUDA;
+  RecArgs r;
+  r.in = static_cast<const unsigned char *>(a.in);
+  r.in_pitch = a.in_pitch;
+  r.out = a.out;
+  r.out_pitch = a.out_pitch;
+  r.H = H;
+  r.Wd = Wd;
+  r.twoT = a.twoT;
+  r.border = a.border;
+  r.E = a.rE;
+  r.T = a.T;
+  r.c0 = 0.5f * a.T;
+  for (int i = 0; i < 2; ++i)
+    for (int j = 0; j < 2; ++j) {
+      r.rn[i][j] = a.rn[i][j];
+      r.rm[i][j] = a.rm[i][j];
+      r.rp[i][j] = a.rp[i][j];
+    }
+  for (int k = 0; k < FBF_KMAX; ++k) r.d[k] = k < K ? a.d[k] : 0.f;
+  r.vt = reinterpret_cast<float *>(scratch);
+  r.s2 = reinterpret_cast<float *>(scratch + vt_b);
+  r.pq = reinterpret_cast<float2 *>(scratch + 2 * vt_b);
+  r.acc = acc_b ? reinterpret_cast<float2 *>(scratch + 2 * vt_b + pq_b) : nullptr;
+  fbf_status st = FBF_OK;
+  for (int n0 = 0; n0 < K && st == FBF_OK; n0 += nh) {
+    r.n0 = n0;
+    r.nh = std::min(nh, K - n0);
+    r.first = n0 == 0;
+    r.last = n0 + r.nh >= K;
+    fbf_rec_v_kernel<<<dim3((Wd + 31) / 32, r.nh), 32, 0, s>>>(r);
+    fbf_rec_h_kernel<<<dim3((H + 31) / 32, r.nh), 32, 0, s>>>(r);
+    fbf_rec_out_kernel<<<dim3((Wd + 31) / 32, (H + 31) / 32), dim3(32, 32), 0, s>>>(r);
+    st = cuda_status(cudaGetLastError());
+  }
+  if (scratch_free(scratch, s) != FBF_OK && st == FBF_OK) st = FBF_ERR_CUDA;
+  return st;
+}
+
+}  // namespace fbf

@@ -19,7 +19,7 @@ WMAX = 48
 FBF_OK, FBF_ERR_INVALID_ARGUMENT, FBF_ERR_NOT_CONVERGED, FBF_ERR_RANGE = 0, 1, 2, 3
 FBF_ERR_UNSUPPORTED, FBF_ERR_CUDA, FBF_ERR_TIMEOUT = 4, 5, 6
 FBF_RANGE_GAUSSIAN, FBF_RANGE_EXPONENTIAL = 0, 1
-FBF_SPATIAL_GAUSSIAN, FBF_SPATIAL_BOX = 0, 1
+FBF_SPATIAL_GAUSSIAN, FBF_SPATIAL_BOX, FBF_SPATIAL_GAUSSIAN_RECURSIVE = 0, 1, 2
 FBF_BORDER_REFLECT, FBF_BORDER_TRUNCATE = 0, 1
 FBF_U8, FBF_F32 = 0, 1
 FBF_FORM_AUTO, FBF_FORM_FP32, FBF_FORM_TC_FP16, FBF_FORM_TC_BF16, FBF_FORM_TC_FP16_SINGLE = 0, 1, 2, 3, 4
@@ -28,7 +28,7 @@ FBF_FORM_TC_BF16_SINGLE = 5
 SCHEDULES = ["persistent", "persistent_wide", "per_image_fp32", "per_image_form", "per_image_fp32_streams",
              "per_image_form_streams", "persistent_tc"]
 
-_NAMES = {"gaussian": 0, "exponential": 1, "box": 1, "reflect": 0, "truncate": 1,
+_NAMES = {"gaussian": 0, "exponential": 1, "box": 1, "gaussian_recursive": 2, "reflect": 0, "truncate": 1,
           "auto": 0, "fp32": 1, "tc_fp16": 2, "tc_bf16": 3, "tc_fp16_single": 4, "tc_bf16_single": 5}
 
 
