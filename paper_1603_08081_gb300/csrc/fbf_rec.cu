@@ -5,7 +5,8 @@
 // second-order sections per channel (coefficients from recursive_coeffs).
 //
 // Per chunk of harmonics (all of them when the scratch fits 4 GiB), three
-// kernels, one thread per image line and harmonic:
+// kernels, one thread per image line, harmonic and channel pair (cos, sin) or
+// ((f - T/2) cos, (f - T/2) sin):
 //   rec_v    thread (column x, harmonic n): modulates f(y, x) on the fly into
 //            the four real channels (cos, sin, (f - T/2) cos, (f - T/2) sin)(n w f)
 //            (exact integer phase n f mod 2T, a 256-entry table per block), runs
@@ -17,7 +18,7 @@
 //   rec_h    thread (row y, harmonic n): the same recursions along x on vt
 //            (consecutive threads read consecutive y: coalesced), the causal
 //            result kept in s2 (same layout), then demodulation:
-//            (P_n, Q_n) = d_n ((cos, sin) . (Fr, Fi), (cos, sin) . (Gr, Gi));
+//            P_n = d_n (cos, sin) . (Fr, Fi) or Q_n = d_n (cos, sin) . (Gr, Gi);
 //   rec_out  sums (P_n, Q_n) over the chunk (and the chunks before it) and, on
 //            the last chunk, writes fhat = P / Q + T/2 through a tile transpose.
 // Borders: TRUNCATE is zero outside the image; REFLECT extends every line by E
@@ -49,7 +50,7 @@ struct RecArgs {
   float rn[2][2], rm[2][2], rp[2][2];
   float *vt;    // [nh][4][Wd][H] vertical pass, transposed
   float *s2;    // [nh][4] planes: causal half of the vertical pass ([y][x]), then of the horizontal one ([x][y])
-  float2 *pq;   // [nh][Wd][H]    (P_n, Q_n)
+  float *pq;    // [nh][2][Wd][H] P_n and Q_n planes
   float2 *acc;  // [Wd][H]        (P, Q) of the chunks so far
   float d[FBF_KMAX];
 };
@@ -65,14 +66,14 @@ __device__ __forceinline__ void build_tab(float2 *tab, int n, const RecArgs &r) 
   __syncthreads();
 }
 
-// One step of the causal recursion (both sections, four channels): input c,
+// One step of the causal recursion (both sections, the thread's two channels): input c,
 // state x1 (previous input), y1, y2 (previous outputs per section); returns
 // the sum of the sections in yo.
 struct Causal {
-  float x1[4] = {}, y1[2][4] = {}, y2[2][4] = {};
-  __device__ __forceinline__ void step(const RecArgs &r, const float (&c)[4], float (&yo)[4]) {
+  float x1[2] = {}, y1[2][2] = {}, y2[2][2] = {};
+  __device__ __forceinline__ void step(const RecArgs &r, const float (&c)[2], float (&yo)[2]) {
 #pragma unroll
-    for (int ch = 0; ch < 4; ++ch) {
+    for (int ch = 0; ch < 2; ++ch) {
 #pragma unroll
       for (int i = 0; i < 2; ++i) {
         const float yn = fmaf(-r.rp[i][0], y1[i][ch],
@@ -88,10 +89,10 @@ struct Causal {
 // The anticausal recursion, run backwards: the output at k uses the inputs at
 // k + 1, k + 2 (x1, x2) and the outputs at k + 1, k + 2; then takes input c.
 struct Anticausal {
-  float x1[4] = {}, x2[4] = {}, z1[2][4] = {}, z2[2][4] = {};
-  __device__ __forceinline__ void step(const RecArgs &r, const float (&c)[4], float (&yo)[4]) {
+  float x1[2] = {}, x2[2] = {}, z1[2][2] = {}, z2[2][2] = {};
+  __device__ __forceinline__ void step(const RecArgs &r, const float (&c)[2], float (&yo)[2]) {
 #pragma unroll
-    for (int ch = 0; ch < 4; ++ch) {
+    for (int ch = 0; ch < 2; ++ch) {
 #pragma unroll
       for (int i = 0; i < 2; ++i) {
         const float zn = fmaf(-r.rp[i][0], z1[i][ch],
@@ -108,37 +109,36 @@ struct Anticausal {
 
 __global__ void __launch_bounds__(32) fbf_rec_v_kernel(const __grid_constant__ RecArgs r) {
   __shared__ float2 tab[256];
-  __shared__ float tile[4][32][33];  // [channel][column in block][row in group]
-  const int lane = threadIdx.x, x0 = blockIdx.x * 32, x = x0 + lane, nl = blockIdx.y;
+  __shared__ float tile[2][32][33];  // [channel of the pair][column in block][row in group]
+  // channel pair cp = blockIdx.z: 0 = (cos, sin), 1 = ((f - T/2) cos, (f - T/2) sin)
+  const int lane = threadIdx.x, x0 = blockIdx.x * 32, x = x0 + lane, nl = blockIdx.y, cp = blockIdx.z;
   build_tab(tab, r.n0 + nl, r);
   const int H = r.H, Wd = r.Wd;
   const bool reflect = r.border == FBF_BORDER_REFLECT;
   const int E = reflect ? r.E : 0;
   const int xs = x < Wd ? x : Wd - 1;  // lanes past the image compute on a clamped column, store nothing
-  float *vt = r.vt + (size_t)nl * 4 * Wd * H;
+  float *vt = r.vt + ((size_t)nl * 4 + 2 * cp) * Wd * H;
   // pixel of extended row ye, or -1 outside a TRUNCATE image
   auto load = [&](int ye) -> int {
     if (!reflect && (ye < 0 || ye >= H)) return -1;
     const int sy = reflect ? reflect_index(ye, H) : ye;
     return __ldg(r.in + (size_t)sy * r.in_pitch + xs);
   };
-  auto chan = [&](int v, float (&c)[4]) {
+  auto chan = [&](int v, float (&c)[2]) {
     if (v < 0) {
-      c[0] = c[1] = c[2] = c[3] = 0.f;
+      c[0] = c[1] = 0.f;
       return;
     }
     const float2 cs = tab[v];
-    const float fv = (float)v - r.c0;
-    c[0] = cs.x;
-    c[1] = cs.y;
-    c[2] = fv * cs.x;
-    c[3] = fv * cs.y;
+    const float fv = cp ? (float)v - r.c0 : 1.f;
+    c[0] = fv * cs.x;
+    c[1] = fv * cs.y;
   };
   // the tile of rows [base, last] to / from vt: lane = row offset (coalesced)
   auto flush = [&](int base, int lastrow) {
     __syncwarp();
     const int y = base + lane;
-    for (int ch = 0; ch < 4; ++ch)
+    for (int ch = 0; ch < 2; ++ch)
       for (int xl = 0; xl < 32 && x0 + xl < Wd; ++xl)
         if (y <= lastrow) vt[((size_t)ch * Wd + x0 + xl) * H + y] = tile[ch][xl][lane];
     __syncwarp();
@@ -148,7 +148,7 @@ __global__ void __launch_bounds__(32) fbf_rec_v_kernel(const __grid_constant__ R
   // half goes to s2 in natural layout ([c][y][x], coalesced over the lanes);
   // the anticausal pass reads it back with its own loads and writes the sum
   // to vt through the transposing tile.
-  float *sh = r.s2 + (size_t)nl * 4 * Wd * H;
+  float *sh = r.s2 + ((size_t)nl * 4 + 2 * cp) * Wd * H;
   const size_t plane = (size_t)Wd * H;
   const bool xin = x < Wd;
   Causal cz;
@@ -160,37 +160,37 @@ __global__ void __launch_bounds__(32) fbf_rec_v_kernel(const __grid_constant__ R
     for (int j = 0; j < kChunk; ++j) {
       const int ye = y0 + j;
       if (ye >= H + E) break;
-      float c[4], yo[4];
+      float c[2], yo[2];
       chan(vv[j], c);
       cz.step(r, c, yo);
       if (xin && ye >= 0 && ye < H) {
 #pragma unroll
-        for (int ch = 0; ch < 4; ++ch) sh[(size_t)ch * plane + (size_t)ye * Wd + x] = yo[ch];
+        for (int ch = 0; ch < 2; ++ch) sh[(size_t)ch * plane + (size_t)ye * Wd + x] = yo[ch];
       }
     }
   }
   Anticausal az;
   for (int y0 = H + E - 1; y0 >= -E; y0 -= kChunkA) {
     int vv[kChunkA];
-    float sv[kChunkA][4];
+    float sv[kChunkA][2];
 #pragma unroll
     for (int j = 0; j < kChunkA; ++j) {
       const int ye = y0 - j;
       vv[j] = ye >= -E ? load(ye) : -1;
       const bool out = xin && ye >= 0 && ye < H;
 #pragma unroll
-      for (int ch = 0; ch < 4; ++ch) sv[j][ch] = out ? sh[(size_t)ch * plane + (size_t)ye * Wd + x] : 0.f;
+      for (int ch = 0; ch < 2; ++ch) sv[j][ch] = out ? sh[(size_t)ch * plane + (size_t)ye * Wd + x] : 0.f;
     }
 #pragma unroll
     for (int j = 0; j < kChunkA; ++j) {
       const int ye = y0 - j;
       if (ye < -E) break;
-      float c[4], yo[4];
+      float c[2], yo[2];
       chan(vv[j], c);
       az.step(r, c, yo);
       if (ye >= 0 && ye < H) {
 #pragma unroll
-        for (int ch = 0; ch < 4; ++ch) tile[ch][lane][ye & 31] = yo[ch] + sv[j][ch];
+        for (int ch = 0; ch < 2; ++ch) tile[ch][lane][ye & 31] = yo[ch] + sv[j][ch];
         if ((ye & 31) == 0) flush(ye, ye + 31 < H - 1 ? ye + 31 : H - 1);
       }
     }
@@ -199,49 +199,49 @@ __global__ void __launch_bounds__(32) fbf_rec_v_kernel(const __grid_constant__ R
 
 __global__ void __launch_bounds__(32) fbf_rec_h_kernel(const __grid_constant__ RecArgs r) {
   __shared__ float2 tab[256];
-  const int lane = threadIdx.x, y = blockIdx.x * 32 + lane, nl = blockIdx.y, n = r.n0 + nl;
+  const int lane = threadIdx.x, y = blockIdx.x * 32 + lane, nl = blockIdx.y, n = r.n0 + nl, cp = blockIdx.z;
   build_tab(tab, n, r);
   const int H = r.H, Wd = r.Wd;
   const bool reflect = r.border == FBF_BORDER_REFLECT;
   const int E = reflect ? r.E : 0;
   const bool yin = y < H;
   const size_t plane = (size_t)Wd * H;
-  const float *vt = r.vt + (size_t)nl * 4 * plane;
-  float *s2 = r.s2 + (size_t)nl * 4 * plane;
-  float2 *pq = r.pq + (size_t)nl * plane;
+  const float *vt = r.vt + ((size_t)nl * 4 + 2 * cp) * plane;
+  float *s2 = r.s2 + ((size_t)nl * 4 + 2 * cp) * plane;
+  float *pq = r.pq + ((size_t)nl * 2 + (cp ? 0 : 1)) * plane;  // P plane (cp 1) or Q plane (cp 0)
   const float dn = r.d[n];
-  auto chan = [&](int xe, float (&c)[4]) {
+  auto chan = [&](int xe, float (&c)[2]) {
     const bool in_img = xe >= 0 && xe < Wd;
     if (!yin || (!reflect && !in_img) || xe < -E || xe >= Wd + E) {
-      c[0] = c[1] = c[2] = c[3] = 0.f;
+      c[0] = c[1] = 0.f;
       return;
     }
     const int sx = reflect ? reflect_index(xe, Wd) : xe;
 #pragma unroll
-    for (int ch = 0; ch < 4; ++ch) c[ch] = vt[(size_t)ch * plane + (size_t)sx * H + y];
+    for (int ch = 0; ch < 2; ++ch) c[ch] = vt[(size_t)ch * plane + (size_t)sx * H + y];
   };
   // kChunkH steps' loads are issued together (see rec_v)
   Causal cz;
   for (int x0 = -E; x0 < Wd + E; x0 += kChunkH) {
-    float cc[kChunkH][4];
+    float cc[kChunkH][2];
 #pragma unroll
     for (int j = 0; j < kChunkH; ++j) chan(x0 + j, cc[j]);
 #pragma unroll
     for (int j = 0; j < kChunkH; ++j) {
       const int xe = x0 + j;
       if (xe >= Wd + E) break;
-      float yo[4];
+      float yo[2];
       cz.step(r, cc[j], yo);
       if (yin && xe >= 0 && xe < Wd) {
 #pragma unroll
-        for (int ch = 0; ch < 4; ++ch) s2[(size_t)ch * plane + (size_t)xe * H + y] = yo[ch];
+        for (int ch = 0; ch < 2; ++ch) s2[(size_t)ch * plane + (size_t)xe * H + y] = yo[ch];
       }
     }
   }
   Anticausal az;
   const unsigned char *row = r.in + (size_t)(yin ? y : 0) * r.in_pitch;
   for (int x0 = Wd + E - 1; x0 >= -E; x0 -= kChunkH) {
-    float cc[kChunkH][4], sv[kChunkH][4];
+    float cc[kChunkH][2], sv[kChunkH][2];
     int fv[kChunkH];
 #pragma unroll
     for (int j = 0; j < kChunkH; ++j) {
@@ -249,22 +249,19 @@ __global__ void __launch_bounds__(32) fbf_rec_h_kernel(const __grid_constant__ R
       chan(xe, cc[j]);
       const bool out = yin && xe >= 0 && xe < Wd;
 #pragma unroll
-      for (int ch = 0; ch < 4; ++ch) sv[j][ch] = out ? s2[(size_t)ch * plane + (size_t)xe * H + y] : 0.f;
+      for (int ch = 0; ch < 2; ++ch) sv[j][ch] = out ? s2[(size_t)ch * plane + (size_t)xe * H + y] : 0.f;
       fv[j] = out ? __ldg(row + xe) : 0;
     }
 #pragma unroll
     for (int j = 0; j < kChunkH; ++j) {
       const int xe = x0 - j;
       if (xe < -E) break;
-      float yo[4];
+      float yo[2];
       az.step(r, cc[j], yo);
       if (yin && xe >= 0 && xe < Wd) {
-        float v[4];
-#pragma unroll
-        for (int ch = 0; ch < 4; ++ch) v[ch] = yo[ch] + sv[j][ch];
-        // demodulate: Re[e^{-i n w f} (filtered channel)] for the G and F pairs
+        // demodulate: Re[e^{-i n w f} (filtered pair)]: Q_n for (cos, sin), P_n for the f-weighted pair
         const float2 cs = tab[fv[j]];
-        pq[(size_t)xe * H + y] = make_float2(dn * fmaf(cs.x, v[2], cs.y * v[3]), dn * fmaf(cs.x, v[0], cs.y * v[1]));
+        pq[(size_t)xe * H + y] = dn * fmaf(cs.x, yo[0] + sv[j][0], cs.y * (yo[1] + sv[j][1]));
       }
     }
   }
@@ -285,9 +282,8 @@ __global__ void __launch_bounds__(1024) fbf_rec_out_kernel(const __grid_constant
     const size_t o = (size_t)x * H + y, plane = (size_t)Wd * H;
     if (!r.first) a = r.acc[o];
     for (int nl = 0; nl < r.nh; ++nl) {
-      const float2 v = r.pq[(size_t)nl * plane + o];
-      a.x += v.x;
-      a.y += v.y;
+      a.x += r.pq[(size_t)(2 * nl) * plane + o];
+      a.y += r.pq[(size_t)(2 * nl + 1) * plane + o];
     }
     if (!r.last) r.acc[o] = a;
   }
@@ -336,7 +332,7 @@ fbf_status launch_rec_u8(const FilterArgs &a, cudaStream_t s) {
   for (int k = 0; k < FBF_KMAX; ++k) r.d[k] = k < K ? a.d[k] : 0.f;
   r.vt = reinterpret_cast<float *>(scratch);
   r.s2 = reinterpret_cast<float *>(scratch + vt_b);
-  r.pq = reinterpret_cast<float2 *>(scratch + 2 * vt_b);
+  r.pq = reinterpret_cast<float *>(scratch + 2 * vt_b);
   r.acc = acc_b ? reinterpret_cast<float2 *>(scratch + 2 * vt_b + pq_b) : nullptr;
   fbf_status st = FBF_OK;
   for (int n0 = 0; n0 < K && st == FBF_OK; n0 += nh) {
@@ -344,8 +340,8 @@ fbf_status launch_rec_u8(const FilterArgs &a, cudaStream_t s) {
     r.nh = std::min(nh, K - n0);
     r.first = n0 == 0;
     r.last = n0 + r.nh >= K;
-    fbf_rec_v_kernel<<<dim3((Wd + 31) / 32, r.nh), 32, 0, s>>>(r);
-    fbf_rec_h_kernel<<<dim3((H + 31) / 32, r.nh), 32, 0, s>>>(r);
+    fbf_rec_v_kernel<<<dim3((Wd + 31) / 32, r.nh, 2), 32, 0, s>>>(r);
+    fbf_rec_h_kernel<<<dim3((H + 31) / 32, r.nh, 2), 32, 0, s>>>(r);
     fbf_rec_out_kernel<<<dim3((Wd + 31) / 32, (H + 31) / 32), dim3(32, 32), 0, s>>>(r);
     st = cuda_status(cudaGetLastError());
   }
