@@ -735,28 +735,43 @@ __device__ __forceinline__ void tc2_body(const FilterArgs *a1, const CUtensorMap
         for (int uu = 0; uu < UPT; ++uu) {
           const int u = uu == 0 ? demod_u : halo_unit(uu - 1);
           int vm[8];
+          // A unit whose 8 pixels lie inside the image and the box (the common
+          // case) is one aligned 8-byte read of the box: the box starts at a
+          // multiple of 16 columns below tx0 - Wp, and units start at multiples
+          // of 8 from there.
+          const int ix0 = tx0 - Wp + 8 * (u < 0 ? 0 : u);
+          const int ry = (reflect ? sy : iy) - by0, bxu = ix0 - bx0;
+          const bool fast = tma_here && u >= 0 && (reflect || row_in) && ix0 >= 0 && ix0 + 8 <= Wd && ry >= 0 &&
+                            ry < kLanes && bxu >= 0 && bxu + 8 <= kBoxW;
+          uint2 w8 = make_uint2(0u, 0u);
+          if (fast) w8 = *reinterpret_cast<const uint2 *>(box + ry * kBoxW + bxu);
   #pragma unroll
           for (int j = 0; j < 8; ++j) {
-            const int ix = tx0 - Wp + 8 * (u < 0 ? 0 : u) + j;
-            bool in_img = row_in && ix >= 0 && ix < Wd;
-            int sx = ix;
-            if (reflect) {
-              sx = reflect_index(ix, Wd);
-              in_img = true;
-            }
             int v = 0;
-            if (in_img && u >= 0) {
-              const int by = (reflect ? sy : iy) - by0, bx = sx - bx0;
-              if (tma_here && by >= 0 && by < kLanes && bx >= 0 && bx < kBoxW)
-                v = box[by * kBoxW + bx];
-              else
-                v = __ldg(in + (size_t)(reflect ? sy : iy) * in_pitch + sx);
+            bool valid = true;
+            if (fast) {
+              v = (int)(((j < 4 ? w8.x : w8.y) >> (8 * (j & 3))) & 0xFFu);
+            } else {
+              const int ix = ix0 + j;
+              bool in_img = row_in && ix >= 0 && ix < Wd;
+              int sx = ix;
+              if (reflect) {
+                sx = reflect_index(ix, Wd);
+                in_img = true;
+              }
+              if (in_img && u >= 0) {
+                const int by = (reflect ? sy : iy) - by0, bx = sx - bx0;
+                if (tma_here && by >= 0 && by < kLanes && bx >= 0 && bx < kBoxW)
+                  v = box[by * kBoxW + bx];
+                else
+                  v = __ldg(in + (size_t)(reflect ? sy : iy) * in_pitch + sx);
+              }
+              valid = in_img && u >= 0;
             }
-            const bool valid = in_img && u >= 0;
             po[uu][j] = (valid ? v : kZeroV) * kEntry + copy_off;
             if (uu == 0) {
               mo[j] = valid ? copy8 : copy8 - kCopies * 8;  // entry m = 0, or the zero entry
-              vm[j] = valid ? (v % twoT) * (kCopies * 8) : 0;
+              vm[j] = valid ? (v < twoT ? v : v % twoT) * (kCopies * 8) : 0;
             }
           }
           if (uu == 0) {
@@ -828,13 +843,40 @@ __device__ __forceinline__ void tc2_body(const FilterArgs *a1, const CUtensorMap
       }
       if (!ok) break;
 
-      // ---- fhat = P / Q + c0 for this thread's 8 pixels of output row iy
-      if (r >= W && r < kLanes - W && iy < H) {
-        float *orow = reinterpret_cast<float *>(reinterpret_cast<char *>(A->out) + (size_t)iy * A->out_pitch);
-        const int x0 = tx0 + 8 * h;
+      // ---- fhat = P / Q + c0, staged in B2 (free: every thread has seen the last
+      // column MMAs complete) so that the stores leave as whole 128-byte row
+      // segments.  Stage row r = ext row r, 32 floats in eight 16-byte slots,
+      // slot s stored at s ^ (r & 7) (conflict-free writes of a warp's 32 rows).
+      {
+        float *stage = reinterpret_cast<float *>(B2);
   #pragma unroll
-        for (int j = 0; j < 8; ++j)
-          if (x0 + j < Wd) orow[x0 + j] = P[j] / Q[j] + c0;
+        for (int k = 0; k < 2; ++k) {
+          const int sl = (2 * h + k) ^ (r & 7);
+          *reinterpret_cast<float4 *>(stage + r * 32 + sl * 4) =
+              make_float4(P[4 * k] / Q[4 * k] + c0, P[4 * k + 1] / Q[4 * k + 1] + c0, P[4 * k + 2] / Q[4 * k + 2] + c0,
+                          P[4 * k + 3] / Q[4 * k + 3] + c0);
+        }
+        asm volatile("bar.sync 1, %0;" ::"n"(kNC) : "memory");  // the compute threads only
+        float *out = static_cast<float *>(A->out);
+        const size_t opitch = A->out_pitch;
+        const bool vec = ((reinterpret_cast<uintptr_t>(out) | opitch) & 15) == 0;
+  #pragma unroll
+        for (int k = 0; k < 2; ++k) {
+          const int e = tid + k * kNC, row = e >> 3, sl = e & 7;  // 128 rows x 8 slots
+          const int oy = ty0 - W + row, ox = tx0 + 4 * sl;
+          if (row >= W && row < kLanes - W && oy < H && ox < Wd) {
+            const float4 v = *reinterpret_cast<const float4 *>(stage + row * 32 + ((sl ^ (row & 7)) * 4));
+            float *orow = reinterpret_cast<float *>(reinterpret_cast<char *>(out) + (size_t)oy * opitch);
+            if (vec && ox + 4 <= Wd) {
+              *reinterpret_cast<float4 *>(orow + ox) = v;
+            } else {
+              orow[ox] = v.x;
+              if (ox + 1 < Wd) orow[ox + 1] = v.y;
+              if (ox + 2 < Wd) orow[ox + 2] = v.z;
+              if (ox + 3 < Wd) orow[ox + 3] = v.w;
+            }
+          }
+        }
       }
     }
     finish(ok);
