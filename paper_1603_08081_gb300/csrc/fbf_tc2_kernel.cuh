@@ -77,7 +77,7 @@ constexpr int kNC = 512;           // compute threads per CTA (four groups of fo
 constexpr int kNT = kNC + 128;     // + one warpgroup of MMA / TMA issuers
 constexpr int kRegCompute = 112;   // registers per thread after setmaxnreg: compute warpgroups
 constexpr int kRegIssue = 24;      //   and the issuing warpgroup (4 x 112 + 24 <= 5 x 96 per SM sub-partition);
-constexpr int kRegIssueBatch = 32; //   32 in batched launches (4 x 112 + 32 = 5 x 96)
+constexpr int kRegIssueBatch = 32; //   32 in batched launches and without barrier A (4 x 112 + 32 = 5 x 96)
 constexpr int kLanes = 128;        // TMEM lanes = ext rows per tile
 constexpr int kBX = 32;            // output columns per tile
 constexpr int kTrigEntries = 510;  // 2T <= 510 (T <= 255)
@@ -227,6 +227,13 @@ __device__ __forceinline__ void tc2_body(const FilterArgs *a1, const CUtensorMap
   static_assert(kA1 + 4 * kA1Parts * kA1Stride <= kD1, "A1 fits below D1");
   static_assert(KXC >= 2 && KXC <= 8, "row chunks");
   constexpr Layout Ly = layout<NSPLIT, KXC>();
+  // kNoA (separate D1 / D2, windows up to 16): no CTA barrier between the
+  // modulation of n + 1 and the rest of harmonic n.  The row issuers wait on
+  // mbarA (one arrival per compute warp, after its A1 stores) instead; every
+  // other dependence across that point is a per-thread MMA wait or the
+  // barrier that ends the harmonic.  -3.5% at W = 9 and 15; at W = 30 the
+  // larger row pass leaves nothing to gain (+0.4%), so it keeps the barrier.
+  constexpr bool kNoA = !SHARED && KXC <= 4;
   extern __shared__ __align__(1024) unsigned char smem[];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -252,6 +259,7 @@ __device__ __forceinline__ void tc2_body(const FilterArgs *a1, const CUtensorMap
   uint64_t *mbarT = reinterpret_cast<uint64_t *>(smem + Ly.bar + 16);
   uint64_t *mbarD = reinterpret_cast<uint64_t *>(smem + Ly.bar + 24);
   uint32_t *tmem_base_s = reinterpret_cast<uint32_t *>(smem + Ly.bar + 32);
+  uint64_t *mbarA = reinterpret_cast<uint64_t *>(smem + Ly.bar + 40);
   // byte offset of entry 0 of the trig table, this lane's copy folded in
   const int tb = (int)Ly.trig + kCopies * 8;
   const int bv = tid & 255, bhalf = tid >> 8;  // channel-table entry built by this thread
@@ -358,6 +366,7 @@ __device__ __forceinline__ void tc2_body(const FilterArgs *a1, const CUtensorMap
     mbar_init(mbarC, 1);
     mbar_init(mbarT, 1);
     mbar_init(mbarD, 3);  // drain: one commit per MMA-issuing thread
+    mbar_init(mbarA, kNC / 32);  // kNoA: A1 of the next harmonic stored, one arrival per compute warp
     mbar_fence_init();
   }
   if (!BATCH) {  // one image: its tables once, by every thread (batch: per image, below)
@@ -425,7 +434,7 @@ __device__ __forceinline__ void tc2_body(const FilterArgs *a1, const CUtensorMap
   };
   unsigned char *t16 = smem + Ly.t16;
 
-  uint32_t phR = 0, phC = 0, phT = 0;
+  uint32_t phR = 0, phC = 0, phT = 0, phA = 0;
   bool fail = false;
   const uint32_t polls = x.polls;
   auto wait_bar = [&](uint64_t *m, uint32_t &ph) {
@@ -641,7 +650,7 @@ __device__ __forceinline__ void tc2_body(const FilterArgs *a1, const CUtensorMap
   // below, issuing at each point what the barrier made ready.
   bool ok = tmem_ok;
   if (!compute) {
-    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(BATCH ? kRegIssueBatch : kRegIssue));
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(BATCH || kNoA ? kRegIssueBatch : kRegIssue));
     for (int it = blockIdx.x; it < nitems && ok; it += gridDim.x) {
       int K = A->K;
       if (BATCH) {  // this item's image: its harmonics and row chunks
@@ -681,7 +690,7 @@ __device__ __forceinline__ void tc2_body(const FilterArgs *a1, const CUtensorMap
       for (int n = 0; n < K; ++n) {
         const bool more = n + 1 < K;
         if (col_issuer) issue_col();  // C(n)
-        if (!(ok = phase_sync())) break;  // A1 <- harmonic n + 1 (SEQ: hi part)
+        if (!kNoA && !(ok = phase_sync())) break;  // A1 <- harmonic n + 1 (SEQ: hi part)
         if (SHARED) {
           if (!(ok = phase_sync())) break;  // D2 (= D1) read
           if (more && row_issuer) issue_row(0);
@@ -689,8 +698,17 @@ __device__ __forceinline__ void tc2_body(const FilterArgs *a1, const CUtensorMap
             if (!(ok = phase_sync())) break;  // A1 <- lo part
             if (row_issuer) issue_row(1);
           }
-        } else {
-          if (more && row_issuer) issue_row(0);  // R(n+1)
+        } else if (more && row_issuer) {  // R(n+1) (kNoA: once every compute warp has stored A1)
+          if (!kNoA) {
+            issue_row(0);
+          } else if (mbar_wait_bounded(mbarA, phA, polls)) {
+            fence_after_sync();
+            issue_row(0);
+            phA ^= 1;
+          } else {
+            fail = true;
+            phA ^= 1;
+          }
         }
         if (!(ok = phase_sync())) break;  // B2 <- harmonic n + 1
       }
@@ -825,7 +843,13 @@ __device__ __forceinline__ void tc2_body(const FilterArgs *a1, const CUtensorMap
       for (int n = 0; n < K; ++n) {
         const bool more = n + 1 < K;
         if (more) modulate((n + 1) & 1, 0);  // A1 <- harmonic n + 1 (while C(n): B2 -> D2 runs)
-        if (!(ok = phase_sync())) break;
+        if (!kNoA) {
+          if (!(ok = phase_sync())) break;
+        } else if (more) {  // this warp's A1 stores are complete: the row MMAs may start
+          fence_before_sync();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(mbarA);
+        }
         // the table of n + 2 replaces that of n (read by the modulation of n, done)
         if (SHARED) {
           if (n + 2 < K) build_table(n + 2, n & 1);
