@@ -232,8 +232,10 @@ __device__ __forceinline__ void tc2_body(const FilterArgs *a1, const CUtensorMap
   // mbarA (one arrival per compute warp, after its A1 stores) instead; every
   // other dependence across that point is a per-thread MMA wait or the
   // barrier that ends the harmonic.  -3.5% at W = 9 and 15; at W = 30 the
-  // larger row pass leaves nothing to gain (+0.4%), so it keeps the barrier.
-  constexpr bool kNoA = !SHARED && KXC <= 4;
+  // larger row pass leaves nothing to gain (+0.4%), so one image keeps the
+  // barrier there; the persistent batch takes the schedule at every window
+  // (5.97 against 6.25 ms on 64 uneven images).
+  constexpr bool kNoA = !SHARED && (KXC <= 4 || BATCH);
   extern __shared__ __align__(1024) unsigned char smem[];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
