@@ -318,6 +318,26 @@ def tensor_peak():
         return 1900.0, "profiling-recipe fallback 1.9 PFLOP/s bf16 burst (of fallback)"
 
 
+def hbm_peak():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"]), "MEASURED_PEAKS.json hbm_gbs (copy) (of measured)"
+    except Exception:
+        return 6800.0, "profiling-recipe fallback 6.8 TB/s (of fallback)"
+
+
+# Recursive form, per pixel and harmonic.  Flops: four channels, two 1-D passes,
+# a causal and an anticausal fourth-order recursion each (4 feed-forward + 4
+# feedback multiply-adds per sample) = 4 * 2 * 2 * 8 * 2 = 256.  Bytes: the
+# planes the three-kernel design streams through HBM -- vertical pass: causal
+# half written and read back (16 + 16), transposed sum written (16); horizontal
+# pass: that sum read (16), causal half written and read back (16 + 16), P_n /
+# Q_n written (8); sum over harmonics: P_n / Q_n read (8).  A design figure, not
+# an algorithmic minimum (a line held on chip would need no causal-half planes).
+REC_FLOP_PER_PX_HARMONIC = 256
+REC_BYTES_PER_PX_HARMONIC = 112
+
+
 def _gen_image(spec):
     from paper_1603_08081_gb300.synth import make_image
 
@@ -511,10 +531,23 @@ def run_recursive(fbf, torch, dev, stream, steps, flush, with_oracle):
     xc = torch.from_numpy(crop).to(dev)
     res = {"workload": "2048x2048 u8 synthetic (seed 1100), sigma_r=20 (K=%d), eps=1e-3, reflect; "
                        "recursive Gaussian (FP32) vs FIR forms" % c.K, "runs": []}
+    hpeak, hsrc = hbm_peak()
+    fp32_peak = fbf.fbf_measure_fp32_peak(dev.index if dev.index is not None else 0)
+    res["roofline_basis"] = {"bytes_per_px_harmonic": REC_BYTES_PER_PX_HARMONIC,
+                             "flop_per_px_harmonic": REC_FLOP_PER_PX_HARMONIC, "hbm_peak_gbs": hpeak,
+                             "hbm_peak_source": hsrc, "fp32_peak_tflops": round(fp32_peak, 3),
+                             "bytes": "plane traffic of the three-kernel design (write + read of the causal halves, "
+                                      "the transposed vertical result and the P_n / Q_n planes), plus 5 B/px of "
+                                      "image in and result out"}
     for ss in (3.0, 5.0, 10.0, 12.0, 16.0, 32.0):
         p = fbf.make_params(c, ss, 0, "gaussian_recursive", "reflect", "fp32")
         ms = _timed_steps(torch, dev, stream, lambda: fbf.fbf_filter(p, x, out=y, stream=stream), steps, flush)
         row = {"sigma_s": ss, "form": "fp32_recursive", "ms": round(ms, 4), "mpix_s": round(H * W_IMG / ms / 1e3, 1)}
+        gbs = (REC_BYTES_PER_PX_HARMONIC * c.K + 5) * H * W_IMG / (ms * 1e-3) / 1e9
+        tf = REC_FLOP_PER_PX_HARMONIC * c.K * H * W_IMG / (ms * 1e-3) / 1e12
+        row["roofline"] = {"bound": "hbm", "achieved": round(gbs, 1), "peak": hpeak, "unit": "GB/s",
+                           "frac": round(gbs / hpeak, 4), "fp32_tflops": round(tf, 3),
+                           "fp32_frac": round(tf / fp32_peak, 4)}
         W = int(math.ceil(3 * ss - 1e-12))
         if W <= 48:
             for f in ("fp32", "tc_fp16_single"):

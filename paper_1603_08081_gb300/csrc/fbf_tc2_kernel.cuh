@@ -227,15 +227,14 @@ __device__ __forceinline__ void tc2_body(const FilterArgs *a1, const CUtensorMap
   static_assert(kA1 + 4 * kA1Parts * kA1Stride <= kD1, "A1 fits below D1");
   static_assert(KXC >= 2 && KXC <= 8, "row chunks");
   constexpr Layout Ly = layout<NSPLIT, KXC>();
-  // kNoA (separate D1 / D2, windows up to 16): no CTA barrier between the
+  // kNoA (separate D1 / D2, windows up to 32): no CTA barrier between the
   // modulation of n + 1 and the rest of harmonic n.  The row issuers wait on
   // mbarA (one arrival per compute warp, after its A1 stores) instead; every
   // other dependence across that point is a per-thread MMA wait or the
-  // barrier that ends the harmonic.  -3.5% at W = 9 and 15; at W = 30 the
-  // larger row pass leaves nothing to gain (+0.4%), so one image keeps the
-  // barrier there; the persistent batch takes the schedule at every window
-  // (5.97 against 6.25 ms on 64 uneven images).
-  constexpr bool kNoA = !SHARED && (KXC <= 4 || BATCH);
+  // barrier that ends the harmonic.  2048^2, K = 17: -3.5% at W = 9 and 15,
+  // -4% at W = 17, 24 and 30 (with four row issuers; with two it gained
+  // nothing from W = 17 on).
+  constexpr bool kNoA = !SHARED;
   extern __shared__ __align__(1024) unsigned char smem[];
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
