@@ -262,7 +262,9 @@ typedef enum {
  * image's output or input.
  * With more than one candidate the plan autotunes: it replays every
  * candidate on the given images -- writing their outputs -- times each with
- * CUDA events and keeps the fastest (fbf_plan_schedule reports which); this
+ * CUDA events (three rounds over the candidates, three replays a round, each
+ * candidate's best round) and keeps the fastest (fbf_plan_schedule reports
+ * which, with that time); this
  * synchronises the device.  The pointers in `descs` are baked into the plan:
  * the images must stay allocated while the plan is used.  Allocates device
  * memory (synchronously) for the persistent tables.  A fit that misses its
