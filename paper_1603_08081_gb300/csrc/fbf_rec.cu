@@ -55,13 +55,15 @@ struct RecArgs {
   float d[FBF_KMAX];
 };
 
-// (cos, sin)(pi m / T), m = n v mod 2T, for v = 0..255 (exact integer phase).
-__device__ __forceinline__ void build_tab(float2 *tab, int n, const RecArgs &r) {
+// (cos, sin)(pi m / T), m = n v mod 2T, for v = 0..255 (exact integer phase),
+// times (v - T/2) when `weighted` (the channels of the f-weighted pair).
+__device__ __forceinline__ void build_tab(float2 *tab, int n, const RecArgs &r, bool weighted) {
   for (int v = threadIdx.x + threadIdx.y * blockDim.x; v < 256; v += blockDim.x * blockDim.y) {
     const int m = (int)(((long long)n * v) % r.twoT);
     float sn, cs;
     sincospif((float)m / r.T, &sn, &cs);
-    tab[v] = make_float2(cs, sn);
+    const float fv = weighted ? (float)v - r.c0 : 1.f;
+    tab[v] = make_float2(fv * cs, fv * sn);
   }
   __syncthreads();
 }
@@ -112,48 +114,88 @@ __global__ void __launch_bounds__(32) fbf_rec_v_kernel(const __grid_constant__ R
   __shared__ float tile[2][32][33];  // [channel of the pair][column in block][row in group]
   // channel pair cp = blockIdx.z: 0 = (cos, sin), 1 = ((f - T/2) cos, (f - T/2) sin)
   const int lane = threadIdx.x, x0 = blockIdx.x * 32, x = x0 + lane, nl = blockIdx.y, cp = blockIdx.z;
-  build_tab(tab, r.n0 + nl, r);
+  build_tab(tab, r.n0 + nl, r, cp != 0);  // tab[v]: the pair's two channels of pixel value v
   const int H = r.H, Wd = r.Wd;
   const bool reflect = r.border == FBF_BORDER_REFLECT;
   const int E = reflect ? r.E : 0;
   const int xs = x < Wd ? x : Wd - 1;  // lanes past the image compute on a clamped column, store nothing
-  float *vt = r.vt + ((size_t)nl * 4 + 2 * cp) * Wd * H;
+  const size_t plane = (size_t)Wd * H, ip = r.in_pitch;
+  float *vt = r.vt + ((size_t)nl * 4 + 2 * cp) * plane;
+  const unsigned char *col = r.in + xs;  // this thread's column
   // pixel of extended row ye, or -1 outside a TRUNCATE image
   auto load = [&](int ye) -> int {
     if (!reflect && (ye < 0 || ye >= H)) return -1;
     const int sy = reflect ? reflect_index(ye, H) : ye;
-    return __ldg(r.in + (size_t)sy * r.in_pitch + xs);
+    return __ldg(col + (size_t)sy * ip);
   };
   auto chan = [&](int v, float (&c)[2]) {
-    if (v < 0) {
-      c[0] = c[1] = 0.f;
-      return;
-    }
-    const float2 cs = tab[v];
-    const float fv = cp ? (float)v - r.c0 : 1.f;
-    c[0] = fv * cs.x;
-    c[1] = fv * cs.y;
+    const float2 t = v < 0 ? make_float2(0.f, 0.f) : tab[v];
+    c[0] = t.x;
+    c[1] = t.y;
   };
-  // the tile of rows [base, last] to / from vt: lane = row offset (coalesced)
+  // the tile of rows [base, last] to vt: lane = row offset (coalesced); a full
+  // tile (32 columns inside the image, 32 rows) without per-store checks
+  const bool full_cols = x0 + 32 <= Wd;
   auto flush = [&](int base, int lastrow) {
     __syncwarp();
     const int y = base + lane;
-    for (int ch = 0; ch < 2; ++ch)
-      for (int xl = 0; xl < 32 && x0 + xl < Wd; ++xl)
-        if (y <= lastrow) vt[((size_t)ch * Wd + x0 + xl) * H + y] = tile[ch][xl][lane];
+    if (full_cols && lastrow == base + 31) {
+      float *q = vt + (size_t)x0 * H + y;
+#pragma unroll 8
+      for (int xl = 0; xl < 32; ++xl, q += H) {
+        q[0] = tile[0][xl][lane];
+        q[plane] = tile[1][xl][lane];
+      }
+    } else {
+      for (int ch = 0; ch < 2; ++ch)
+        for (int xl = 0; xl < 32 && x0 + xl < Wd; ++xl)
+          if (y <= lastrow) vt[((size_t)ch * Wd + x0 + xl) * H + y] = tile[ch][xl][lane];
+    }
     __syncwarp();
   };
   // The loads of a chunk of steps are issued together, then the recursion runs
   // over them: one load latency per chunk instead of one per step.  The causal
   // half goes to s2 in natural layout ([c][y][x], coalesced over the lanes);
   // the anticausal pass reads it back with its own loads and writes the sum
-  // to vt through the transposing tile.
-  float *sh = r.s2 + ((size_t)nl * 4 + 2 * cp) * Wd * H;
-  const size_t plane = (size_t)Wd * H;
+  // to vt through the transposing tile.  Chunks wholly inside the image take
+  // strided pointers and no border logic.
+  float *sh = r.s2 + ((size_t)nl * 4 + 2 * cp) * plane;
   const bool xin = x < Wd;
   Causal cz;
   for (int y0 = -E; y0 < H + E; y0 += kChunk) {
     int vv[kChunk];
+    if (y0 >= 0 && y0 + kChunk <= H) {
+      const unsigned char *p = col + (size_t)y0 * ip;
+#pragma unroll
+      for (int j = 0; j < kChunk; ++j) vv[j] = __ldg(p + j * ip);
+      float *q = sh + (size_t)y0 * Wd + xs;
+#pragma unroll
+      for (int j = 0; j < kChunk; ++j, q += Wd) {
+        float c[2], yo[2];
+        chan(vv[j], c);
+        cz.step(r, c, yo);
+        if (xin) {
+          q[0] = yo[0];
+          q[plane] = yo[1];
+        }
+      }
+      continue;
+    }
+    const int y1 = y0 + kChunk - 1;
+    if (reflect && y1 < H + E && ((y0 >= -H && y1 < 0) || (y0 >= H && y1 < 2 * H))) {
+      // extension rows mirrored once: source rows s0, s0 - 1, ... (no output)
+      const int s0 = y1 < 0 ? -1 - y0 : 2 * H - 1 - y0;
+      const unsigned char *p = col + (size_t)s0 * ip;
+#pragma unroll
+      for (int j = 0; j < kChunk; ++j) vv[j] = __ldg(p - (size_t)j * ip);
+#pragma unroll
+      for (int j = 0; j < kChunk; ++j) {
+        float c[2], yo[2];
+        chan(vv[j], c);
+        cz.step(r, c, yo);
+      }
+      continue;
+    }
 #pragma unroll
     for (int j = 0; j < kChunk; ++j) vv[j] = y0 + j < H + E ? load(y0 + j) : -1;
 #pragma unroll
@@ -173,6 +215,42 @@ __global__ void __launch_bounds__(32) fbf_rec_v_kernel(const __grid_constant__ R
   for (int y0 = H + E - 1; y0 >= -E; y0 -= kChunkA) {
     int vv[kChunkA];
     float sv[kChunkA][2];
+    if (y0 - (kChunkA - 1) >= 0 && y0 < H) {
+      const unsigned char *p = col + (size_t)y0 * ip;
+      const float *q = sh + (size_t)y0 * Wd + xs;  // clamped column: in bounds, unused past the image
+#pragma unroll
+      for (int j = 0; j < kChunkA; ++j) {
+        vv[j] = __ldg(p - (size_t)j * ip);
+        sv[j][0] = q[-(ptrdiff_t)j * Wd];
+        sv[j][1] = q[plane - (size_t)j * Wd];
+      }
+#pragma unroll
+      for (int j = 0; j < kChunkA; ++j) {
+        const int ye = y0 - j;
+        float c[2], yo[2];
+        chan(vv[j], c);
+        az.step(r, c, yo);
+        tile[0][lane][ye & 31] = yo[0] + sv[j][0];
+        tile[1][lane][ye & 31] = yo[1] + sv[j][1];
+        if ((ye & 31) == 0) flush(ye, ye + 31 < H - 1 ? ye + 31 : H - 1);
+      }
+      continue;
+    }
+    const int y1 = y0 - (kChunkA - 1);
+    if (reflect && y1 >= -E && ((y1 >= H && y0 < 2 * H) || (y1 >= -H && y0 < 0))) {
+      // extension rows mirrored once: source rows s0, s0 + 1, ... (no output)
+      const int s0 = y0 < 0 ? -1 - y0 : 2 * H - 1 - y0;
+      const unsigned char *p = col + (size_t)s0 * ip;
+#pragma unroll
+      for (int j = 0; j < kChunkA; ++j) vv[j] = __ldg(p + (size_t)j * ip);
+#pragma unroll
+      for (int j = 0; j < kChunkA; ++j) {
+        float c[2], yo[2];
+        chan(vv[j], c);
+        az.step(r, c, yo);
+      }
+      continue;
+    }
 #pragma unroll
     for (int j = 0; j < kChunkA; ++j) {
       const int ye = y0 - j;
@@ -200,11 +278,12 @@ __global__ void __launch_bounds__(32) fbf_rec_v_kernel(const __grid_constant__ R
 __global__ void __launch_bounds__(32) fbf_rec_h_kernel(const __grid_constant__ RecArgs r) {
   __shared__ float2 tab[256];
   const int lane = threadIdx.x, y = blockIdx.x * 32 + lane, nl = blockIdx.y, n = r.n0 + nl, cp = blockIdx.z;
-  build_tab(tab, n, r);
+  build_tab(tab, n, r, false);  // the plain (cos, sin) for the demodulation
   const int H = r.H, Wd = r.Wd;
   const bool reflect = r.border == FBF_BORDER_REFLECT;
   const int E = reflect ? r.E : 0;
   const bool yin = y < H;
+  const int yc = yin ? y : H - 1;  // rows past the image load from a clamped row, store nothing
   const size_t plane = (size_t)Wd * H;
   const float *vt = r.vt + ((size_t)nl * 4 + 2 * cp) * plane;
   float *s2 = r.s2 + ((size_t)nl * 4 + 2 * cp) * plane;
@@ -220,10 +299,47 @@ __global__ void __launch_bounds__(32) fbf_rec_h_kernel(const __grid_constant__ R
 #pragma unroll
     for (int ch = 0; ch < 2; ++ch) c[ch] = vt[(size_t)ch * plane + (size_t)sx * H + y];
   };
-  // kChunkH steps' loads are issued together (see rec_v)
+  // kChunkH steps' loads are issued together (see rec_v); chunks wholly inside
+  // the image take strided pointers and no border logic
   Causal cz;
   for (int x0 = -E; x0 < Wd + E; x0 += kChunkH) {
     float cc[kChunkH][2];
+    if (x0 >= 0 && x0 + kChunkH <= Wd) {
+      const float *p = vt + (size_t)x0 * H + yc;
+#pragma unroll
+      for (int j = 0; j < kChunkH; ++j) {
+        cc[j][0] = p[(size_t)j * H];
+        cc[j][1] = p[plane + (size_t)j * H];
+      }
+      float *q = s2 + (size_t)x0 * H + yc;
+#pragma unroll
+      for (int j = 0; j < kChunkH; ++j) {
+        float yo[2];
+        cz.step(r, cc[j], yo);
+        if (yin) {
+          q[(size_t)j * H] = yo[0];
+          q[plane + (size_t)j * H] = yo[1];
+        }
+      }
+      continue;
+    }
+    const int x1 = x0 + kChunkH - 1;
+    if (reflect && x1 < Wd + E && ((x0 >= -Wd && x1 < 0) || (x0 >= Wd && x1 < 2 * Wd))) {
+      // extension columns mirrored once: source columns s0, s0 - 1, ... (no output)
+      const int s0 = x1 < 0 ? -1 - x0 : 2 * Wd - 1 - x0;
+      const float *p = vt + (size_t)s0 * H + yc;
+#pragma unroll
+      for (int j = 0; j < kChunkH; ++j) {
+        cc[j][0] = p[-(ptrdiff_t)j * H];
+        cc[j][1] = p[plane - (size_t)j * H];
+      }
+#pragma unroll
+      for (int j = 0; j < kChunkH; ++j) {
+        float yo[2];
+        cz.step(r, cc[j], yo);
+      }
+      continue;
+    }
 #pragma unroll
     for (int j = 0; j < kChunkH; ++j) chan(x0 + j, cc[j]);
 #pragma unroll
@@ -240,9 +356,50 @@ __global__ void __launch_bounds__(32) fbf_rec_h_kernel(const __grid_constant__ R
   }
   Anticausal az;
   const unsigned char *row = r.in + (size_t)(yin ? y : 0) * r.in_pitch;
+  const unsigned char *rowc = r.in + (size_t)yc * r.in_pitch;
   for (int x0 = Wd + E - 1; x0 >= -E; x0 -= kChunkH) {
     float cc[kChunkH][2], sv[kChunkH][2];
     int fv[kChunkH];
+    if (x0 - (kChunkH - 1) >= 0 && x0 < Wd) {
+      const float *p = vt + (size_t)x0 * H + yc;
+      const float *q = s2 + (size_t)x0 * H + yc;
+#pragma unroll
+      for (int j = 0; j < kChunkH; ++j) {
+        cc[j][0] = p[-(ptrdiff_t)j * H];
+        cc[j][1] = p[plane - (size_t)j * H];
+        sv[j][0] = q[-(ptrdiff_t)j * H];
+        sv[j][1] = q[plane - (size_t)j * H];
+        fv[j] = __ldg(rowc + x0 - j);
+      }
+      float *o = pq + (size_t)x0 * H + yc;
+#pragma unroll
+      for (int j = 0; j < kChunkH; ++j) {
+        float yo[2];
+        az.step(r, cc[j], yo);
+        if (yin) {
+          const float2 cs = tab[fv[j]];
+          o[-(ptrdiff_t)j * H] = dn * fmaf(cs.x, yo[0] + sv[j][0], cs.y * (yo[1] + sv[j][1]));
+        }
+      }
+      continue;
+    }
+    const int x1 = x0 - (kChunkH - 1);
+    if (reflect && x1 >= -E && ((x1 >= Wd && x0 < 2 * Wd) || (x1 >= -Wd && x0 < 0))) {
+      // extension columns mirrored once: source columns s0, s0 + 1, ... (no output)
+      const int s0 = x0 < 0 ? -1 - x0 : 2 * Wd - 1 - x0;
+      const float *p = vt + (size_t)s0 * H + yc;
+#pragma unroll
+      for (int j = 0; j < kChunkH; ++j) {
+        cc[j][0] = p[(size_t)j * H];
+        cc[j][1] = p[plane + (size_t)j * H];
+      }
+#pragma unroll
+      for (int j = 0; j < kChunkH; ++j) {
+        float yo[2];
+        az.step(r, cc[j], yo);
+      }
+      continue;
+    }
 #pragma unroll
     for (int j = 0; j < kChunkH; ++j) {
       const int xe = x0 - j;
