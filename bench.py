@@ -330,12 +330,14 @@ def hbm_peak():
 # a causal and an anticausal fourth-order recursion each (4 feed-forward + 4
 # feedback multiply-adds per sample) = 4 * 2 * 2 * 8 * 2 = 256.  Bytes: the
 # planes the three-kernel design streams through HBM -- vertical pass: causal
-# half written and read back (16 + 16), transposed sum written (16); horizontal
-# pass: that sum read (16), causal half written and read back (16 + 16), P_n /
-# Q_n written (8); sum over harmonics: P_n / Q_n read (8).  A design figure, not
-# an algorithmic minimum (a line held on chip would need no causal-half planes).
+# half written and read back (16 + 16), transposed sum written (16);
+# horizontal pass: that sum read by each direction (16 + 16), causal half
+# written and read back (16 + 16), P_n / Q_n written (8); sum over harmonics:
+# P_n / Q_n read (8).  A design figure (ncu measures 118 B on a 1024^2 image,
+# a few reads hitting L2), not an algorithmic minimum: a line held on chip
+# would need no intermediate planes.
 REC_FLOP_PER_PX_HARMONIC = 256
-REC_BYTES_PER_PX_HARMONIC = 112
+REC_BYTES_PER_PX_HARMONIC = 128
 
 
 def _gen_image(spec):
@@ -536,9 +538,9 @@ def run_recursive(fbf, torch, dev, stream, steps, flush, with_oracle):
     res["roofline_basis"] = {"bytes_per_px_harmonic": REC_BYTES_PER_PX_HARMONIC,
                              "flop_per_px_harmonic": REC_FLOP_PER_PX_HARMONIC, "hbm_peak_gbs": hpeak,
                              "hbm_peak_source": hsrc, "fp32_peak_tflops": round(fp32_peak, 3),
-                             "bytes": "plane traffic of the three-kernel design (write + read of the causal halves, "
-                                      "the transposed vertical result and the P_n / Q_n planes), plus 5 B/px of "
-                                      "image in and result out"}
+                             "bytes": "plane traffic of the three-kernel design (write + read of the causal halves "
+                                      "and of the P_n / Q_n planes, the transposed vertical result written once and "
+                                      "read by both horizontal directions), plus 5 B/px of image in and result out"}
     for ss in (3.0, 5.0, 10.0, 12.0, 16.0, 32.0):
         p = fbf.make_params(c, ss, 0, "gaussian_recursive", "reflect", "fp32")
         ms = _timed_steps(torch, dev, stream, lambda: fbf.fbf_filter(p, x, out=y, stream=stream), steps, flush)
