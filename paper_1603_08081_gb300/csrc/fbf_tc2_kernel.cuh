@@ -316,14 +316,26 @@ __device__ __forceinline__ void tc2_body(const FilterArgs *a1, const CUtensorMap
   };
   // Row Toeplitz blocks (shared memory, K-major, 1 KB each): chunk i, output x,
   // K index k = ext column 16 i + k: tap 16 i + k - Wp - x + W.
+  // A thread's taps are loaded before any is stored (at most KXC x weight parts
+  // each: stride >= 512), so that their latencies overlap when a batch's CTA
+  // moves to another image.
   auto setup_row_toeplitz = [&](int t0, int stride) {
-    for (int e = t0; e < kcr * kWParts * 512; e += stride) {
-      const int blk = e >> 9, el = e & 511, n = el >> 4, k = el & 15;
-      const int i = blk / kWParts, bp = blk % kWParts;
-      const int t = 16 * i + k - Wp - n + W;
-      const float wv = (t >= 0 && t <= 2 * W) ? A->w[t] : 0.f;
-      const unsigned short hi = to16<BF>(wv);
-      const unsigned short v = bp == 0 ? hi : to16<BF>(wv - from16<BF>(hi));
+    constexpr int kMaxE = KXC * kWParts;
+    const int total = kcr * kWParts * 512;
+    float wv[kMaxE];
+#pragma unroll
+    for (int j = 0; j < kMaxE; ++j) {
+      const int e = t0 + j * stride, blk = e >> 9, el = e & 511, n = el >> 4, k = el & 15;
+      const int t = 16 * (blk / kWParts) + k - Wp - n + W;
+      wv[j] = (e < total && t >= 0 && t <= 2 * W) ? A->w[t] : 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < kMaxE; ++j) {
+      const int e = t0 + j * stride;
+      if (e >= total) break;
+      const int blk = e >> 9, el = e & 511, n = el >> 4, k = el & 15, bp = blk % kWParts;
+      const unsigned short hi = to16<BF>(wv[j]);
+      const unsigned short v = bp == 0 ? hi : to16<BF>(wv[j] - from16<BF>(hi));
       const int off = (n & 7) * 16 + (n >> 3) * 256 + (k & 7) * 2 + (k >> 3) * 128;
       *reinterpret_cast<unsigned short *>(BR + (size_t)blk * 1024 + off) = v;
     }
