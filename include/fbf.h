@@ -235,7 +235,7 @@ typedef enum {
   FBF_SCHEDULE_PER_IMAGE_FORM = 3,  /* one launch per image in the plan's form        */
   FBF_SCHEDULE_PER_IMAGE_FP32_STREAMS = 4, /* PER_IMAGE_FP32 on 4 concurrent branches */
   FBF_SCHEDULE_PER_IMAGE_FORM_STREAMS = 5, /* PER_IMAGE_FORM on 4 concurrent branches */
-  FBF_SCHEDULE_PERSISTENT_TC = 6           /* one persistent tensor-core launch       */
+  FBF_SCHEDULE_PERSISTENT_TC = 6           /* persistent tensor-core launches, one per window band */
 } fbf_schedule;
 
 /*
@@ -249,11 +249,13 @@ typedef enum {
  * spread over four concurrent graph branches (largest images first, each to
  * the least loaded branch), so that small images and the last wave of one
  * image's tiles share the GPU with other images (PERSISTENT needs every
- * W <= 32), and PERSISTENT_TC: one launch of the tensor-core kernel with one
- * CTA per SM taking (image, tile) items of all images -- sorted by estimated
- * cost, most expensive first, CTA b taking items b, b + #SMs, ... -- and
- * rebuilding the image's Toeplitz matrices whenever its next item belongs to
- * another image (tiles 32 x (128 - 2W), every W <= FBF_WMAX, T <= 255).
+ * W <= 32), and PERSISTENT_TC: one persistent launch of the tensor-core
+ * kernel per window band present (W <= 16, 17..32, 33..48), each with one CTA
+ * per SM taking the (image, tile) items of the band's images -- sorted by
+ * estimated cost, most expensive first, CTA b taking items b, b + #SMs, ...
+ * -- and rebuilding the image's Toeplitz matrices whenever its next item
+ * belongs to another image (tiles 32 x (128 - 2W), every W <= FBF_WMAX,
+ * T <= 255).
  * form FP32: PERSISTENT, PERSISTENT_WIDE and both PER_IMAGE_FP32 schedules;
  * AUTO: those and both PER_IMAGE_FORM schedules (per image as fbf_filter's
  * AUTO); TC_FP16_SINGLE: PERSISTENT_TC and both PER_IMAGE_FORM schedules; the
