@@ -209,8 +209,9 @@ fbf_status fbf_filter(const fbf_params *p, const void *d_in, fbf_dtype dtype, in
 /* ---- Batched filtering ---------------------------------------------------
  * Many uint8 images of uneven sizes, each with its own spatial window, range
  * kernel, sigma_r, T and tolerance (hence its own K), filtered by one
- * CUDA graph whose schedule (one persistent launch, or one launch per image)
- * the plan picks by timing the candidates on the batch itself. */
+ * CUDA graph whose schedule (persistent launches over all the images, or one
+ * launch per image) the plan picks by timing the candidates on the batch
+ * itself. */
 
 typedef struct fbf_plan fbf_plan; /* owns its device tables and the graph */
 
