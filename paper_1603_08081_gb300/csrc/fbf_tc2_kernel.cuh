@@ -43,15 +43,18 @@
 // column Toeplitz matrix lives in TMEM (written once per CTA), so the column
 // MMA reads only B2 from shared memory.
 //
-// Schedule (separate D1, D2): per harmonic two phases separated by CTA
-// barriers --
+// Schedule (separate D1, D2): per harmonic two phases, one CTA barrier --
 //   (A) one thread issues the column MMAs of n while every thread modulates
 //       n + 1 (A1 is free: the row MMAs of n finished before the re-split of n);
-//   (B) four threads issue the row MMAs of n + 1; every thread waits for the
-//       column MMAs of n (its own mbarrier wait: it reads only its own lanes),
-//       demodulates n, waits for the row MMAs of n + 1 and re-splits them.
-// With D1 = D2 (SHARED, when A1 needs the TMEM of D2) phase B is split in two:
-// demodulate n, barrier, then the row MMAs of n + 1 and their re-split.
+//       each compute warp then arrives on an mbarrier;
+//   (B) four threads issue the row MMAs of n + 1 once all sixteen warps have
+//       arrived; meanwhile every thread builds the table of n + 2, waits for
+//       the column MMAs of n (its own mbarrier wait: it reads only its own
+//       lanes), demodulates n, waits for the row MMAs of n + 1 and re-splits
+//       them; the CTA barrier then ends the harmonic (B2 rewritten).
+// With D1 = D2 (SHARED, when A1 needs the TMEM of D2) A ends in a CTA barrier
+// and phase B is split in two: demodulate n, barrier, then the row MMAs of
+// n + 1 and their re-split.
 //
 // Bounded waits: every mbarrier wait gives up after a poll limit (a launch
 // argument); the CTA then agrees on the failure at the next barrier, waits
@@ -76,8 +79,8 @@ using namespace tc;
 constexpr int kNC = 512;           // compute threads per CTA (four groups of four warps)
 constexpr int kNT = kNC + 128;     // + one warpgroup of MMA / TMA issuers
 constexpr int kRegCompute = 112;   // registers per thread after setmaxnreg: compute warpgroups
-constexpr int kRegIssue = 24;      //   and the issuing warpgroup (4 x 112 + 24 <= 5 x 96 per SM sub-partition);
-constexpr int kRegIssueBatch = 32; //   32 in batched launches and without barrier A (4 x 112 + 32 = 5 x 96)
+constexpr int kRegIssue = 24;      //   and the issuing warpgroup: 24 for D1 = D2 (W = 33..48; 4 x 112 + 24 <= 5 x 96
+constexpr int kRegIssueBatch = 32; //   per SM sub-partition), 32 otherwise and in batches (4 x 112 + 32 = 5 x 96)
 constexpr int kLanes = 128;        // TMEM lanes = ext rows per tile
 constexpr int kBX = 32;            // output columns per tile
 constexpr int kTrigEntries = 510;  // 2T <= 510 (T <= 255)
