@@ -751,9 +751,12 @@ __device__ __forceinline__ void tc2_body(const FilterArgs *a1, const CUtensorMap
       }
       if (BATCH) {
         const int img = item_image(it);
+        // the image's scalars are read again for every tile (L1 hits) instead
+        // of being held in registers across the harmonic loop (with them held,
+        // the 6- and 8-chunk batched instantiations spilled)
+        set_image(bt.imgs + img);
         if (img != cur) {  // another image: its tables (no MMA is in flight between tiles)
           cur = img;
-          set_image(bt.imgs + img);
           if (A->T != cur_T) {
             setup_trig(tid, kNC);
             cur_T = A->T;
